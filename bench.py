@@ -1,0 +1,351 @@
+"""Benchmark of the lattice Burgers functional-integral hot path on GB300.
+
+One step = one pass of the whole path over the paper-shaped workload: a 10x2
+lattice (20 dimensions, nu = D = a = tau = 1), the box [-5,5]^20 bisected
+along coordinates 0..9 into 1024 subvolumes, 2^20 Philox4x32-10 points per
+subvolume (2^30 samples), evaluated in FP64: points, action, shifted
+weights, products, per-subvolume reduction and the FP64 merge into Z, C(r)
+and their errors.  The metric is samples per second.
+
+With N ranks (torchrun, one GPU each) the box is bisected into 1024 N
+subvolumes and rank r integrates subvolumes [1024 r, 1024 (r + 1)) (weak
+scaling); the per-subvolume records are then gathered to rank 0, which merges
+them (the only exchange of the method).
+
+--impl reference times the plain FP64 CPU oracle on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SAMPLES_PER_SUB = 1 << 20
+NSUB_PER_RANK = 1024
+NX, NT = 10, 2
+D = NX * NT
+R = NX // 2 + 1
+K = 2 + 3 * R
+FP32_SAMPLES_PER_SUB = 1 << 24      # the 2^34-point FP32 form of the same job
+
+# Peaks (derived from the unit counts and clocks of GB300).
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_OPS = 1.25e12 / 2         # nominal 1.25 TFLOP/s FP64 = 6.25e11 FMA/s
+ISSUE_PEAK_OPS = 4 * 32 * SM_COUNT * SM_MAX_MHZ * 1e6   # thread-instructions/s
+
+
+def ops_per_sample_fp64(nx, nt):
+    """Algorithmic FP64 operations per sample (Philox runs on the integer pipes)."""
+    d, r = nx * nt, nx // 2 + 1
+    k = 2 + 3 * r
+    return d + 8 * d + d * r + 1 + 2 * k
+
+
+def ops_per_sample_fp32(nx, nt):
+    """Algorithmic thread operations per sample in the FP32 form."""
+    d, r = nx * nt, nx // 2 + 1
+    k = 2 + 3 * r
+    philox = ((d + 3) // 4) * 10 * 4
+    return philox + 2 * d + 8 * d + d * r + 2 + 5 * k
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def cpu_sample_job():
+    """Bounded sample for the CPU oracle: every 32nd subvolume of the
+    10x2 job (32 subvolumes, their own sub_ids) at the full 2^20 points."""
+    import workloads
+    job = workloads.paper_10x2(SAMPLES_PER_SUB)
+    return job.subset(np.arange(0, 1024, 32))
+
+
+def time_oracle(steps=1):
+    import oracle
+    job = cpu_sample_job()
+    lat = oracle.lattice(job.nx, job.nt)
+    cores = os.cpu_count() or 1
+    oracle.build()
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.integrate(lat, job.lo, job.hi, job.samples, job.seed, job.job_id, sub_id=job.sub_id,
+                         nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    return job.total_samples, times, cores
+
+
+def run_reference(args):
+    rank, _, world = rank_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    samples, times, cores = time_oracle(args.warmup + args.steps)
+    t = times[args.warmup:] if len(times) > args.warmup else times
+    sec = sum(t) / len(t)
+    value = samples / sec
+    sample_desc = ("32 of the 1024 subvolumes (every 32nd) x 2^20 points of the 10x2 job, "
+                   "FP64 oracle, OpenMP over subvolumes")
+    print(json.dumps({
+        "impl": "reference", "metric": "samples/s", "value": value, "unit": "samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(world),
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def workload_config(world):
+    return {"workload": "10x2 lattice (d=20), nu=D=a=tau=1, box [-5,5]^20 bisected along coords "
+                        f"0..9 into 1024 subvolumes per GPU, 2^20 Philox4x32-10 points each (seed 2), FP64",
+            "model": None, "global_batch": world * NSUB_PER_RANK * SAMPLES_PER_SUB,
+            "subvolumes_per_gpu": NSUB_PER_RANK, "samples_per_subvolume": SAMPLES_PER_SUB,
+            "parallelism": f"subvolume shards x{world}",
+            "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)"}
+
+
+def make_job(rank, world, samples_per_sub):
+    import workloads
+    k = 10 + int(round(math.log2(world)))
+    lo, hi = workloads.bisected_boxes(D, k)
+    sl = slice(rank * NSUB_PER_RANK, (rank + 1) * NSUB_PER_RANK)
+    return workloads.Job(NX, NT, lo[sl], hi[sl], np.full(NSUB_PER_RANK, samples_per_sub, dtype=np.uint64),
+                         seed=2, sub_id=np.arange(sl.start, sl.stop, dtype=np.uint32))
+
+
+def timed_steps(plan, lo, hi, sid, job, steps, warmup, flush_buf, dist, stream):
+    """Per-step CUDA events on the launch stream; the L2 flush sits between steps."""
+    import torch
+    for _ in range(warmup):
+        plan.execute(lo, hi, job.seed, job.job_id, sub_id=sid, stream=stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    total_ms, kern_ms = 0.0, 0.0
+    slots = totals = None
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush_buf.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        slots, totals = plan.execute(lo, hi, job.seed, job.job_id, sub_id=sid, stream=stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        kern_ms += plan.timing()[0]
+    plan.set_timing(False)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    return total_ms / steps, kern_ms / steps, slots, totals
+
+
+def run_bfi(args):
+    import torch
+    rank, local_rank, world = rank_info()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+        dist = tdist
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1803_07560_gb300 as bfi
+
+    stream = torch.cuda.Stream(dev)
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lat = bfi.lattice(NX, NT)
+
+    # ---- headline: FP64, 2^20 points per subvolume ----
+    job = make_job(rank, world, SAMPLES_PER_SUB)
+    lo = torch.tensor(job.lo, device=dev)
+    hi = torch.tensor(job.hi, device=dev)
+    sid = torch.tensor(job.sub_id.astype(np.int32), device=dev)
+    plan = bfi.Plan(lat, job.samples, bfi.FP64, device=local_rank)
+    info = plan.info()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    ms, kern_ms, slots, totals = timed_steps(plan, lo, hi, sid, job, args.steps, args.warmup, flush_buf,
+                                             dist, stream)
+    clocks = sampler.stop() if sampler else None
+
+    # the exchange: gather every rank's subvolume records, merge on rank 0
+    if dist is not None:
+        gathered = [torch.empty_like(slots) for _ in range(world)]
+        dist.all_gather(gathered, slots)
+        all_slots = torch.cat(gathered).cpu().numpy()
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    else:
+        all_slots = slots.cpu().numpy()
+    merged = bfi.merge_host(NX, all_slots)
+
+    samples_all = world * job.total_samples
+    value = samples_all / (ms * 1e-3)
+    kern_ops = job.total_samples * ops_per_sample_fp64(NX, NT)
+    achieved = kern_ops / (kern_ms * 1e-3)
+
+    # ---- FP32 form of the same job with 2^24 points per subvolume ----
+    fp32 = None
+    if not args.skip_fp32:
+        job32 = make_job(rank, world, FP32_SAMPLES_PER_SUB)
+        plan32 = bfi.Plan(lat, job32.samples, bfi.FP32, device=local_rank)
+        ms32, kern32, _, tot32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
+                                             max(1, args.warmup // 2), flush_buf, dist, stream)
+        ach32 = job32.total_samples * ops_per_sample_fp32(NX, NT) / (kern32 * 1e-3)
+        fp32 = {"value": world * job32.total_samples / (ms32 * 1e-3), "unit": "samples/s",
+                "ms_per_step": ms32, "samples_per_subvolume": FP32_SAMPLES_PER_SUB,
+                "dtype": "f32 (compensated sums, f64 shift and merge)",
+                "roofline": {"bound": "alu", "achieved": ach32 / 1e9, "peak": ISSUE_PEAK_OPS / 1e9,
+                             "unit": "Gop/s", "frac": ach32 / ISSUE_PEAK_OPS, "traffic": None,
+                             "kernel_ms": kern32,
+                             "ops_per_sample": ops_per_sample_fp32(NX, NT)},
+                "logZ": float(tot32[0].item())}
+        plan32.close()
+
+    # ---- end to end through the host-buffer C-ABI call ----
+    ctx = bfi.Context(local_rank)
+    lo_h = torch.empty(job.lo.shape, dtype=torch.float64, pin_memory=True).numpy()
+    hi_h = torch.empty(job.hi.shape, dtype=torch.float64, pin_memory=True).numpy()
+    lo_h[:] = job.lo
+    hi_h[:] = job.hi
+    sid_h = torch.empty(job.nsub, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    sid_h[:] = job.sub_id
+    slots_h = torch.empty((job.nsub, bfi.slot_len(NX)), dtype=torch.float64, pin_memory=True).numpy()
+    tot_h = torch.empty(bfi.totals_len(NX), dtype=torch.float64, pin_memory=True).numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    ctx.integrate(lat, lo_h, hi_h, job.samples, job.seed, 0, sub_id=sid_h, out_slots=slots_h, out_totals=tot_h)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.integrate(lat, lo_h, hi_h, job.samples, job.seed, 0, sub_id=sid_h, out_slots=slots_h,
+                      out_totals=tot_h)
+    e2e_sec = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_sec], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    ctx.close()
+    h2d = lo_h.nbytes + hi_h.nbytes + sid_h.nbytes
+    d2h = slots_h.nbytes + tot_h.nbytes
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        samples, times, cores = time_oracle(1)
+        cpu = {"value": samples / times[0], "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": "32 of the 1024 subvolumes (every 32nd) x 2^20 points of the same job, FP64 oracle"}
+
+    if rank == 0:
+        line = {
+            "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(world),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9,
+                         "unit": "Gop/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
+                         "kernel": "integrand_tps<10,2,double>", "kernel_ms": kern_ms,
+                         "ops_per_sample": ops_per_sample_fp64(NX, NT),
+                         "peak_source": "nominal FP64 1.25 TFLOP/s (FMA = 2 flops)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": samples_all / e2e_sec, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+            "plan": {"grid": info.grid, "block": info.block, "chunks": info.chunks,
+                     "chunk_samples": info.chunk_samples},
+            "result": {"logZ": float(merged[0]), "Z_err_rel": float(merged[1]),
+                       "C": [float(x) for x in merged[4:4 + R]],
+                       "C_err": [float(x) for x in merged[4 + R:4 + 2 * R]]},
+            "fp32": fp32,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bfi", choices=["bfi", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp32", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_bfi(args)
+
+
+if __name__ == "__main__":
+    main()

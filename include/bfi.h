@@ -1,0 +1,223 @@
+/*
+ * bfi.h -- C ABI of the GB300 (sm_103a) library for the Monte Carlo
+ * evaluation of the lattice Burgers functional integral of Honkonen &
+ * Honkonen, "Modelling turbulence via numerical functional integration using
+ * Burgers' equation" (arXiv:1803.07560).
+ *
+ * The library computes, for one lattice and a list of box-shaped
+ * subvolumes of the integration volume, the plain Monte Carlo estimates of
+ *
+ *   Z    = int prod dv  exp(-S[v])                    (the normaliser, Sec. 4)
+ *   N(r) = int prod dv  P_r[v] exp(-S[v])             (numerator of Eq. (Gen2))
+ *   C(r) = N(r) / Z                                   (Eq. (Gen2), C = 1/Z)
+ *
+ * with S the lattice action of Eq. (Gen2):
+ *
+ *   S = 1/(2 D tau) sum_{l,m} R_{l,m}^2,
+ *   R_{l,m} = v_{l+1,m} - v_{l,m}
+ *           + tau ( v_{l,m} (v_{l,m+1} - v_{l,m-1}) / (2a)
+ *                   - nu (v_{l,m+1} - 2 v_{l,m} + v_{l,m-1}) / a^2 ),
+ *
+ * periodic in time (l, Nt slices) and space (m, Nx sites) (Sec. 2), and
+ * P_r = (1/d) sum_{l,m} v_{l,m} v_{l,m+r} the site-averaged equal-time
+ * product at distance r = 0..floor(Nx/2), d = Nx Nt.  Subvolumes are
+ * integrated independently and summed (Sec. 1 and 3); each gets plain MC
+ * with uniform points (Sec. 3: result = V mean f, error = V sigma / sqrt n).
+ *
+ * Conventions used by every call below.
+ *
+ *  - Coordinates: coordinate j = m*Nt + l holds v(t_l, x_m).
+ *  - Points: sample i (0-based) of subvolume s draws the Philox4x32-10 block
+ *    (counter (j/4, i mod 2^32, i / 2^32, sub_id[s]), key (seed, job_id));
+ *    word j%4 of it, w, gives coordinate j:
+ *      BFI_FP64:  y = fma((w + 0.5) 2^-32, hi - lo, lo)               (double)
+ *      BFI_FP32:  y = fmaf(((w >> 9) + 0.5) 2^-23, (float)(hi - lo), (float)lo)
+ *  - Weights: w_i = exp(-(S_i - m_s)), m_s the smallest action seen in the
+ *    subvolume, so nothing underflows or overflows whatever the lattice size.
+ *  - Subvolume record ("slot"), bfi_slot_len(nx) = 5 + 3R doubles, R = nx/2+1:
+ *      [0] n_s  [1] m_s  [2] log V_s  [3] sum w  [4] sum w^2
+ *      [5 + r] sum w P_r   [5 + R + r] sum w^2 P_r   [5 + 2R + r] sum w^2 P_r^2
+ *    so that Z_s = exp(log V_s - log n_s - m_s) * sum w.
+ *  - Totals, bfi_totals_len(nx) = 4 + 2R doubles:
+ *      [0] log Z  [1] relative standard error of Z  [2] samples  [3] subvolumes
+ *      with samples  [4 + r] C(r)  [4 + R + r] standard error of C(r)
+ *    The errors are the plain-MC standard errors, combined over independent
+ *    subvolumes; the error of C(r) is the first-order (delta-method) error of
+ *    a ratio of sums.  A subvolume with exactly one sample makes the errors
+ *    +inf; subvolumes with no samples are skipped.
+ *  - Precision: BFI_FP64 evaluates everything in double.  BFI_FP32 evaluates
+ *    the points, the action, the products and the weights in float,
+ *    accumulates per thread in compensated float, and merges in double.
+ *  - Errors: every call returns a bfi_status; bfi_last_error() gives a
+ *    message for the calling thread.  No call aborts the process.
+ *  - Pointers: "host" pointers are ordinary CPU memory, "device" pointers
+ *    are CUDA device memory of the plan's or context's device.  The caller
+ *    owns every array it passes and may free it once the call returns (for
+ *    asynchronous calls: once the stream has passed the call).
+ */
+#ifndef BFI_H
+#define BFI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BFI_OK = 0,
+    BFI_E_INVALID = 1,      /* an argument is out of range or inconsistent */
+    BFI_E_NOMEM = 2,        /* a host or device allocation failed */
+    BFI_E_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+    BFI_E_TIMEOUT = 4,      /* a bounded wait ran out */
+    BFI_E_CANCELLED = 5,    /* the job was cancelled */
+    BFI_E_BUSY = 6,         /* the resource is in use */
+    BFI_E_UNSUPPORTED = 7   /* lattice shape not compiled into this library */
+} bfi_status;
+
+typedef enum { BFI_FP64 = 0, BFI_FP32 = 1 } bfi_precision;
+
+/* Lattice and parameters of Eq. (Gen2) (Sec. 2; the paper uses
+ * nu = D = a = tau = 1).  nx = M spatial sites (>= 2), nt = L time slices
+ * (>= 1), d = nx * nt <= 512.  D is the variance of the random force.
+ * Two test knobs that are not in the paper: 'nonlinear' multiplies the
+ * advection term (1 = Eq. (Gen2), 0 = linear limit) and 'mass2' (>= 0) adds
+ * mass2/2 * sum v^2 to S (0 = Eq. (Gen2)). */
+typedef struct {
+    int32_t nx;
+    int32_t nt;
+    double nu;
+    double D;
+    double a;
+    double tau;
+    double nonlinear;
+    double mass2;
+} bfi_lattice;
+
+/* Sizes of the records above. */
+int32_t bfi_num_r(int32_t nx);
+int32_t bfi_slot_len(int32_t nx);
+int32_t bfi_totals_len(int32_t nx);
+
+/* Message describing the last failed call on this thread ("" if none). */
+const char *bfi_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Plans: the device-resident hot path.                                      */
+/* ------------------------------------------------------------------------ */
+
+/* A plan fixes the lattice, the precision, the number of subvolumes and
+ * their sample budgets (Sec. 3: "number of samples and the extent of the
+ * integration volume"), and owns the device scratch the integration needs
+ * (chunk table, per-chunk partial records).  Creating it allocates device
+ * memory on 'device' and may take milliseconds; executing it allocates
+ * nothing.  samples: host [nsub], per-subvolume budgets (0 allowed).
+ * Errors: BFI_E_INVALID (bad lattice, nsub < 1, d > 512, a budget >= 2^48),
+ * BFI_E_UNSUPPORTED, BFI_E_NOMEM, BFI_E_CUDA. */
+typedef struct bfi_plan bfi_plan;
+
+bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t nsub,
+                           const uint64_t *samples, bfi_precision precision, int device);
+bfi_status bfi_plan_destroy(bfi_plan *plan);
+
+typedef struct {
+    int64_t nsub;
+    int64_t chunks;            /* work units of one execution */
+    int64_t chunk_samples;     /* samples per chunk (the last chunk of a subvolume is ragged) */
+    int64_t total_samples;
+    int32_t grid;              /* CTAs of the integrand kernel */
+    int32_t block;             /* threads per CTA */
+    int32_t kernel;            /* 0 = thread-per-sample (compiled shape), 1 = warp-per-sample */
+    int32_t slot_len;
+    int32_t totals_len;
+    size_t scratch_bytes;      /* device scratch owned by the plan */
+} bfi_plan_info;
+
+bfi_status bfi_plan_get_info(const bfi_plan *plan, bfi_plan_info *info);
+
+/* Run the whole hot path on 'stream' (a cudaStream_t; NULL = legacy default
+ * stream): points, action, weights, products, per-subvolume reduction and
+ * the FP64 merge.  Asynchronous: returns after enqueueing.
+ *   lo, hi  device [nsub * d]  subvolume bounds (row s, coordinate j); lo < hi
+ *   sub_id  device [nsub] or NULL (then sub_id[s] = s): Philox counter word 3
+ *   seed, job_id               Philox key
+ *   slots   device [nsub * bfi_slot_len(nx)]   out
+ *   totals  device [bfi_totals_len(nx)]        out
+ * Bounds are not validated on the device; lo >= hi gives undefined numbers
+ * (never an out-of-range access).  Errors: BFI_E_INVALID (NULL pointers),
+ * BFI_E_CUDA (launch failure). */
+bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi,
+                            const uint32_t *sub_id, uint32_t seed, uint32_t job_id,
+                            double *slots, double *totals, void *stream);
+
+/* Per-stage timing of bfi_plan_execute with CUDA events recorded on the
+ * execution stream.  After bfi_plan_set_timing(plan, 1), each execution
+ * records events around its integrand kernel and around its merge kernels;
+ * bfi_plan_get_timing waits for the last execution's events and writes
+ * ms[0] = integrand kernel, ms[1] = merges (milliseconds).  Off by default.
+ * Errors: BFI_E_INVALID (NULL, or no timed execution yet), BFI_E_CUDA. */
+bfi_status bfi_plan_set_timing(bfi_plan *plan, int enable);
+bfi_status bfi_plan_get_timing(bfi_plan *plan, float *ms);
+
+/* ------------------------------------------------------------------------ */
+/* One-call integration with host buffers (the end-to-end path).            */
+/* ------------------------------------------------------------------------ */
+
+/* A context binds a device and a CUDA stream it creates, and caches the plan
+ * and device buffers of the last job shape it ran.  A context is used by one
+ * thread at a time; a concurrent call returns BFI_E_BUSY.
+ * Errors: BFI_E_INVALID, BFI_E_NOMEM, BFI_E_CUDA. */
+typedef struct bfi_ctx bfi_ctx;
+
+bfi_status bfi_ctx_create(bfi_ctx **out, int device);
+bfi_status bfi_ctx_destroy(bfi_ctx *ctx);
+
+/* Integrate one job with host inputs and outputs: copies the bounds in, runs
+ * the plan (re-planned only when the lattice, precision or budgets change),
+ * copies the results out and waits for them.
+ *   lo, hi   host [nsub * d]     samples host [nsub]     sub_id host [nsub] or NULL
+ *   slots    host [nsub * slot_len] or NULL (then not copied back)
+ *   totals   host [totals_len]
+ * Page-locked host buffers make the copies asynchronous with respect to other
+ * host work; pageable ones work too.
+ * Errors: as bfi_plan_create and bfi_plan_execute, BFI_E_BUSY. */
+bfi_status bfi_integrate(bfi_ctx *ctx, const bfi_lattice *lattice, int64_t nsub, const double *lo,
+                         const double *hi, const uint64_t *samples, const uint32_t *sub_id,
+                         uint32_t seed, uint32_t job_id, bfi_precision precision,
+                         double *slots, double *totals);
+
+/* ------------------------------------------------------------------------ */
+/* FP64 merge of subvolume records on the host.                             */
+/* ------------------------------------------------------------------------ */
+
+/* Merge nsub slots (host, [nsub * slot_len]) into totals (host) with the
+ * same definitions as the device merge; used to combine records produced by
+ * several executions, devices or processes (Sec. 1: the integral over a
+ * region is the sum of the integrals over its parts).  Errors: BFI_E_INVALID. */
+bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double *totals);
+
+/* ------------------------------------------------------------------------ */
+/* Single steps of the path, for step-by-step checks.                        */
+/* ------------------------------------------------------------------------ */
+
+/* Coordinates of samples [first, first + count) of one subvolume (step 1 of
+ * the path), widened to double.  lo, hi: device [d]; y: device [count * d].
+ * Synchronous on 'stream'.  Errors: BFI_E_INVALID, BFI_E_CUDA. */
+bfi_status bfi_points(int32_t d, const double *lo, const double *hi, uint32_t sub_id,
+                      uint32_t seed, uint32_t job_id, uint64_t first, int64_t count,
+                      bfi_precision precision, double *y, void *stream);
+
+/* Action S and products P_r at given points (steps 2 and 4), evaluated by
+ * the same device code as the integrand in the given precision (BFI_FP32
+ * rounds y to float first).  y: device [npts * d]; S: device [npts];
+ * P: device [npts * R].  Synchronous on 'stream'.
+ * Errors: BFI_E_INVALID, BFI_E_UNSUPPORTED, BFI_E_CUDA. */
+bfi_status bfi_eval(const bfi_lattice *lattice, int64_t npts, const double *y,
+                    bfi_precision precision, double *S, double *P, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFI_H */

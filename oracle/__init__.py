@@ -11,13 +11,14 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB = os.path.join(_HERE, "_build", platform.machine(), "liboracle.so")  # per host architecture
 _lib = None
 
 

@@ -1,0 +1,255 @@
+"""GB300 (sm_103a) Monte Carlo evaluation of the lattice Burgers functional
+integral of Honkonen & Honkonen (arXiv:1803.07560).
+
+Thin ctypes binding of the C ABI in ``include/bfi.h``: argument marshalling
+only; every step of the computation runs in the CUDA library
+``_build/libbfi.so``.  There is no CPU fallback: importing this package fails
+if the library has not been built (``paper_1803_07560_gb300._build.build()``).
+Device arrays are torch CUDA tensors (torch supplies device memory and
+streams); host arrays are numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+FP64 = 0
+FP32 = 1
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+
+
+class BfiError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"bfi status {status}: {message}")
+        self.status = status
+
+
+class Lattice(ctypes.Structure):
+    """Lattice of Eq. (Gen2): nx spatial sites (M), nt time slices (L)."""
+
+    _fields_ = [("nx", ctypes.c_int32), ("nt", ctypes.c_int32), ("nu", ctypes.c_double),
+                ("D", ctypes.c_double), ("a", ctypes.c_double), ("tau", ctypes.c_double),
+                ("nonlinear", ctypes.c_double), ("mass2", ctypes.c_double)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("nsub", ctypes.c_int64), ("chunks", ctypes.c_int64),
+                ("chunk_samples", ctypes.c_int64), ("total_samples", ctypes.c_int64),
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("slot_len", ctypes.c_int32), ("totals_len", ctypes.c_int32),
+                ("scratch_bytes", ctypes.c_size_t)]
+
+
+def lattice(nx, nt, nu=1.0, D=1.0, a=1.0, tau=1.0, nonlinear=1.0, mass2=0.0) -> Lattice:
+    return Lattice(nx, nt, nu, D, a, tau, nonlinear, mass2)
+
+
+# Every symbol the header declares, with its ctypes signature.
+_SIGNATURES = {
+    "bfi_num_r": (ctypes.c_int32, [ctypes.c_int32]),
+    "bfi_slot_len": (ctypes.c_int32, [ctypes.c_int32]),
+    "bfi_totals_len": (ctypes.c_int32, [ctypes.c_int32]),
+    "bfi_last_error": (ctypes.c_char_p, []),
+    "bfi_plan_create": (ctypes.c_int, [_P(_vp), _P(Lattice), ctypes.c_int64, _P(ctypes.c_uint64),
+                                       ctypes.c_int, ctypes.c_int]),
+    "bfi_plan_destroy": (ctypes.c_int, [_vp]),
+    "bfi_plan_get_info": (ctypes.c_int, [_vp, _P(PlanInfo)]),
+    "bfi_plan_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32,
+                                        _vp, _vp, _vp]),
+    "bfi_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "bfi_plan_get_timing": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
+    "bfi_ctx_create": (ctypes.c_int, [_P(_vp), ctypes.c_int]),
+    "bfi_ctx_destroy": (ctypes.c_int, [_vp]),
+    "bfi_integrate": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, _vp,
+                                     ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _vp, _vp]),
+    "bfi_merge_host": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp]),
+    "bfi_points": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32,
+                                  ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
+                                  _vp, _vp]),
+    "bfi_eval": (ctypes.c_int, [_P(Lattice), ctypes.c_int64, _vp, ctypes.c_int, _vp, _vp, _vp]),
+}
+
+
+def _load_library():
+    if not os.path.exists(_build.LIB):
+        raise ImportError(
+            f"CUDA library not built: {_build.LIB} is missing "
+            "(build it with paper_1803_07560_gb300._build.build())")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load_library()
+LIBRARY_PATH = _build.LIB
+
+
+def _check(status: int):
+    if status != 0:
+        raise BfiError(status, _lib.bfi_last_error().decode())
+
+
+def num_r(nx: int) -> int:
+    return _lib.bfi_num_r(nx)
+
+
+def slot_len(nx: int) -> int:
+    return _lib.bfi_slot_len(nx)
+
+
+def totals_len(nx: int) -> int:
+    return _lib.bfi_totals_len(nx)
+
+
+def _dev_ptr(t, dtype=None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+class Plan:
+    """A planned job (lattice, precision, per-subvolume budgets) on one device."""
+
+    def __init__(self, lat: Lattice, samples, precision: int = FP64, device: int = 0):
+        smp = np.ascontiguousarray(np.atleast_1d(samples), dtype=np.uint64)
+        self.lattice = lat
+        self.precision = precision
+        self.device = device
+        self.nsub = int(smp.size)
+        handle = ctypes.c_void_p()
+        _check(_lib.bfi_plan_create(ctypes.byref(handle), ctypes.byref(lat), smp.size,
+                                    smp.ctypes.data_as(_P(ctypes.c_uint64)), precision, device))
+        self._h = handle
+
+    def info(self) -> PlanInfo:
+        info = PlanInfo()
+        _check(_lib.bfi_plan_get_info(self._h, ctypes.byref(info)))
+        return info
+
+    def execute(self, lo, hi, seed: int, job_id: int = 0, sub_id=None, slots=None, totals=None,
+                stream=None):
+        """Enqueue the whole path on 'stream'; lo/hi [nsub, d] float64 CUDA tensors."""
+        import torch
+        nx = self.lattice.nx
+        if slots is None:
+            slots = torch.empty((self.nsub, slot_len(nx)), dtype=torch.float64, device=lo.device)
+        if totals is None:
+            totals = torch.empty(totals_len(nx), dtype=torch.float64, device=lo.device)
+        _check(_lib.bfi_plan_execute(self._h, _dev_ptr(lo, torch.float64), _dev_ptr(hi, torch.float64),
+                                     _dev_ptr(sub_id, torch.int32) if sub_id is not None else None,
+                                     seed & 0xFFFFFFFF, job_id & 0xFFFFFFFF,
+                                     _dev_ptr(slots, torch.float64), _dev_ptr(totals, torch.float64),
+                                     _stream_ptr(stream)))
+        return slots, totals
+
+    def set_timing(self, enable: bool = True):
+        _check(_lib.bfi_plan_set_timing(self._h, int(enable)))
+
+    def timing(self):
+        """(integrand ms, merge ms) of the last timed execution (waits for it)."""
+        ms = (ctypes.c_float * 2)()
+        _check(_lib.bfi_plan_get_timing(self._h, ms))
+        return float(ms[0]), float(ms[1])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.bfi_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """One device and stream; integrate() takes and returns host arrays."""
+
+    def __init__(self, device: int = 0):
+        handle = ctypes.c_void_p()
+        _check(_lib.bfi_ctx_create(ctypes.byref(handle), device))
+        self._h = handle
+        self.device = device
+
+    def integrate(self, lat: Lattice, lo, hi, samples, seed: int, job_id: int = 0, sub_id=None,
+                  precision: int = FP64, want_slots: bool = True, out_slots=None, out_totals=None):
+        d = lat.nx * lat.nt
+        lo_a, lo_p = _host(np.reshape(lo, (-1, d)), np.float64)
+        hi_a, hi_p = _host(np.reshape(hi, (-1, d)), np.float64)
+        nsub = lo_a.shape[0]
+        smp_a, smp_p = _host(np.broadcast_to(np.asarray(samples, dtype=np.uint64), (nsub,)), np.uint64)
+        sid_a, sid_p = (None, None) if sub_id is None else _host(sub_id, np.uint32)
+        slots = out_slots if out_slots is not None else (
+            np.empty((nsub, slot_len(lat.nx))) if want_slots else None)
+        totals = out_totals if out_totals is not None else np.empty(totals_len(lat.nx))
+        _check(_lib.bfi_integrate(self._h, ctypes.byref(lat), nsub, lo_p, hi_p, smp_p, sid_p,
+                                  seed & 0xFFFFFFFF, job_id & 0xFFFFFFFF, precision,
+                                  None if slots is None else ctypes.c_void_p(slots.ctypes.data),
+                                  ctypes.c_void_p(totals.ctypes.data)))
+        return slots, totals
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.bfi_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def merge_host(nx: int, slots) -> np.ndarray:
+    """FP64 merge of subvolume records on the host (the library's own merge)."""
+    s_a, s_p = _host(np.reshape(slots, (-1, slot_len(nx))), np.float64)
+    out = np.empty(totals_len(nx))
+    _check(_lib.bfi_merge_host(nx, s_a.shape[0], s_p, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def points(d, lo, hi, sub_id, seed, job_id, first, count, precision=FP64, stream=None):
+    """Coordinates of samples [first, first+count) of one subvolume (CUDA tensors)."""
+    import torch
+    y = torch.empty((count, d), dtype=torch.float64, device=lo.device)
+    _check(_lib.bfi_points(d, _dev_ptr(lo, torch.float64), _dev_ptr(hi, torch.float64), sub_id,
+                           seed, job_id, first, count, precision, _dev_ptr(y), _stream_ptr(stream)))
+    return y
+
+
+def evaluate(lat: Lattice, y, precision=FP64, stream=None):
+    """Action S and products P_r at points y [npts, d] (CUDA float64 tensor)."""
+    import torch
+    n = y.shape[0]
+    S = torch.empty(n, dtype=torch.float64, device=y.device)
+    P = torch.empty((n, num_r(lat.nx)), dtype=torch.float64, device=y.device)
+    _check(_lib.bfi_eval(ctypes.byref(lat), n, _dev_ptr(y, torch.float64), precision, _dev_ptr(S),
+                         _dev_ptr(P), _stream_ptr(stream)))
+    return S, P

@@ -1,0 +1,473 @@
+// api.cu -- the C ABI declared in include/bfi.h: argument checks, plans
+// (chunking of the sample budgets and the device scratch), the one-call
+// host-buffer path, the host FP64 merge and the single-step entry points.
+#include "bfi.h"
+#include "bfi_device.cuh"
+#include "bfi_kernels.h"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bfi_status fail(bfi_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define BFI_CUDA(expr)                                                                                   \
+    do {                                                                                                 \
+        cudaError_t e_ = (expr);                                                                         \
+        if (e_ != cudaSuccess) return fail(BFI_E_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Makes 'device' current for the scope and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int device) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != device) err = cudaSetDevice(device);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+bfi_status check_lattice(const bfi_lattice *L) {
+    if (!L) return fail(BFI_E_INVALID, "lattice is NULL");
+    if (L->nx < 2 || L->nt < 1) return fail(BFI_E_INVALID, "lattice %dx%d: need nx >= 2, nt >= 1", L->nx, L->nt);
+    if (static_cast<int64_t>(L->nx) * L->nt > bfi::kMaxD)
+        return fail(BFI_E_INVALID, "lattice %dx%d: d = nx*nt must be <= %d", L->nx, L->nt, bfi::kMaxD);
+    if (!finite_pos(L->D) || !finite_pos(L->a) || !finite_pos(L->tau))
+        return fail(BFI_E_INVALID, "D, a and tau must be finite and > 0");
+    if (!std::isfinite(L->nu) || L->nu < 0.0) return fail(BFI_E_INVALID, "nu must be finite and >= 0");
+    if (!std::isfinite(L->nonlinear)) return fail(BFI_E_INVALID, "nonlinear must be finite");
+    if (!std::isfinite(L->mass2) || L->mass2 < 0.0) return fail(BFI_E_INVALID, "mass2 must be finite and >= 0");
+    return BFI_OK;
+}
+
+bfi::LatticeParams to_params(const bfi_lattice *L) {
+    return bfi::LatticeParams{L->nx, L->nt, L->nu, L->D, L->a, L->tau, L->nonlinear, L->mass2};
+}
+
+int num_r(int nx) { return nx / 2 + 1; }
+
+// Samples per chunk: a multiple of the block size, chosen from the job alone
+// (never from the device or from other jobs) so that a job's rounding is the
+// same wherever and with whatever else it runs.
+int64_t choose_chunk_samples(uint64_t total) {
+    uint64_t per_thread = total / (static_cast<uint64_t>(bfi::kBlock) * 2048u);
+    uint64_t spt = 4;
+    while (spt * 2 <= per_thread && spt < 256) spt *= 2;
+    return static_cast<int64_t>(spt) * bfi::kBlock;
+}
+
+}  // namespace
+
+struct bfi_plan {
+    int device = 0;
+    bfi::LatticeParams lat{};
+    bfi_precision precision = BFI_FP64;
+    const bfi::ShapeKernels *shape = nullptr;
+    int64_t nsub = 0, nchunks = 0, chunk_samples = 0, total = 0;
+    int grid = 1;
+    int R = 0, K = 0, d = 0;
+    std::vector<uint64_t> samples;
+    int64_t *d_chunk_off = nullptr;
+    uint64_t *d_samples = nullptr;
+    double *d_partials = nullptr;
+    size_t scratch_bytes = 0;
+    bool timing = false, timed = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+extern "C" {
+
+int32_t bfi_num_r(int32_t nx) { return nx / 2 + 1; }
+int32_t bfi_slot_len(int32_t nx) { return 5 + 3 * (nx / 2 + 1); }
+int32_t bfi_totals_len(int32_t nx) { return 4 + 2 * (nx / 2 + 1); }
+const char *bfi_last_error(void) { return g_last_error.c_str(); }
+
+bfi_status bfi_plan_destroy(bfi_plan *plan) {
+    if (!plan) return BFI_OK;
+    {
+        DeviceGuard g(plan->device);
+        cudaFree(plan->d_chunk_off);
+        cudaFree(plan->d_samples);
+        cudaFree(plan->d_partials);
+        for (auto &e : plan->ev)
+            if (e) cudaEventDestroy(e);
+    }
+    delete plan;
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t nsub, const uint64_t *samples,
+                           bfi_precision precision, int device) {
+    if (!out) return fail(BFI_E_INVALID, "out is NULL");
+    *out = nullptr;
+    bfi_status st = check_lattice(lattice);
+    if (st != BFI_OK) return st;
+    if (nsub < 1) return fail(BFI_E_INVALID, "nsub must be >= 1 (got %lld)", static_cast<long long>(nsub));
+    if (!samples) return fail(BFI_E_INVALID, "samples is NULL");
+    if (precision != BFI_FP64 && precision != BFI_FP32) return fail(BFI_E_INVALID, "unknown precision %d", precision);
+    const bfi::ShapeKernels *shape = bfi::find_shape(lattice->nx, lattice->nt);
+    if (!shape)
+        return fail(BFI_E_UNSUPPORTED, "lattice %dx%d has no compiled kernel in this library", lattice->nx,
+                    lattice->nt);
+    uint64_t total = 0;
+    for (int64_t s = 0; s < nsub; ++s) {
+        if (samples[s] >= (1ull << 48))
+            return fail(BFI_E_INVALID, "samples[%lld] = %llu must be < 2^48", static_cast<long long>(s),
+                        static_cast<unsigned long long>(samples[s]));
+        total += samples[s];
+    }
+    if (total >= (1ull << 62)) return fail(BFI_E_INVALID, "total sample budget too large");
+
+    DeviceGuard g(device);
+    if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device %d: %s", device, cudaGetErrorString(g.err));
+
+    bfi_plan *p = new (std::nothrow) bfi_plan();
+    if (!p) return fail(BFI_E_NOMEM, "host allocation failed");
+    p->device = device;
+    p->lat = to_params(lattice);
+    p->precision = precision;
+    p->shape = shape;
+    p->nsub = nsub;
+    p->R = num_r(lattice->nx);
+    p->K = bfi::sum_count(p->R);
+    p->d = lattice->nx * lattice->nt;
+    p->total = static_cast<int64_t>(total);
+    p->samples.assign(samples, samples + nsub);
+    p->chunk_samples = choose_chunk_samples(total);
+    std::vector<int64_t> off(nsub + 1, 0);
+    for (int64_t s = 0; s < nsub; ++s)
+        off[s + 1] = off[s] + static_cast<int64_t>((samples[s] + p->chunk_samples - 1) / p->chunk_samples);
+    p->nchunks = off[nsub];
+
+    int sms = 0, per_sm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = shape->occupancy[precision](&per_sm);
+    if (e != cudaSuccess) {
+        delete p;
+        return fail(BFI_E_CUDA, "device query failed: %s", cudaGetErrorString(e));
+    }
+    const int64_t resident = static_cast<int64_t>(sms) * (per_sm > 0 ? per_sm : 1);
+    p->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(p->nchunks, resident)));
+
+    const size_t off_bytes = sizeof(int64_t) * (nsub + 1);
+    const size_t smp_bytes = sizeof(uint64_t) * nsub;
+    const size_t par_bytes = sizeof(double) * static_cast<size_t>(std::max<int64_t>(p->nchunks, 1)) * (p->K + 2);
+    p->scratch_bytes = off_bytes + smp_bytes + par_bytes;
+    if (cudaMalloc(&p->d_chunk_off, off_bytes) != cudaSuccess || cudaMalloc(&p->d_samples, smp_bytes) != cudaSuccess ||
+        cudaMalloc(&p->d_partials, par_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        bfi_plan_destroy(p);
+        return fail(BFI_E_NOMEM, "device allocation of %zu bytes failed", p->scratch_bytes);
+    }
+    e = cudaMemcpy(p->d_chunk_off, off.data(), off_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_samples, samples, smp_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        bfi_plan_destroy(p);
+        return fail(BFI_E_CUDA, "copy of the chunk table failed: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_get_info(const bfi_plan *plan, bfi_plan_info *info) {
+    if (!plan || !info) return fail(BFI_E_INVALID, "plan or info is NULL");
+    info->nsub = plan->nsub;
+    info->chunks = plan->nchunks;
+    info->chunk_samples = plan->chunk_samples;
+    info->total_samples = plan->total;
+    info->grid = plan->grid;
+    info->block = bfi::kBlock;
+    info->kernel = 0;
+    info->slot_len = 5 + 3 * plan->R;
+    info->totals_len = 4 + 2 * plan->R;
+    info->scratch_bytes = plan->scratch_bytes;
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, const uint32_t *sub_id, uint32_t seed,
+                            uint32_t job_id, double *slots, double *totals, void *stream) {
+    if (!plan) return fail(BFI_E_INVALID, "plan is NULL");
+    if (!lo || !hi || !slots || !totals) return fail(BFI_E_INVALID, "lo, hi, slots and totals must be non-NULL");
+    DeviceGuard g(plan->device);
+    if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device: %s", cudaGetErrorString(g.err));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[0], st));
+    if (plan->nchunks > 0) {
+        bfi::IntegrandArgs a{lo, hi, sub_id, plan->d_samples, plan->d_chunk_off, plan->d_partials,
+                             plan->nsub, plan->nchunks, plan->chunk_samples};
+        BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
+    }
+    if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[1], st));
+    bfi::MergeArgs m{lo, hi, plan->d_chunk_off, plan->d_partials, slots, plan->nsub, plan->R, plan->d};
+    bfi::TotalsArgs t{slots, totals, plan->nsub, plan->R};
+    BFI_CUDA(bfi::launch_merges(m, t, st));
+    if (plan->timing) {
+        BFI_CUDA(cudaEventRecord(plan->ev[2], st));
+        plan->timed = true;
+    }
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_set_timing(bfi_plan *plan, int enable) {
+    if (!plan) return fail(BFI_E_INVALID, "plan is NULL");
+    DeviceGuard g(plan->device);
+    if (enable && !plan->ev[0])
+        for (auto &e : plan->ev) BFI_CUDA(cudaEventCreate(&e));
+    plan->timing = enable != 0;
+    plan->timed = false;
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_get_timing(bfi_plan *plan, float *ms) {
+    if (!plan || !ms) return fail(BFI_E_INVALID, "plan or ms is NULL");
+    if (!plan->timed) return fail(BFI_E_INVALID, "no timed execution yet");
+    DeviceGuard g(plan->device);
+    BFI_CUDA(cudaEventSynchronize(plan->ev[2]));
+    BFI_CUDA(cudaEventElapsedTime(&ms[0], plan->ev[0], plan->ev[1]));
+    BFI_CUDA(cudaEventElapsedTime(&ms[1], plan->ev[1], plan->ev[2]));
+    return BFI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Context: one device, one stream, a cached plan and device buffers.
+// ---------------------------------------------------------------------------
+struct bfi_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::atomic<bool> busy{false};
+    bfi_plan *plan = nullptr;
+    bfi_lattice lat{};
+    bfi_precision precision = BFI_FP64;
+    double *d_lo = nullptr, *d_hi = nullptr, *d_slots = nullptr, *d_totals = nullptr;
+    uint32_t *d_sid = nullptr;
+    size_t cap_lo = 0, cap_hi = 0, cap_sid = 0, cap_slots = 0, cap_totals = 0;
+};
+
+namespace {
+
+bool same_lattice(const bfi_lattice &a, const bfi_lattice &b) { return std::memcmp(&a, &b, sizeof a) == 0; }
+
+template <typename T>
+bfi_status grow(T *&ptr, size_t &cap, size_t need) {
+    if (need <= cap) return BFI_OK;
+    cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    if (cudaMalloc(&ptr, need * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BFI_E_NOMEM, "device allocation of %zu bytes failed", need * sizeof(T));
+    }
+    cap = need;
+    return BFI_OK;
+}
+
+struct BusyGuard {
+    std::atomic<bool> &flag;
+    bool ok;
+    explicit BusyGuard(std::atomic<bool> &f) : flag(f) {
+        bool expected = false;
+        ok = flag.compare_exchange_strong(expected, true);
+    }
+    ~BusyGuard() {
+        if (ok) flag.store(false);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+bfi_status bfi_ctx_create(bfi_ctx **out, int device) {
+    if (!out) return fail(BFI_E_INVALID, "out is NULL");
+    *out = nullptr;
+    DeviceGuard g(device);
+    if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device %d: %s", device, cudaGetErrorString(g.err));
+    bfi_ctx *c = new (std::nothrow) bfi_ctx();
+    if (!c) return fail(BFI_E_NOMEM, "host allocation failed");
+    c->device = device;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(BFI_E_CUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return BFI_OK;
+}
+
+bfi_status bfi_ctx_destroy(bfi_ctx *ctx) {
+    if (!ctx) return BFI_OK;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        bfi_plan_destroy(ctx->plan);
+        cudaFree(ctx->d_lo);
+        cudaFree(ctx->d_hi);
+        cudaFree(ctx->d_sid);
+        cudaFree(ctx->d_slots);
+        cudaFree(ctx->d_totals);
+        cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+    return BFI_OK;
+}
+
+bfi_status bfi_integrate(bfi_ctx *ctx, const bfi_lattice *lattice, int64_t nsub, const double *lo, const double *hi,
+                         const uint64_t *samples, const uint32_t *sub_id, uint32_t seed, uint32_t job_id,
+                         bfi_precision precision, double *slots, double *totals) {
+    if (!ctx) return fail(BFI_E_INVALID, "ctx is NULL");
+    BusyGuard busy(ctx->busy);
+    if (!busy.ok) return fail(BFI_E_BUSY, "context is in use by another thread");
+    bfi_status st = check_lattice(lattice);
+    if (st != BFI_OK) return st;
+    if (!lo || !hi || !samples || !totals) return fail(BFI_E_INVALID, "lo, hi, samples and totals must be non-NULL");
+    if (nsub < 1) return fail(BFI_E_INVALID, "nsub must be >= 1");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device: %s", cudaGetErrorString(g.err));
+
+    bool replan = !ctx->plan || !same_lattice(ctx->lat, *lattice) || ctx->precision != precision ||
+                  ctx->plan->nsub != nsub ||
+                  std::memcmp(ctx->plan->samples.data(), samples, sizeof(uint64_t) * nsub) != 0;
+    if (replan) {
+        bfi_plan_destroy(ctx->plan);
+        ctx->plan = nullptr;
+        st = bfi_plan_create(&ctx->plan, lattice, nsub, samples, precision, ctx->device);
+        if (st != BFI_OK) return st;
+        ctx->lat = *lattice;
+        ctx->precision = precision;
+    }
+    const int d = lattice->nx * lattice->nt;
+    const size_t nbox = static_cast<size_t>(nsub) * d;
+    const size_t nslot = static_cast<size_t>(nsub) * bfi_slot_len(lattice->nx);
+    if ((st = grow(ctx->d_lo, ctx->cap_lo, nbox)) != BFI_OK) return st;
+    if ((st = grow(ctx->d_hi, ctx->cap_hi, nbox)) != BFI_OK) return st;
+    if (sub_id && (st = grow(ctx->d_sid, ctx->cap_sid, static_cast<size_t>(nsub))) != BFI_OK) return st;
+    if ((st = grow(ctx->d_slots, ctx->cap_slots, nslot)) != BFI_OK) return st;
+    if ((st = grow(ctx->d_totals, ctx->cap_totals, static_cast<size_t>(bfi_totals_len(lattice->nx)))) != BFI_OK)
+        return st;
+
+    cudaStream_t s = ctx->stream;
+    BFI_CUDA(cudaMemcpyAsync(ctx->d_lo, lo, nbox * sizeof(double), cudaMemcpyHostToDevice, s));
+    BFI_CUDA(cudaMemcpyAsync(ctx->d_hi, hi, nbox * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (sub_id) BFI_CUDA(cudaMemcpyAsync(ctx->d_sid, sub_id, nsub * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    st = bfi_plan_execute(ctx->plan, ctx->d_lo, ctx->d_hi, sub_id ? ctx->d_sid : nullptr, seed, job_id, ctx->d_slots,
+                          ctx->d_totals, s);
+    if (st != BFI_OK) return st;
+    if (slots) BFI_CUDA(cudaMemcpyAsync(slots, ctx->d_slots, nslot * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BFI_CUDA(cudaMemcpyAsync(totals, ctx->d_totals, bfi_totals_len(lattice->nx) * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    BFI_CUDA(cudaStreamSynchronize(s));
+    return BFI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host FP64 merge: the same definitions as the device merge (merge_totals).
+// ---------------------------------------------------------------------------
+bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double *totals) {
+    if (nx < 2 || nsub < 0 || !slots || !totals) return fail(BFI_E_INVALID, "bad arguments to bfi_merge_host");
+    const int R = num_r(nx), SL = 5 + 3 * R;
+    auto usable = [&](const double *q) { return q[0] > 0.0 && q[3] > 0.0; };
+    double L = -INFINITY, n_tot = 0.0, used = 0.0;
+    bool inf_err = false;
+    for (int64_t s = 0; s < nsub; ++s) {
+        const double *q = slots + s * SL;
+        if (q[0] <= 0.0) continue;
+        n_tot += q[0];
+        used += 1.0;
+        if (q[3] > 0.0) L = std::fmax(L, q[2] - std::log(q[0]) - q[1]);
+    }
+    std::vector<double> f(static_cast<size_t>(nsub), 0.0);
+    double Z = 0.0, VZ = 0.0;
+    for (int64_t s = 0; s < nsub; ++s) {
+        const double *q = slots + s * SL;
+        if (!usable(q)) continue;
+        const double n = q[0];
+        f[s] = std::exp(q[2] - std::log(n) - q[1] - L);
+        Z += f[s] * q[3];
+        if (n < 2.0) {
+            inf_err = true;
+            continue;
+        }
+        VZ += f[s] * f[s] * (n * q[4] - q[3] * q[3]) / (n - 1.0);
+    }
+    totals[0] = L + std::log(Z);
+    totals[1] = inf_err ? INFINITY : std::sqrt(VZ) / Z;
+    totals[2] = n_tot;
+    totals[3] = used;
+    for (int r = 0; r < R; ++r) {
+        double N = 0.0;
+        for (int64_t s = 0; s < nsub; ++s)
+            if (usable(slots + s * SL)) N += f[s] * slots[s * SL + 5 + r];
+        const double C = N / Z;
+        double V = 0.0;
+        for (int64_t s = 0; s < nsub; ++s) {
+            const double *q = slots + s * SL;
+            if (!usable(q) || q[0] < 2.0) continue;
+            const double n = q[0];
+            const double vN = (n * q[5 + 2 * R + r] - q[5 + r] * q[5 + r]) / (n - 1.0);
+            const double cov = (n * q[5 + R + r] - q[3] * q[5 + r]) / (n - 1.0);
+            const double vZ = (n * q[4] - q[3] * q[3]) / (n - 1.0);
+            V += f[s] * f[s] * (vN - 2.0 * C * cov + C * C * vZ);
+        }
+        totals[4 + r] = C;
+        totals[4 + R + r] = inf_err ? INFINITY : std::sqrt(V > 0.0 ? V : 0.0) / Z;
+    }
+    return BFI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Single steps.
+// ---------------------------------------------------------------------------
+bfi_status bfi_points(int32_t d, const double *lo, const double *hi, uint32_t sub_id, uint32_t seed, uint32_t job_id,
+                      uint64_t first, int64_t count, bfi_precision precision, double *y, void *stream) {
+    if (d < 1 || d > bfi::kMaxD || count < 0 || !lo || !hi || (count > 0 && !y))
+        return fail(BFI_E_INVALID, "bad arguments to bfi_points");
+    if (precision != BFI_FP64 && precision != BFI_FP32) return fail(BFI_E_INVALID, "unknown precision");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bfi::PointsArgs a{lo, hi, y, first, count, d, sub_id};
+    BFI_CUDA(bfi::launch_points(a, precision == BFI_FP32, seed, job_id, st));
+    BFI_CUDA(cudaStreamSynchronize(st));
+    return BFI_OK;
+}
+
+bfi_status bfi_eval(const bfi_lattice *lattice, int64_t npts, const double *y, bfi_precision precision, double *S,
+                    double *P, void *stream) {
+    bfi_status st = check_lattice(lattice);
+    if (st != BFI_OK) return st;
+    if (npts < 0 || (npts > 0 && (!y || !S || !P))) return fail(BFI_E_INVALID, "bad arguments to bfi_eval");
+    if (precision != BFI_FP64 && precision != BFI_FP32) return fail(BFI_E_INVALID, "unknown precision");
+    const bfi::ShapeKernels *shape = bfi::find_shape(lattice->nx, lattice->nt);
+    if (!shape)
+        return fail(BFI_E_UNSUPPORTED, "lattice %dx%d has no compiled kernel in this library", lattice->nx,
+                    lattice->nt);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    bfi::EvalArgs a{y, S, P, npts};
+    BFI_CUDA(shape->eval[precision](a, to_params(lattice), cs));
+    BFI_CUDA(cudaStreamSynchronize(cs));
+    return BFI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+// bfi_device.cuh -- device building blocks of the lattice Burgers integrand
+// (Honkonen & Honkonen, arXiv:1803.07560): the Philox4x32-10 point generator,
+// the uniform-to-box map, the action of Eq. (Gen2), the equal-time products,
+// per-thread shifted accumulators and the merge of shifted records.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bfi {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).  The per-round keys are
+// precomputed once per job (key + r * Weyl constant) and passed in the kernel
+// parameters, so the XOR with the key reads the constant bank.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+struct RoundKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+inline RoundKeys make_round_keys(uint32_t seed, uint32_t job_id) {
+    RoundKeys rk;
+    uint32_t a = seed, b = job_id;
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = a;
+        rk.k1[r] = b;
+        a += kPhiloxW0;
+        b += kPhiloxW1;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t lo1 = kPhiloxM1 * c.z;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Uniform (0,1) from one 32-bit word, built from the exponent bits so that no
+// integer-to-float conversion is issued:
+//   float:  1 + (w>>9) 2^-23 in [1,2), minus (1 - 2^-24)  =  ((w>>9) + 0.5) 2^-23
+//   double: 1 + w 2^-32 in [1,2),      minus (1 - 2^-33)  =  (w + 0.5) 2^-32
+// Both subtractions are exact (the results have 24 and 33 significant bits).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float unit_f32(uint32_t w) {
+    return __uint_as_float(0x3f800000u | (w >> 9)) - 0.99999994f;
+}
+
+__device__ __forceinline__ double unit_f64(uint32_t w) {
+    return __hiloint2double(static_cast<int>(0x3ff00000u | (w >> 12)), static_cast<int>(w << 20)) -
+           0.99999999988358467817306518554688;  // 1 - 2^-33
+}
+
+template <typename Real>
+struct Coord;
+
+template <>
+struct Coord<float> {
+    __device__ __forceinline__ static float map(uint32_t w, float lo, float width) {
+        return __fmaf_rn(unit_f32(w), width, lo);
+    }
+};
+
+template <>
+struct Coord<double> {
+    __device__ __forceinline__ static double map(uint32_t w, double lo, double width) {
+        return __fma_rn(unit_f64(w), width, lo);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Lattice constants of Eq. (Gen2) folded for the residual
+//   R = v_next + v (c_adv (v_r - v_l) + (2 c_dif - 1)) - c_dif (v_r + v_l)
+// which equals v_next - v + tau (v (v_r - v_l)/(2a) - nu (v_r - 2v + v_l)/a^2)
+// with c_adv = nonlinear tau / (2a) and c_dif = nu tau / a^2.
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct LatticeConst {
+    Real c_adv;
+    Real k1;         // 2 c_dif - 1
+    Real neg_c_dif;  // -c_dif
+    Real inv_2Dtau;  // 1 / (2 D tau)
+    Real half_mass2; // mass2 / 2
+};
+
+// Sum of squared residuals over the periodic lattice (d = NX * NT values in
+// registers, coordinate j = m * NT + l).
+template <int NX, int NT, typename Real>
+__device__ __forceinline__ Real residual_sq_sum(const Real (&u)[NX * NT], const LatticeConst<Real> &c) {
+    Real acc = Real(0);
+#pragma unroll
+    for (int m = 0; m < NX; ++m) {
+#pragma unroll
+        for (int l = 0; l < NT; ++l) {
+            const Real here = u[m * NT + l];
+            const Real next = u[m * NT + (l + 1) % NT];
+            const Real right = u[((m + 1) % NX) * NT + l];
+            const Real left = u[((m + NX - 1) % NX) * NT + l];
+            const Real t = fma(c.c_adv, right - left, c.k1);
+            Real R = fma(here, t, next);
+            R = fma(c.neg_c_dif, right + left, R);
+            acc = fma(R, R, acc);
+        }
+    }
+    return acc;
+}
+
+// Unscaled equal-time products Q_r = sum_{l,m} v_{l,m} v_{l,m+r} = d P_r,
+// r = 0..NX/2.  For even NX the r = NX/2 pairs are counted twice.
+template <int NX, int NT, typename Real>
+__device__ __forceinline__ void products(const Real (&u)[NX * NT], Real (&Q)[NX / 2 + 1]) {
+    constexpr int R = NX / 2 + 1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        Real s = Real(0);
+        const bool half = (2 * r == NX) && r > 0;
+#pragma unroll
+        for (int m = 0; m < (half ? NX / 2 : NX); ++m) {
+#pragma unroll
+            for (int l = 0; l < NT; ++l) s = fma(u[m * NT + l], u[((m + r) % NX) * NT + l], s);
+        }
+        Q[r] = half ? Real(2) * s : s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shifted sums.  A record (m, s[K]) with K = 2 + 3R stands for the sums of
+// w = exp(-(S - m)):   [0] w  [1] w^2  [2+r] w Q_r  [2+R+r] w^2 Q_r
+// [2+2R+r] w^2 Q_r^2.  "order" 1 sums scale with exp(-dm), order 2 with
+// exp(-2 dm) when the shift moves.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int sum_count(int R) { return 2 + 3 * R; }
+__host__ __device__ constexpr bool second_order(int k, int R) { return k == 1 || k >= 2 + R; }
+
+// Per-thread accumulators.  Float: Kahan-compensated; double: plain.
+template <typename Real, int K>
+struct ThreadSums;
+
+template <int K>
+struct ThreadSums<float, K> {
+    float s[K];
+    float c[K];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[k] = c[k] = 0.f;
+    }
+    __device__ __forceinline__ void add(int k, float x) {
+        const float y = x - c[k];
+        const float t = s[k] + y;
+        c[k] = (t - s[k]) - y;
+        s[k] = t;
+    }
+    __device__ __forceinline__ void scale(int k, float f) {
+        s[k] *= f;
+        c[k] *= f;
+    }
+    __device__ __forceinline__ double value(int k) const {
+        return static_cast<double>(s[k]) - static_cast<double>(c[k]);
+    }
+};
+
+template <int K>
+struct ThreadSums<double, K> {
+    double s[K];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[k] = 0.0;
+    }
+    __device__ __forceinline__ void add(int k, double x) { s[k] += x; }
+    __device__ __forceinline__ void scale(int k, double f) { s[k] *= f; }
+    __device__ __forceinline__ double value(int k) const { return s[k]; }
+};
+
+__device__ __forceinline__ float exp_real(float x) { return expf(x); }
+__device__ __forceinline__ double exp_real(double x) { return exp(x); }
+
+// Combine record b into record a (both in double).  Written without fused
+// multiply-adds so that it is commutative: a butterfly exchange then leaves
+// every lane with bit-identical values.
+template <int K, int R>
+__device__ __forceinline__ void merge_record(double &ma, double (&sa)[K], double mb, const double (&sb)[K]) {
+    const double mn = fmin(ma, mb);
+    const double fa = (ma == INFINITY) ? 0.0 : exp(mn - ma);
+    const double fb = (mb == INFINITY) ? 0.0 : exp(mn - mb);
+    const double fa2 = fa * fa, fb2 = fb * fb;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const bool sq = second_order(k, R);
+        sa[k] = __dadd_rn(__dmul_rn(sa[k], sq ? fa2 : fa), __dmul_rn(sb[k], sq ? fb2 : fb));
+    }
+    ma = mn;
+}
+
+}  // namespace bfi

@@ -1,0 +1,82 @@
+// bfi_kernels.h -- internal interface between the C ABI (api.cu) and the
+// kernels (integrand.cu).  Not installed; the public header is include/bfi.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bfi {
+
+constexpr int kBlock = 256;   // threads per CTA of the integrand kernels
+constexpr int kMaxD = 512;    // largest lattice (d = nx * nt) the library accepts
+
+// Lattice shapes with a compiled thread-per-sample kernel (NX, NT).
+#define BFI_COMPILED_SHAPES(X) \
+    X(2, 1) X(3, 1) X(4, 1) X(2, 2) X(3, 2) X(4, 2) X(10, 2)
+
+struct LatticeParams {
+    int32_t nx, nt;
+    double nu, D, a, tau, nonlinear, mass2;
+};
+
+struct IntegrandArgs {
+    const double *lo;          // [nsub * d]
+    const double *hi;          // [nsub * d]
+    const uint32_t *sub_id;    // [nsub] or null
+    const uint64_t *samples;   // [nsub]
+    const int64_t *chunk_off;  // [nsub + 1]
+    double *partials;          // [nchunks * (K + 2)]
+    int64_t nsub;
+    int64_t nchunks;
+    int64_t chunk_samples;
+};
+
+struct MergeArgs {
+    const double *lo, *hi;
+    const int64_t *chunk_off;
+    const double *partials;
+    double *slots;
+    int64_t nsub;
+    int32_t R, d;
+};
+
+struct TotalsArgs {
+    const double *slots;
+    double *totals;
+    int64_t nsub;
+    int32_t R;
+};
+
+struct PointsArgs {
+    const double *lo, *hi;
+    double *y;
+    uint64_t first;
+    int64_t count;
+    int32_t d;
+    uint32_t sub_id;
+};
+
+struct EvalArgs {
+    const double *y;
+    double *S, *P;
+    int64_t npts;
+};
+
+using IntegrandLauncher = cudaError_t (*)(const IntegrandArgs &, const LatticeParams &, uint32_t, uint32_t, int,
+                                          cudaStream_t);
+using OccupancyQuery = cudaError_t (*)(int *);
+using EvalLauncher = cudaError_t (*)(const EvalArgs &, const LatticeParams &, cudaStream_t);
+
+// index 0 = FP64, 1 = FP32
+struct ShapeKernels {
+    int nx, nt;
+    IntegrandLauncher integrand[2];
+    OccupancyQuery occupancy[2];
+    EvalLauncher eval[2];
+};
+
+const ShapeKernels *find_shape(int nx, int nt);
+cudaError_t launch_merges(const MergeArgs &m, const TotalsArgs &t, cudaStream_t st);
+cudaError_t launch_points(const PointsArgs &a, bool fp32, uint32_t seed, uint32_t job, cudaStream_t st);
+
+}  // namespace bfi

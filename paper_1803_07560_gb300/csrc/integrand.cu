@@ -1,0 +1,410 @@
+// integrand.cu -- the hot path of the Monte Carlo evaluation of the lattice
+// Burgers functional integral (Honkonen & Honkonen, arXiv:1803.07560,
+// Eq. (Gen2), Sec. 3 and Sec. 4) as sm_103a kernels:
+//
+//   integrand_tps  persistent, thread-per-sample: Philox points -> action ->
+//                  shifted weight -> products -> per-thread sums; then a
+//                  warp / block merge of shifted records into one partial
+//                  record per chunk of samples
+//   merge_subvolumes   FP64 merge of each subvolume's chunk records, in chunk
+//                      order, into its slot
+//   merge_totals       FP64 merge of all slots into Z, C(r) and errors
+//
+// Every reduction has a fixed order, so results are bitwise reproducible and do
+// not depend on what else runs on the device.
+#include "bfi_device.cuh"
+#include "bfi_kernels.h"
+
+#include <cmath>
+
+namespace bfi {
+
+// ---------------------------------------------------------------------------
+// Chunk lookup: chunks of subvolume s are [chunk_off[s], chunk_off[s+1]).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t find_subvolume(const int64_t *chunk_off, int64_t nsub, int64_t c) {
+    int64_t lo = 0, hi = nsub;  // invariant: chunk_off[lo] <= c < chunk_off[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (chunk_off[mid] <= c) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename Real>
+struct BoxPair;
+template <>
+struct BoxPair<float> {
+    __device__ __forceinline__ static void load(const double *lo, const double *hi, int j, float &b, float &w) {
+        b = __double2float_rn(lo[j]);
+        w = __double2float_rn(hi[j] - lo[j]);
+    }
+};
+template <>
+struct BoxPair<double> {
+    __device__ __forceinline__ static void load(const double *lo, const double *hi, int j, double &b, double &w) {
+        b = lo[j];
+        w = hi[j] - lo[j];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Thread-per-sample integrand.  One CTA processes chunks blockIdx.x,
+// blockIdx.x + gridDim.x, ...; within a chunk thread t takes samples
+// first + t, first + t + B, ...  Lattice, box and sums live in registers.
+// ---------------------------------------------------------------------------
+template <int NX, int NT, typename Real, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) integrand_tps(const IntegrandArgs args, const LatticeConst<Real> lc,
+                                                       const RoundKeys rk) {
+    constexpr int D = NX * NT;
+    constexpr int R = NX / 2 + 1;
+    constexpr int K = sum_count(R);
+    constexpr int NQ = (D + 3) / 4;
+    constexpr int WARPS = BLOCK / 32;
+    __shared__ double s_rec[WARPS][K + 1];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+
+    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+        const int64_t s = find_subvolume(args.chunk_off, args.nsub, c);
+        const uint64_t n_s = args.samples[s];
+        const uint64_t first = static_cast<uint64_t>(c - args.chunk_off[s]) * args.chunk_samples;
+        const uint64_t cnt = min(static_cast<uint64_t>(args.chunk_samples), n_s - first);
+        const uint32_t sid = args.sub_id ? args.sub_id[s] : static_cast<uint32_t>(s);
+        const double *lo = args.lo + s * D;
+        const double *hi = args.hi + s * D;
+
+        Real box_lo[D], box_w[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) BoxPair<Real>::load(lo, hi, j, box_lo[j], box_w[j]);
+
+        ThreadSums<Real, K> acc;
+        acc.zero();
+        Real m_t = Real(INFINITY);
+
+        for (uint64_t k = tid; k < cnt; k += BLOCK) {
+            const uint64_t i = first + k;
+            Real u[D];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const uint4 wd = philox4x32_10(
+                    make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid),
+                    rk);
+                const uint32_t w4[4] = {wd.x, wd.y, wd.z, wd.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (4 * q + t < D) u[4 * q + t] = Coord<Real>::map(w4[t], box_lo[4 * q + t], box_w[4 * q + t]);
+            }
+            Real Q[R];
+            products<NX, NT, Real>(u, Q);
+            const Real S = fma(residual_sq_sum<NX, NT, Real>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]);
+            if (S < m_t) {  // new smallest action: move the shift down
+                const Real f = exp_real(S - m_t);
+                const Real f2 = f * f;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
+                m_t = S;
+            }
+            const Real w = exp_real(m_t - S);
+            acc.add(0, w);
+            acc.add(1, w * w);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const Real wq = w * Q[r];
+                acc.add(2 + r, wq);
+                acc.add(2 + R + r, w * wq);
+                acc.add(2 + 2 * R + r, wq * wq);
+            }
+        }
+
+        // ---- warp butterfly, then warps in order ----
+        double m = (m_t == Real(INFINITY)) ? INFINITY : static_cast<double>(m_t);
+        double rec[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) rec[kk] = acc.value(kk);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            double other[K];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) other[kk] = __shfl_xor_sync(0xffffffffu, rec[kk], off);
+            const double mo = __shfl_xor_sync(0xffffffffu, m, off);
+            merge_record<K, R>(m, rec, mo, other);
+        }
+        if (lane == 0) {
+            s_rec[warp][0] = m;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) s_rec[warp][1 + kk] = rec[kk];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double mb = s_rec[0][0];
+            double rb[K];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) rb[kk] = s_rec[0][1 + kk];
+            for (int wv = 1; wv < WARPS; ++wv) {
+                double ro[K];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) ro[kk] = s_rec[wv][1 + kk];
+                merge_record<K, R>(mb, rb, s_rec[wv][0], ro);
+            }
+            double *out = args.partials + c * (K + 2);
+            out[0] = static_cast<double>(cnt);
+            out[1] = mb;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) out[2 + kk] = rb[kk];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-subvolume FP64 merge of chunk records, in chunk order.  Also scales the
+// unscaled products Q_r = d P_r back to P_r and records log V_s.
+// ---------------------------------------------------------------------------
+__global__ void merge_subvolumes(const MergeArgs a) {
+    const int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (s >= a.nsub) return;
+    const int R = a.R, K = 2 + 3 * R, SL = 5 + 3 * R;
+    double *slot = a.slots + s * SL;
+    double n = 0.0, m = INFINITY;
+    for (int k = 0; k < K; ++k) slot[3 + k] = 0.0;
+    for (int64_t c = a.chunk_off[s]; c < a.chunk_off[s + 1]; ++c) {
+        const double *p = a.partials + c * (K + 2);
+        n += p[0];
+        const double mb = p[1];
+        const double mn = fmin(m, mb);
+        const double fa = (m == INFINITY) ? 0.0 : exp(mn - m);
+        const double fb = (mb == INFINITY) ? 0.0 : exp(mn - mb);
+        for (int k = 0; k < K; ++k) {
+            const bool sq = (k == 1) || (k >= 2 + R);
+            slot[3 + k] = __dadd_rn(__dmul_rn(slot[3 + k], sq ? fa * fa : fa), __dmul_rn(p[2 + k], sq ? fb * fb : fb));
+        }
+        m = mn;
+    }
+    const double inv_d = 1.0 / static_cast<double>(a.d);
+    for (int r = 0; r < R; ++r) {
+        slot[5 + r] *= inv_d;
+        slot[5 + R + r] *= inv_d;
+        slot[5 + 2 * R + r] *= inv_d * inv_d;
+    }
+    double log_vol = 0.0;
+    for (int j = 0; j < a.d; ++j) log_vol += log(a.hi[s * a.d + j] - a.lo[s * a.d + j]);
+    slot[0] = n;
+    slot[1] = m;
+    slot[2] = log_vol;
+}
+
+// ---------------------------------------------------------------------------
+// Cross-subvolume FP64 merge (one CTA of 256 threads, fixed-order trees).
+//   ls_s = log V_s - log n_s - m_s,  L = max ls_s,  f_s = exp(ls_s - L)
+//   Z' = sum f_s sum w,  N'(r) = sum f_s sum w P_r,  C = N'/Z'
+//   Var Z' = sum f_s^2 (n sum w^2 - (sum w)^2)/(n-1)
+//   Var C  = sum f_s^2 [V_N - 2 C Cov + C^2 V_Z] / Z'^2   (delta method)
+// ---------------------------------------------------------------------------
+constexpr int kTotThreads = 256;
+
+__device__ double block_sum(double v, double *sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int off = kTotThreads / 2; off > 0; off >>= 1) {
+        if (t < off) sh[t] = sh[t] + sh[t + off];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ double block_max(double v, double *sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int off = kTotThreads / 2; off > 0; off >>= 1) {
+        if (t < off) sh[t] = fmax(sh[t], sh[t + off]);
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kTotThreads) merge_totals(const TotalsArgs a) {
+    __shared__ double sh[kTotThreads];
+    const int t = threadIdx.x;
+    const int R = a.R, SL = 5 + 3 * R;
+    double lmax = -INFINITY, n_tot = 0.0, used = 0.0;
+    for (int64_t s = t; s < a.nsub; s += kTotThreads) {
+        const double *q = a.slots + s * SL;
+        if (q[0] <= 0.0) continue;
+        n_tot += q[0];
+        used += 1.0;
+        if (!(q[3] > 0.0)) continue;
+        lmax = fmax(lmax, q[2] - log(q[0]) - q[1]);
+    }
+    const double L = block_max(lmax, sh);
+    n_tot = block_sum(n_tot, sh);
+    used = block_sum(used, sh);
+
+    // Z' and Var Z'
+    double z = 0.0, vz = 0.0, bad = 0.0;
+    for (int64_t s = t; s < a.nsub; s += kTotThreads) {
+        const double *q = a.slots + s * SL;
+        if (q[0] <= 0.0 || !(q[3] > 0.0)) continue;
+        const double n = q[0];
+        const double f = exp(q[2] - log(n) - q[1] - L);
+        z += f * q[3];
+        if (n < 2.0) { bad = 1.0; continue; }
+        vz += f * f * (n * q[4] - q[3] * q[3]) / (n - 1.0);
+    }
+    const double Z = block_sum(z, sh);
+    const double VZ = block_sum(vz, sh);
+    const bool inf_err = block_max(bad, sh) > 0.0;
+    if (t == 0) {
+        a.totals[0] = L + log(Z);
+        a.totals[1] = inf_err ? INFINITY : sqrt(VZ) / Z;
+        a.totals[2] = n_tot;
+        a.totals[3] = used;
+    }
+    for (int r = 0; r < R; ++r) {
+        double nr = 0.0;
+        for (int64_t s = t; s < a.nsub; s += kTotThreads) {
+            const double *q = a.slots + s * SL;
+            if (q[0] <= 0.0 || !(q[3] > 0.0)) continue;
+            nr += exp(q[2] - log(q[0]) - q[1] - L) * q[5 + r];
+        }
+        const double C = block_sum(nr, sh) / Z;
+        double var = 0.0;
+        for (int64_t s = t; s < a.nsub; s += kTotThreads) {
+            const double *q = a.slots + s * SL;
+            if (q[0] <= 0.0 || !(q[3] > 0.0)) continue;
+            const double n = q[0];
+            if (n < 2.0) continue;
+            const double f = exp(q[2] - log(n) - q[1] - L);
+            const double vN = (n * q[5 + 2 * R + r] - q[5 + r] * q[5 + r]) / (n - 1.0);
+            const double cov = (n * q[5 + R + r] - q[3] * q[5 + r]) / (n - 1.0);
+            const double vZ = (n * q[4] - q[3] * q[3]) / (n - 1.0);
+            var += f * f * (vN - 2.0 * C * cov + C * C * vZ);
+        }
+        const double V = block_sum(var, sh);
+        if (t == 0) {
+            a.totals[4 + r] = C;
+            a.totals[4 + R + r] = inf_err ? INFINITY : sqrt(V > 0.0 ? V : 0.0) / Z;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-step kernels for step-by-step checks.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void points_kernel(const PointsArgs a, const RoundKeys rk) {
+    const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int nq = (a.d + 3) / 4;
+    if (idx >= a.count * nq) return;
+    const int64_t k = idx / nq;
+    const int q = static_cast<int>(idx % nq);
+    const uint64_t i = a.first + static_cast<uint64_t>(k);
+    const uint4 wd = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), a.sub_id), rk);
+    const uint32_t w4[4] = {wd.x, wd.y, wd.z, wd.w};
+    for (int t = 0; t < 4; ++t) {
+        const int j = 4 * q + t;
+        if (j >= a.d) break;
+        Real b, w;
+        BoxPair<Real>::load(a.lo, a.hi, j, b, w);
+        a.y[k * a.d + j] = static_cast<double>(Coord<Real>::map(w4[t], b, w));
+    }
+}
+
+template <int NX, int NT, typename Real>
+__global__ void eval_kernel(const EvalArgs a, const LatticeConst<Real> lc) {
+    constexpr int D = NX * NT;
+    constexpr int R = NX / 2 + 1;
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= a.npts) return;
+    Real u[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) u[j] = static_cast<Real>(a.y[i * D + j]);
+    Real Q[R];
+    products<NX, NT, Real>(u, Q);
+    const Real S = fma(residual_sq_sum<NX, NT, Real>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]);
+    a.S[i] = static_cast<double>(S);
+#pragma unroll
+    for (int r = 0; r < R; ++r) a.P[i * R + r] = static_cast<double>(Q[r]) / static_cast<double>(D);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers and the table of compiled shapes.
+// ---------------------------------------------------------------------------
+template <typename Real>
+LatticeConst<Real> make_const(const LatticeParams &p) {
+    LatticeConst<Real> c;
+    const double c_adv = p.nonlinear * p.tau / (2.0 * p.a);
+    const double c_dif = p.nu * p.tau / (p.a * p.a);
+    c.c_adv = static_cast<Real>(c_adv);
+    c.k1 = static_cast<Real>(2.0 * c_dif - 1.0);
+    c.neg_c_dif = static_cast<Real>(-c_dif);
+    c.inv_2Dtau = static_cast<Real>(1.0 / (2.0 * p.D * p.tau));
+    c.half_mass2 = static_cast<Real>(0.5 * p.mass2);
+    return c;
+}
+
+template <int NX, int NT, typename Real>
+cudaError_t launch_integrand(const IntegrandArgs &args, const LatticeParams &p, uint32_t seed, uint32_t job,
+                             int grid, cudaStream_t st) {
+    integrand_tps<NX, NT, Real, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<Real>(p), make_round_keys(seed, job));
+    return cudaGetLastError();
+}
+
+template <int NX, int NT, typename Real>
+cudaError_t occupancy_integrand(int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrand_tps<NX, NT, Real, kBlock>, kBlock, 0);
+}
+
+template <int NX, int NT, typename Real>
+cudaError_t launch_eval(const EvalArgs &a, const LatticeParams &p, cudaStream_t st) {
+    const int threads = 128;
+    const int64_t blocks = (a.npts + threads - 1) / threads;
+    if (blocks > 0) eval_kernel<NX, NT, Real><<<static_cast<unsigned>(blocks), threads, 0, st>>>(a, make_const<Real>(p));
+    return cudaGetLastError();
+}
+
+#define BFI_SHAPE_ENTRY(NX, NT)                                                                         \
+    {NX, NT,                                                                                            \
+     {launch_integrand<NX, NT, double>, launch_integrand<NX, NT, float>},                               \
+     {occupancy_integrand<NX, NT, double>, occupancy_integrand<NX, NT, float>},                         \
+     {launch_eval<NX, NT, double>, launch_eval<NX, NT, float>}},
+
+static const ShapeKernels kShapes[] = {BFI_COMPILED_SHAPES(BFI_SHAPE_ENTRY)};
+
+const ShapeKernels *find_shape(int nx, int nt) {
+    for (const auto &s : kShapes)
+        if (s.nx == nx && s.nt == nt) return &s;
+    return nullptr;
+}
+
+cudaError_t launch_merges(const MergeArgs &m, const TotalsArgs &t, cudaStream_t st) {
+    const int threads = 128;
+    const int64_t blocks = (m.nsub + threads - 1) / threads;
+    merge_subvolumes<<<static_cast<unsigned>(blocks), threads, 0, st>>>(m);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    merge_totals<<<1, kTotThreads, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points(const PointsArgs &a, bool fp32, uint32_t seed, uint32_t job, cudaStream_t st) {
+    const int threads = 128;
+    const int64_t work = a.count * ((a.d + 3) / 4);
+    const int64_t blocks = (work + threads - 1) / threads;
+    if (blocks == 0) return cudaSuccess;
+    if (fp32)
+        points_kernel<float><<<static_cast<unsigned>(blocks), threads, 0, st>>>(a, make_round_keys(seed, job));
+    else
+        points_kernel<double><<<static_cast<unsigned>(blocks), threads, 0, st>>>(a, make_round_keys(seed, job));
+    return cudaGetLastError();
+}
+
+}  // namespace bfi

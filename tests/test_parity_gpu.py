@@ -1,0 +1,224 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances.  FP64 mode: every sum within 1e-12 relative of the oracle, where
+sums that can cancel (those with P_r, |P_r| <= P_0 per sample) are measured
+against their P_0 counterpart; C(r) within 1e-12 of C(0).  FP32 mode is
+compared with the oracle's FP32-points mode (the identical float points
+evaluated in FP64), within FP32_RTOL, the bound the FP32 path states.
+Statistical error estimates (variances, which cancel) are compared at 1e-9
+(FP64) and 1e-3 (FP32).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-12
+FP32_RTOL = 1e-5
+SHAPES = [(2, 1), (3, 1), (4, 1), (2, 2), (3, 2), (4, 2), (10, 2)]
+
+
+@pytest.fixture(scope="module")
+def dev(bfi):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def lat_of(mod, job, **kw):
+    return mod.lattice(job.nx, job.nt, job.nu, job.D, job.a, job.tau, **kw)
+
+
+def run_gpu(bfi, dev, job, precision, nonlinear=1.0, mass2=0.0):
+    lat = lat_of(bfi, job, nonlinear=nonlinear, mass2=mass2)
+    plan = bfi.Plan(lat, job.samples, precision)
+    lo = torch.tensor(job.lo, dtype=torch.float64, device=dev)
+    hi = torch.tensor(job.hi, dtype=torch.float64, device=dev)
+    sid = None if job.sub_id is None else torch.tensor(job.sub_id.astype(np.int32), device=dev)
+    slots, totals = plan.execute(lo, hi, job.seed, job.job_id, sub_id=sid)
+    torch.cuda.synchronize()
+    return slots.cpu().numpy(), totals.cpu().numpy(), plan
+
+
+def run_oracle(job, fp32_points=False, nonlinear=1.0, mass2=0.0):
+    lat = lat_of(oracle, job, nonlinear=nonlinear, mass2=mass2)
+    return oracle.integrate(lat, job.lo, job.hi, job.samples, job.seed, job.job_id,
+                            sub_id=job.sub_id, fp32_points=fp32_points)
+
+
+def assert_slots_close(g, o, R, rtol, rtol_var):
+    assert np.array_equal(g[:, 0], o[:, 0]), "sample counts differ"
+    used = o[:, 0] > 0
+    g, o = g[used], o[used]
+    np.testing.assert_allclose(g[:, 1], o[:, 1], rtol=rtol)                 # m_s
+    np.testing.assert_allclose(g[:, 2], o[:, 2], rtol=1e-14, atol=1e-14)    # log V_s
+    dm = g[:, 1] - o[:, 1]                                                  # express GPU sums in the oracle's shift
+    f1, f2 = np.exp(-dm)[:, None], np.exp(-2 * dm)[:, None]
+    sw, sw2 = g[:, 3:4] * f1, g[:, 4:5] * f2
+    swp = g[:, 5:5 + R] * f1
+    sw2p = g[:, 5 + R:5 + 2 * R] * f2
+    sw2p2 = g[:, 5 + 2 * R:] * f2
+    np.testing.assert_allclose(sw, o[:, 3:4], rtol=rtol)
+    np.testing.assert_allclose(sw2, o[:, 4:5], rtol=rtol)
+    np.testing.assert_allclose(sw2p2, o[:, 5 + 2 * R:], rtol=rtol)
+    # |P_r| <= P_0 per sample: scale the cancelling sums by their r = 0 member
+    assert np.all(np.abs(swp - o[:, 5:5 + R]) <= rtol * o[:, 5:6])
+    assert np.all(np.abs(sw2p - o[:, 5 + R:5 + 2 * R]) <= rtol * o[:, 5 + R:5 + R + 1])
+
+
+def assert_totals_close(g, o, R, rtol, rtol_var):
+    assert g[2] == o[2] and g[3] == o[3]
+    assert abs(g[0] - o[0]) <= rtol * max(1.0, abs(o[0])) + rtol            # log Z  ->  Z within rtol
+    assert np.all(np.abs(g[4:4 + R] - o[4:4 + R]) <= rtol * o[4])          # C(r), |C(r)| <= C(0)
+    np.testing.assert_allclose(g[1], o[1], rtol=rtol_var)
+    np.testing.assert_allclose(g[4 + R:], o[4 + R:], rtol=rtol_var)
+
+
+# ---------------------------------------------------------------------------
+# step 1: points
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("d,first", [(8, 0), (20, 12345), (21, (3 << 32) - 5), (512, 7)])
+def test_points_bit_exact(bfi, dev, precision, d, first):
+    rng = np.random.default_rng(d)
+    lo = rng.uniform(-5, 0, d)
+    hi = lo + rng.uniform(0.1, 5, d)
+    count = 3000 if d < 100 else 200
+    y = bfi.points(d, torch.tensor(lo, device=dev), torch.tensor(hi, device=dev), 77, 9, 4, first,
+                   count, precision).cpu().numpy()
+    yo = oracle.points(d, lo, hi, 77, 9, 4, first, count, fp32_points=bool(precision))
+    assert np.array_equal(y, yo)
+
+
+# ---------------------------------------------------------------------------
+# steps 2 and 4: action and products at given points
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,nt", SHAPES)
+@pytest.mark.parametrize("params", [dict(), dict(nu=0.3, D=2.0, a=0.7, tau=0.5, nonlinear=1.0, mass2=0.4),
+                                    dict(nonlinear=0.0, mass2=1.0)])
+def test_eval_matches_oracle(bfi, dev, nx, nt, params):
+    d = nx * nt
+    rng = np.random.default_rng(nx * 10 + nt)
+    y = rng.uniform(-5, 5, (4096, d))
+    S_o, P_o = oracle.eval_points(oracle.lattice(nx, nt, **params), y)
+    S, P = bfi.evaluate(bfi.lattice(nx, nt, **params), torch.tensor(y, device=dev), 0)
+    np.testing.assert_allclose(S.cpu().numpy(), S_o, rtol=1e-13)
+    assert np.all(np.abs(P.cpu().numpy() - P_o) <= 1e-13 * P_o[:, :1])
+    # FP32: the same device code on float points, against FP64 on the same points
+    y32 = y.astype(np.float32).astype(np.float64)
+    S_o32, P_o32 = oracle.eval_points(oracle.lattice(nx, nt, **params), y32)
+    S32, P32 = bfi.evaluate(bfi.lattice(nx, nt, **params), torch.tensor(y32, device=dev), 1)
+    np.testing.assert_allclose(S32.cpu().numpy(), S_o32, rtol=2e-5)
+    assert np.all(np.abs(P32.cpu().numpy() - P_o32) <= 2e-6 * P_o32[:, :1])
+
+
+# ---------------------------------------------------------------------------
+# the whole path
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,nt", SHAPES)
+def test_integrate_fp64_ragged(bfi, dev, nx, nt):
+    job = workloads.small_ragged(nx, nt, seed=5 + nx, nsub=3, base=30_000)
+    g_s, g_t, plan = run_gpu(bfi, dev, job, 0)
+    info = plan.info()
+    assert info.chunks > 3 * 8  # several chunks per subvolume, ragged last ones
+    o_s, o_t = run_oracle(job)
+    R = nx // 2 + 1
+    assert_slots_close(g_s, o_s, R, FP64_RTOL, 1e-9)
+    assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9)
+
+
+@pytest.mark.parametrize("nonlinear,mass2,params", [(0.0, 1.0, {}), (1.0, 0.5, dict(nu=0.4, a=0.8, tau=0.6, D=1.7))])
+def test_integrate_fp64_parameters(bfi, dev, nonlinear, mass2, params):
+    job = workloads.small_ragged(4, 2, seed=11, nsub=2, base=20_000)
+    for k, v in params.items():
+        setattr(job, k, v)
+    job.job_id = 3
+    job.sub_id = np.array([17, 4_000_000_000], dtype=np.uint32)
+    g_s, g_t, _ = run_gpu(bfi, dev, job, 0, nonlinear, mass2)
+    o_s, o_t = run_oracle(job, False, nonlinear, mass2)
+    assert_slots_close(g_s, o_s, 3, FP64_RTOL, 1e-9)
+    assert_totals_close(g_t, o_t, 3, FP64_RTOL, 1e-9)
+
+
+@pytest.mark.parametrize("nx,nt", [(3, 1), (4, 2), (10, 2)])
+def test_integrate_fp32_against_fp32_points(bfi, dev, nx, nt):
+    job = workloads.small_ragged(nx, nt, seed=21 + nx, nsub=3, base=30_000)
+    g_s, g_t, _ = run_gpu(bfi, dev, job, 1)
+    o_s, o_t = run_oracle(job, fp32_points=True)
+    R = nx // 2 + 1
+    assert_slots_close(g_s, o_s, R, FP32_RTOL, 1e-3)
+    assert_totals_close(g_t, o_t, R, FP32_RTOL, 1e-3)
+
+
+def test_edge_cases_empty_single_and_tiny(bfi, dev):
+    job = workloads.small_ragged(4, 2, seed=3, nsub=4, base=100)
+    job.samples = np.array([0, 1, 37, 1000], dtype=np.uint64)
+    g_s, g_t, _ = run_gpu(bfi, dev, job, 0)
+    o_s, o_t = run_oracle(job)
+    assert g_s[0, 0] == 0 and g_s[0, 3] == 0
+    assert np.isinf(g_t[1]) and np.isinf(o_t[1])
+    assert_slots_close(g_s, o_s, 3, FP64_RTOL, 1e-9)
+    assert g_t[0] == pytest.approx(o_t[0], rel=1e-12)
+    # without the one-sample subvolume the errors are finite again
+    sub = job.subset([0, 2, 3])
+    g_s2, g_t2, _ = run_gpu(bfi, dev, sub, 0)
+    o_s2, o_t2 = run_oracle(sub)
+    assert_totals_close(g_t2, o_t2, 3, FP64_RTOL, 1e-9)
+
+
+def test_device_merge_equals_host_merge_and_is_deterministic(bfi, dev):
+    job = workloads.small_ragged(10, 2, seed=2, nsub=5, base=20_000)
+    g_s, g_t, _ = run_gpu(bfi, dev, job, 0)
+    g_s2, g_t2, _ = run_gpu(bfi, dev, job, 0)
+    assert np.array_equal(g_s, g_s2) and np.array_equal(g_t, g_t2)
+    np.testing.assert_allclose(bfi.merge_host(10, g_s), g_t, rtol=1e-13)
+
+
+def test_host_buffer_path_equals_device_path(bfi, dev):
+    job = workloads.small_ragged(4, 2, seed=8, nsub=3, base=25_000)
+    g_s, g_t, _ = run_gpu(bfi, dev, job, 1)
+    ctx = bfi.Context(0)
+    h_s, h_t = ctx.integrate(lat_of(bfi, job), job.lo, job.hi, job.samples, job.seed, job.job_id,
+                             precision=1)
+    assert np.array_equal(g_s, h_s) and np.array_equal(g_t, h_t)
+    h_s2, h_t2 = ctx.integrate(lat_of(bfi, job), job.lo, job.hi, job.samples, job.seed, job.job_id,
+                               precision=1)
+    assert np.array_equal(h_t, h_t2)
+    ctx.close()
+
+
+def test_unsupported_shape_is_an_error(bfi, dev):
+    with pytest.raises(bfi.BfiError) as e:
+        bfi.Plan(bfi.lattice(5, 5), [100])
+    assert e.value.status == 7
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, in the launch configuration the benchmark uses
+# ---------------------------------------------------------------------------
+def test_plain_4x2_full_size(bfi, dev):
+    job = workloads.plain_4x2()
+    g_s, g_t, _ = run_gpu(bfi, dev, job, 0)
+    o_s, o_t = run_oracle(job)
+    assert_slots_close(g_s, o_s, 3, FP64_RTOL, 1e-9)
+    assert_totals_close(g_t, o_t, 3, FP64_RTOL, 1e-9)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_paper_10x2_full_size_sampled(bfi, dev, precision):
+    job = workloads.paper_10x2()
+    g_s, g_t, _ = run_gpu(bfi, dev, job, precision)
+    pick = [0, 517, 1023]
+    o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision))
+    tol = FP64_RTOL if precision == 0 else FP32_RTOL
+    assert_slots_close(g_s[pick], o_s, 6, tol, 1e-9 if precision == 0 else 1e-3)
+    # totals: the device merge of all 1024 records equals the oracle's merge of them
+    o_t = oracle.merge(10, g_s)
+    assert_totals_close(g_t, o_t, 6, 1e-13, 1e-9)
+    assert g_t[2] == 1024 * (1 << 20) and g_t[3] == 1024
+    # invariants: Z > 0 (finite log), C(0) > 0, |C(r)| <= C(0)
+    assert np.isfinite(g_t[0]) and g_t[4] > 0 and np.all(np.abs(g_t[4:10]) <= g_t[4])
