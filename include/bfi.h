@@ -32,8 +32,9 @@
  *    word j%4 of it, w, gives coordinate j:
  *      BFI_FP64:  y = fma((w + 0.5) 2^-32, hi - lo, lo)               (double)
  *      BFI_FP32:  y = fmaf(((w >> 9) + 0.5) 2^-23, (float)(hi - lo), (float)lo)
- *  - Weights: w_i = exp(-(S_i - m_s)), m_s the smallest action seen in the
- *    subvolume, so nothing underflows or overflows whatever the lattice size.
+ *  - Weights: w_i = exp(-(S_i - m_s)) with a per-subvolume shift m_s close to
+ *    the smallest action, so nothing underflows or overflows whatever the
+ *    lattice size.
  *  - Subvolume record ("slot"), bfi_slot_len(nx) = 5 + 3R doubles, R = nx/2+1:
  *      [0] n_s  [1] m_s  [2] log V_s  [3] sum w  [4] sum w^2
  *      [5 + r] sum w P_r   [5 + R + r] sum w^2 P_r   [5 + 2R + r] sum w^2 P_r^2
@@ -45,9 +46,18 @@
  *    subvolumes; the error of C(r) is the first-order (delta-method) error of
  *    a ratio of sums.  A subvolume with exactly one sample makes the errors
  *    +inf; subvolumes with no samples are skipped.
- *  - Precision: BFI_FP64 evaluates everything in double.  BFI_FP32 evaluates
- *    the points, the action, the products and the weights in float,
- *    accumulates per thread in compensated float, and merges in double.
+ *  - Precision: BFI_FP64 evaluates everything in double; m_s is then the
+ *    smallest action of the subvolume.  BFI_FP32 evaluates the points, the
+ *    action, the products and the weights in float, accumulates per thread in
+ *    Kahan-compensated float, and merges in double.  Its shift m_s starts at
+ *    the smallest FP32 action among the subvolume's first 4096 samples and
+ *    moves down only when a sample beats it by more than 16.  Samples whose
+ *    FP32 action lies within 28 of the smallest action seen get the action
+ *    recomputed in compensated FP32 (pairs of floats carrying the rounding
+ *    error, about 2^-44 relative); every other sample has a weight below
+ *    e^-28 of the largest.  The stated bound of the FP32 path, against the
+ *    FP64 evaluation of the same float points, is 1e-6 relative on Z and on
+ *    C(r) (relative to C(0)).
  *  - Errors: every call returns a bfi_status; bfi_last_error() gives a
  *    message for the calling thread.  No call aborts the process.
  *  - Pointers: "host" pointers are ordinary CPU memory, "device" pointers
@@ -76,7 +86,11 @@ typedef enum {
     BFI_E_UNSUPPORTED = 7   /* lattice shape not compiled into this library */
 } bfi_status;
 
-typedef enum { BFI_FP64 = 0, BFI_FP32 = 1 } bfi_precision;
+typedef enum {
+    BFI_FP64 = 0,
+    BFI_FP32 = 1,
+    BFI_FP32_COMPENSATED = 2  /* bfi_eval only: the compensated FP32 action (see Precision) */
+} bfi_precision;
 
 /* Lattice and parameters of Eq. (Gen2) (Sec. 2; the paper uses
  * nu = D = a = tau = 1).  nx = M spatial sites (>= 2), nt = L time slices

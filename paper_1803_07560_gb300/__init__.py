@@ -19,6 +19,7 @@ from . import _build
 
 FP64 = 0
 FP32 = 1
+FP32_COMPENSATED = 2   # evaluate() only
 
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p

@@ -92,6 +92,7 @@ struct bfi_plan {
     int64_t *d_chunk_off = nullptr;
     uint64_t *d_samples = nullptr;
     double *d_partials = nullptr;
+    float *d_hint = nullptr;
     size_t scratch_bytes = 0;
     bool timing = false, timed = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -111,6 +112,7 @@ bfi_status bfi_plan_destroy(bfi_plan *plan) {
         cudaFree(plan->d_chunk_off);
         cudaFree(plan->d_samples);
         cudaFree(plan->d_partials);
+        cudaFree(plan->d_hint);
         for (auto &e : plan->ev)
             if (e) cudaEventDestroy(e);
     }
@@ -174,9 +176,11 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
     const size_t off_bytes = sizeof(int64_t) * (nsub + 1);
     const size_t smp_bytes = sizeof(uint64_t) * nsub;
     const size_t par_bytes = sizeof(double) * static_cast<size_t>(std::max<int64_t>(p->nchunks, 1)) * (p->K + 2);
-    p->scratch_bytes = off_bytes + smp_bytes + par_bytes;
+    const size_t hint_bytes = precision == BFI_FP32 ? sizeof(float) * nsub : 0;
+    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes;
     if (cudaMalloc(&p->d_chunk_off, off_bytes) != cudaSuccess || cudaMalloc(&p->d_samples, smp_bytes) != cudaSuccess ||
-        cudaMalloc(&p->d_partials, par_bytes) != cudaSuccess) {
+        cudaMalloc(&p->d_partials, par_bytes) != cudaSuccess ||
+        (hint_bytes && cudaMalloc(&p->d_hint, hint_bytes) != cudaSuccess)) {
         cudaGetLastError();
         bfi_plan_destroy(p);
         return fail(BFI_E_NOMEM, "device allocation of %zu bytes failed", p->scratch_bytes);
@@ -215,8 +219,8 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[0], st));
     if (plan->nchunks > 0) {
-        bfi::IntegrandArgs a{lo, hi, sub_id, plan->d_samples, plan->d_chunk_off, plan->d_partials,
-                             plan->nsub, plan->nchunks, plan->chunk_samples};
+        bfi::IntegrandArgs a{lo,           hi,          sub_id,       plan->d_samples,     plan->d_chunk_off,
+                             plan->d_partials, plan->d_hint, plan->nsub, plan->nchunks, plan->chunk_samples};
         BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
     }
     if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[1], st));
@@ -458,14 +462,15 @@ bfi_status bfi_eval(const bfi_lattice *lattice, int64_t npts, const double *y, b
     bfi_status st = check_lattice(lattice);
     if (st != BFI_OK) return st;
     if (npts < 0 || (npts > 0 && (!y || !S || !P))) return fail(BFI_E_INVALID, "bad arguments to bfi_eval");
-    if (precision != BFI_FP64 && precision != BFI_FP32) return fail(BFI_E_INVALID, "unknown precision");
+    if (precision != BFI_FP64 && precision != BFI_FP32 && precision != BFI_FP32_COMPENSATED)
+        return fail(BFI_E_INVALID, "unknown precision");
     const bfi::ShapeKernels *shape = bfi::find_shape(lattice->nx, lattice->nt);
     if (!shape)
         return fail(BFI_E_UNSUPPORTED, "lattice %dx%d has no compiled kernel in this library", lattice->nx,
                     lattice->nt);
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     bfi::EvalArgs a{y, S, P, npts};
-    BFI_CUDA(shape->eval[precision](a, to_params(lattice), cs));
+    BFI_CUDA(shape->eval(a, to_params(lattice), static_cast<int>(precision), cs));
     BFI_CUDA(cudaStreamSynchronize(cs));
     return BFI_OK;
 }

@@ -137,6 +137,101 @@ __device__ __forceinline__ void products(const Real (&u)[NX * NT], Real (&Q)[NX 
 }
 
 // ---------------------------------------------------------------------------
+// Compensated ("double-float") FP32 arithmetic: a value is an unevaluated sum
+// hi + lo of two floats.  Built from the error-free transformations TwoSum
+// (Knuth) and TwoProduct (one FMA), as in Ogita, Rump & Oishi, "Accurate sum
+// and dot product" (SIAM J. Sci. Comput. 26, 2005).  About 2^-44 relative
+// accuracy, in FP32 instructions only.
+// ---------------------------------------------------------------------------
+struct DF {
+    float h, l;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, e};
+}
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return DF{p, __fmaf_rn(a, b, -p)};
+}
+
+// (a.h + a.l) * (b.h + b.l), dropping the a.l * b.l term
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    DF p = two_prod(a.h, b.h);
+    p.l = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l));
+    return fast_two_sum(p.h, p.l);
+}
+
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    DF p = two_prod(a.h, b);
+    p.l = __fmaf_rn(a.l, b, p.l);
+    return fast_two_sum(p.h, p.l);
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.h, b.h);
+    s.l = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    return fast_two_sum(s.h, s.l);
+}
+
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+    DF s = two_sum(a.h, b);
+    s.l = __fadd_rn(s.l, a.l);
+    return fast_two_sum(s.h, s.l);
+}
+
+// The constants of the residual split into hi + lo floats.
+struct LatticeConstDF {
+    DF c_adv, k1, c_dif, inv_2Dtau, half_mass2;
+};
+
+inline DF split_df(double x) {
+    const float h = static_cast<float>(x);
+    return DF{h, static_cast<float>(x - static_cast<double>(h))};
+}
+
+// S of Eq. (Gen2) at float coordinates, in compensated FP32: every residual
+// R = v_next + v (c_adv (v_r - v_l) + k1) - c_dif (v_r + v_l), its square and
+// the sum over sites carry their rounding errors along.
+template <int NX, int NT>
+__device__ __forceinline__ DF action_df(const float (&u)[NX * NT], const LatticeConstDF &c) {
+    DF acc{0.f, 0.f};
+    DF mass{0.f, 0.f};
+    const bool with_mass = c.half_mass2.h != 0.f;
+#pragma unroll
+    for (int m = 0; m < NX; ++m) {
+#pragma unroll
+        for (int l = 0; l < NT; ++l) {
+            const float here = u[m * NT + l];
+            const float next = u[m * NT + (l + 1) % NT];
+            const float right = u[((m + 1) % NX) * NT + l];
+            const float left = u[((m + NX - 1) % NX) * NT + l];
+            const DF dx = two_sum(right, -left);                    // exact
+            const DF t = df_add(df_mul(c.c_adv, dx), c.k1);         // c_adv dx + k1
+            const DF q = df_add_f(df_mul_f(t, here), next);         // v t + v_next
+            const DF lr = two_sum(right, left);                     // exact
+            const DF R = df_add(q, df_mul(c.c_dif, DF{-lr.h, -lr.l}));
+            DF sq = two_prod(R.h, R.h);
+            sq.l = __fmaf_rn(2.f * R.h, R.l, sq.l);
+            acc = df_add(acc, sq);
+            if (with_mass) mass = df_add(mass, two_prod(here, here));
+        }
+    }
+    DF S = df_mul(acc, c.inv_2Dtau);
+    if (with_mass) S = df_add(S, df_mul(mass, c.half_mass2));
+    return S;
+}
+
+// ---------------------------------------------------------------------------
 // Shifted sums.  A record (m, s[K]) with K = 2 + 3R stands for the sums of
 // w = exp(-(S - m)):   [0] w  [1] w^2  [2+r] w Q_r  [2+R+r] w^2 Q_r
 // [2+2R+r] w^2 Q_r^2.  "order" 1 sums scale with exp(-dm), order 2 with

@@ -26,6 +26,7 @@ struct IntegrandArgs {
     const uint64_t *samples;   // [nsub]
     const int64_t *chunk_off;  // [nsub + 1]
     double *partials;          // [nchunks * (K + 2)]
+    float *hint;               // [nsub] FP32 shift hints (FP32 plans only)
     int64_t nsub;
     int64_t nchunks;
     int64_t chunk_samples;
@@ -65,14 +66,14 @@ struct EvalArgs {
 using IntegrandLauncher = cudaError_t (*)(const IntegrandArgs &, const LatticeParams &, uint32_t, uint32_t, int,
                                           cudaStream_t);
 using OccupancyQuery = cudaError_t (*)(int *);
-using EvalLauncher = cudaError_t (*)(const EvalArgs &, const LatticeParams &, cudaStream_t);
+using EvalLauncher = cudaError_t (*)(const EvalArgs &, const LatticeParams &, int mode, cudaStream_t);
 
 // index 0 = FP64, 1 = FP32
 struct ShapeKernels {
     int nx, nt;
     IntegrandLauncher integrand[2];
     OccupancyQuery occupancy[2];
-    EvalLauncher eval[2];
+    EvalLauncher eval;   // mode 0 = FP64, 1 = FP32, 2 = FP32 compensated action
 };
 
 const ShapeKernels *find_shape(int nx, int nt);

@@ -2,10 +2,12 @@
 // Burgers functional integral (Honkonen & Honkonen, arXiv:1803.07560,
 // Eq. (Gen2), Sec. 3 and Sec. 4) as sm_103a kernels:
 //
-//   integrand_tps  persistent, thread-per-sample: Philox points -> action ->
+//   integrand_f64 / integrand_f32
+//                  persistent, thread-per-sample: Philox points -> action ->
 //                  shifted weight -> products -> per-thread sums; then a
 //                  warp / block merge of shifted records into one partial
 //                  record per chunk of samples
+//   hint_f32       per-subvolume starting shift of the FP32 kernel
 //   merge_subvolumes   FP64 merge of each subvolume's chunk records, in chunk
 //                      order, into its slot
 //   merge_totals       FP64 merge of all slots into Z, C(r) and errors
@@ -49,113 +51,251 @@ struct BoxPair<double> {
 };
 
 // ---------------------------------------------------------------------------
-// Thread-per-sample integrand.  One CTA processes chunks blockIdx.x,
-// blockIdx.x + gridDim.x, ...; within a chunk thread t takes samples
-// first + t, first + t + B, ...  Lattice, box and sums live in registers.
+// Chunk set-up shared by the integrand kernels.
 // ---------------------------------------------------------------------------
-template <int NX, int NT, typename Real, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) integrand_tps(const IntegrandArgs args, const LatticeConst<Real> lc,
+struct ChunkView {
+    int64_t s;          // subvolume
+    uint64_t first;     // first sample index of the chunk
+    uint64_t cnt;       // samples in the chunk
+    uint32_t sid;       // Philox counter word 3
+    const double *lo, *hi;
+};
+
+__device__ __forceinline__ ChunkView chunk_view(const IntegrandArgs &args, int64_t c, int d) {
+    ChunkView v;
+    v.s = find_subvolume(args.chunk_off, args.nsub, c);
+    const uint64_t n_s = args.samples[v.s];
+    v.first = static_cast<uint64_t>(c - args.chunk_off[v.s]) * static_cast<uint64_t>(args.chunk_samples);
+    v.cnt = min(static_cast<uint64_t>(args.chunk_samples), n_s - v.first);
+    v.sid = args.sub_id ? args.sub_id[v.s] : static_cast<uint32_t>(v.s);
+    v.lo = args.lo + v.s * d;
+    v.hi = args.hi + v.s * d;
+    return v;
+}
+
+// Coordinates of sample i (Philox blocks (q, i lo, i hi, sid), q < ceil(D/4)).
+template <int D, typename Real>
+__device__ __forceinline__ void make_point(uint64_t i, uint32_t sid, const RoundKeys &rk, const Real (&box_lo)[D],
+                                           const Real (&box_w)[D], Real (&u)[D]) {
+    constexpr int NQ = (D + 3) / 4;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint4 wd = philox4x32_10(
+            make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
+        const uint32_t w4[4] = {wd.x, wd.y, wd.z, wd.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (4 * q + t < D) u[4 * q + t] = Coord<Real>::map(w4[t], box_lo[4 * q + t], box_w[4 * q + t]);
+    }
+}
+
+// Warp butterfly, then the warps in order; thread 0 writes [cnt, m, sums].
+template <int K, int R, int WARPS>
+__device__ __forceinline__ void write_chunk_record(double m, double (&rec)[K], double (*s_rec)[K + 1], double *out,
+                                                   uint64_t cnt) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        double other[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) other[kk] = __shfl_xor_sync(0xffffffffu, rec[kk], off);
+        const double mo = __shfl_xor_sync(0xffffffffu, m, off);
+        merge_record<K, R>(m, rec, mo, other);
+    }
+    if (lane == 0) {
+        s_rec[warp][0] = m;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) s_rec[warp][1 + kk] = rec[kk];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double mb = s_rec[0][0];
+        double rb[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) rb[kk] = s_rec[0][1 + kk];
+        for (int wv = 1; wv < WARPS; ++wv) {
+            double ro[K];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) ro[kk] = s_rec[wv][1 + kk];
+            merge_record<K, R>(mb, rb, s_rec[wv][0], ro);
+        }
+        out[0] = static_cast<double>(cnt);
+        out[1] = mb;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) out[2 + kk] = rb[kk];
+    }
+    __syncthreads();
+}
+
+// Adds one weighted sample to the per-thread sums.
+template <typename Real, int K, int R>
+__device__ __forceinline__ void accumulate(ThreadSums<Real, K> &acc, Real w, const Real (&Q)[R]) {
+    acc.add(0, w);
+    acc.add(1, w * w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const Real wq = w * Q[r];
+        acc.add(2 + r, wq);
+        acc.add(2 + R + r, w * wq);
+        acc.add(2 + 2 * R + r, wq * wq);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 integrand, thread per sample.  One CTA processes chunks blockIdx.x,
+// blockIdx.x + gridDim.x, ...; within a chunk thread t takes samples
+// first + t, first + t + B, ...  The shift is the thread's running minimum
+// of S; the sums are rescaled whenever it moves.
+// ---------------------------------------------------------------------------
+template <int NX, int NT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) integrand_f64(const IntegrandArgs args, const LatticeConst<double> lc,
                                                        const RoundKeys rk) {
     constexpr int D = NX * NT;
     constexpr int R = NX / 2 + 1;
     constexpr int K = sum_count(R);
-    constexpr int NQ = (D + 3) / 4;
     constexpr int WARPS = BLOCK / 32;
     __shared__ double s_rec[WARPS][K + 1];
-
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
-        const int64_t s = find_subvolume(args.chunk_off, args.nsub, c);
-        const uint64_t n_s = args.samples[s];
-        const uint64_t first = static_cast<uint64_t>(c - args.chunk_off[s]) * args.chunk_samples;
-        const uint64_t cnt = min(static_cast<uint64_t>(args.chunk_samples), n_s - first);
-        const uint32_t sid = args.sub_id ? args.sub_id[s] : static_cast<uint32_t>(s);
-        const double *lo = args.lo + s * D;
-        const double *hi = args.hi + s * D;
-
-        Real box_lo[D], box_w[D];
+        const ChunkView v = chunk_view(args, c, D);
+        double box_lo[D], box_w[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) BoxPair<Real>::load(lo, hi, j, box_lo[j], box_w[j]);
+        for (int j = 0; j < D; ++j) BoxPair<double>::load(v.lo, v.hi, j, box_lo[j], box_w[j]);
 
-        ThreadSums<Real, K> acc;
+        ThreadSums<double, K> acc;
         acc.zero();
-        Real m_t = Real(INFINITY);
-
-        for (uint64_t k = tid; k < cnt; k += BLOCK) {
-            const uint64_t i = first + k;
-            Real u[D];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const uint4 wd = philox4x32_10(
-                    make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid),
-                    rk);
-                const uint32_t w4[4] = {wd.x, wd.y, wd.z, wd.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (4 * q + t < D) u[4 * q + t] = Coord<Real>::map(w4[t], box_lo[4 * q + t], box_w[4 * q + t]);
-            }
-            Real Q[R];
-            products<NX, NT, Real>(u, Q);
-            const Real S = fma(residual_sq_sum<NX, NT, Real>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]);
+        double m_t = INFINITY;
+        for (uint64_t k = tid; k < v.cnt; k += BLOCK) {
+            double u[D];
+            make_point<D, double>(v.first + k, v.sid, rk, box_lo, box_w, u);
+            double Q[R];
+            products<NX, NT, double>(u, Q);
+            const double S = fma(residual_sq_sum<NX, NT, double>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]);
             if (S < m_t) {  // new smallest action: move the shift down
-                const Real f = exp_real(S - m_t);
-                const Real f2 = f * f;
+                const double f = exp(S - m_t);
+                const double f2 = f * f;
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
                 m_t = S;
             }
-            const Real w = exp_real(m_t - S);
-            acc.add(0, w);
-            acc.add(1, w * w);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const Real wq = w * Q[r];
-                acc.add(2 + r, wq);
-                acc.add(2 + R + r, w * wq);
-                acc.add(2 + 2 * R + r, wq * wq);
-            }
+            accumulate<double, K, R>(acc, exp(m_t - S), Q);
         }
-
-        // ---- warp butterfly, then warps in order ----
-        double m = (m_t == Real(INFINITY)) ? INFINITY : static_cast<double>(m_t);
         double rec[K];
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) rec[kk] = acc.value(kk);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            double other[K];
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) other[kk] = __shfl_xor_sync(0xffffffffu, rec[kk], off);
-            const double mo = __shfl_xor_sync(0xffffffffu, m, off);
-            merge_record<K, R>(m, rec, mo, other);
-        }
-        if (lane == 0) {
-            s_rec[warp][0] = m;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) s_rec[warp][1 + kk] = rec[kk];
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double mb = s_rec[0][0];
-            double rb[K];
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) rb[kk] = s_rec[0][1 + kk];
-            for (int wv = 1; wv < WARPS; ++wv) {
-                double ro[K];
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) ro[kk] = s_rec[wv][1 + kk];
-                merge_record<K, R>(mb, rb, s_rec[wv][0], ro);
-            }
-            double *out = args.partials + c * (K + 2);
-            out[0] = static_cast<double>(cnt);
-            out[1] = mb;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) out[2 + kk] = rb[kk];
-        }
-        __syncthreads();
+        write_chunk_record<K, R, WARPS>(m_t, rec, s_rec, args.partials + c * (K + 2), v.cnt);
     }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 integrand.  Points, action, products and weights in float; per-thread
+// Kahan sums; merges in double.  Two things keep it within ~1e-7 of the FP64
+// result on the same points:
+//  * the shift m_acc starts at a per-subvolume hint (the smallest FP32 action
+//    of the subvolume's first samples) and moves only when a sample beats it
+//    by more than kRescaleMargin, so the sums are rescaled a handful of times;
+//  * a sample whose FP32 action lies within kRefineWindow of the running
+//    minimum m_ref (the weights that matter) gets its action recomputed in
+//    compensated FP32 (action_df); all others have weights below
+//    e^-kRefineWindow of the largest, where the FP32 action error is harmless.
+//    m_ref is shared across the CTA every kShareRows rows of samples, at
+//    fixed points, so every refinement decision is reproducible.
+// ---------------------------------------------------------------------------
+constexpr float kRefineWindow = 28.f;
+constexpr float kRescaleMargin = 16.f;
+constexpr int kShareRows = 16;
+
+template <int NX, int NT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) integrand_f32(const IntegrandArgs args, const LatticeConst<float> lc,
+                                                       const LatticeConstDF lcd, const RoundKeys rk) {
+    constexpr int D = NX * NT;
+    constexpr int R = NX / 2 + 1;
+    constexpr int K = sum_count(R);
+    constexpr int WARPS = BLOCK / 32;
+    __shared__ double s_rec[WARPS][K + 1];
+    __shared__ int s_min;
+    const int tid = threadIdx.x;
+
+    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+        const ChunkView v = chunk_view(args, c, D);
+        float box_lo[D], box_w[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) BoxPair<float>::load(v.lo, v.hi, j, box_lo[j], box_w[j]);
+        const float hint = args.hint[v.s];
+        float m_acc = hint, m_ref = hint;
+        if (tid == 0) s_min = __float_as_int(hint);  // S >= 0: float order = int order
+        __syncthreads();
+
+        ThreadSums<float, K> acc;
+        acc.zero();
+        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
+        for (uint64_t row = 0; row < nrows; ++row) {
+            const uint64_t k = row * BLOCK + tid;
+            if (k < v.cnt) {
+                float u[D];
+                make_point<D, float>(v.first + k, v.sid, rk, box_lo, box_w, u);
+                float Q[R];
+                products<NX, NT, float>(u, Q);
+                const float S_f = fmaf(residual_sq_sum<NX, NT, float>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]);
+                DF S{S_f, 0.f};
+                if (S_f < m_ref + kRefineWindow) {
+                    S = action_df<NX, NT>(u, lcd);
+                    m_ref = fminf(m_ref, S.h);
+                }
+                if (S.h < m_acc - kRescaleMargin) {  // rare: move the shift down
+                    const float f = expf(S.h - m_acc);
+                    const float f2 = f * f;
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
+                    m_acc = S.h;
+                }
+                const float w = expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l));
+                accumulate<float, K, R>(acc, w, Q);
+            }
+            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
+                atomicMin(&s_min, __float_as_int(m_ref));
+                __syncthreads();
+                m_ref = __int_as_float(s_min);
+                __syncthreads();
+            }
+        }
+        double rec[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) rec[kk] = acc.value(kk);
+        write_chunk_record<K, R, WARPS>(static_cast<double>(m_acc), rec, s_rec, args.partials + c * (K + 2), v.cnt);
+    }
+}
+
+// Per-subvolume hint for the FP32 shift: the smallest FP32 action among the
+// first min(n_s, kHintSamples) samples.  One CTA per subvolume.
+constexpr int kHintSamples = 4096;
+
+template <int NX, int NT>
+__global__ void __launch_bounds__(kBlock) hint_f32(const IntegrandArgs args, const LatticeConst<float> lc,
+                                                   const RoundKeys rk) {
+    constexpr int D = NX * NT;
+    constexpr int R = NX / 2 + 1;
+    __shared__ int s_min;
+    const int64_t s = blockIdx.x;
+    if (threadIdx.x == 0) s_min = __float_as_int(INFINITY);
+    __syncthreads();
+    const uint64_t n = min(args.samples[s], static_cast<uint64_t>(kHintSamples));
+    const uint32_t sid = args.sub_id ? args.sub_id[s] : static_cast<uint32_t>(s);
+    float box_lo[D], box_w[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) BoxPair<float>::load(args.lo + s * D, args.hi + s * D, j, box_lo[j], box_w[j]);
+    float mn = INFINITY;
+    for (uint64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        float u[D];
+        make_point<D, float>(k, sid, rk, box_lo, box_w, u);
+        float Q[R];
+        products<NX, NT, float>(u, Q);
+        mn = fminf(mn, fmaf(residual_sq_sum<NX, NT, float>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]));
+    }
+    atomicMin(&s_min, __float_as_int(mn));
+    __syncthreads();
+    if (threadIdx.x == 0) args.hint[s] = __int_as_float(s_min);
 }
 
 // ---------------------------------------------------------------------------
@@ -319,7 +459,7 @@ __global__ void points_kernel(const PointsArgs a, const RoundKeys rk) {
 }
 
 template <int NX, int NT, typename Real>
-__global__ void eval_kernel(const EvalArgs a, const LatticeConst<Real> lc) {
+__global__ void eval_kernel(const EvalArgs a, const LatticeConst<Real> lc, const LatticeConstDF lcd, bool compensated) {
     constexpr int D = NX * NT;
     constexpr int R = NX / 2 + 1;
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -329,8 +469,14 @@ __global__ void eval_kernel(const EvalArgs a, const LatticeConst<Real> lc) {
     for (int j = 0; j < D; ++j) u[j] = static_cast<Real>(a.y[i * D + j]);
     Real Q[R];
     products<NX, NT, Real>(u, Q);
-    const Real S = fma(residual_sq_sum<NX, NT, Real>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]);
-    a.S[i] = static_cast<double>(S);
+    double S = static_cast<double>(fma(residual_sq_sum<NX, NT, Real>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]));
+    if constexpr (sizeof(Real) == 4) {
+        if (compensated) {
+            const DF Sd = action_df<NX, NT>(u, lcd);
+            S = static_cast<double>(Sd.h) + static_cast<double>(Sd.l);
+        }
+    }
+    a.S[i] = S;
 #pragma unroll
     for (int r = 0; r < R; ++r) a.P[i * R + r] = static_cast<double>(Q[r]) / static_cast<double>(D);
 }
@@ -351,23 +497,51 @@ LatticeConst<Real> make_const(const LatticeParams &p) {
     return c;
 }
 
+LatticeConstDF make_const_df(const LatticeParams &p) {
+    LatticeConstDF c;
+    const double c_dif = p.nu * p.tau / (p.a * p.a);
+    c.c_adv = split_df(p.nonlinear * p.tau / (2.0 * p.a));
+    c.k1 = split_df(2.0 * c_dif - 1.0);
+    c.c_dif = split_df(c_dif);
+    c.inv_2Dtau = split_df(1.0 / (2.0 * p.D * p.tau));
+    c.half_mass2 = split_df(0.5 * p.mass2);
+    return c;
+}
+
 template <int NX, int NT, typename Real>
 cudaError_t launch_integrand(const IntegrandArgs &args, const LatticeParams &p, uint32_t seed, uint32_t job,
                              int grid, cudaStream_t st) {
-    integrand_tps<NX, NT, Real, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<Real>(p), make_round_keys(seed, job));
+    const RoundKeys rk = make_round_keys(seed, job);
+    if constexpr (sizeof(Real) == 8) {
+        integrand_f64<NX, NT, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<double>(p), rk);
+    } else {
+        hint_f32<NX, NT><<<static_cast<unsigned>(args.nsub), kBlock, 0, st>>>(args, make_const<float>(p), rk);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        integrand_f32<NX, NT, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<float>(p), make_const_df(p), rk);
+    }
     return cudaGetLastError();
 }
 
 template <int NX, int NT, typename Real>
 cudaError_t occupancy_integrand(int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrand_tps<NX, NT, Real, kBlock>, kBlock, 0);
+    if constexpr (sizeof(Real) == 8)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrand_f64<NX, NT, kBlock>, kBlock, 0);
+    else
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrand_f32<NX, NT, kBlock>, kBlock, 0);
 }
 
-template <int NX, int NT, typename Real>
-cudaError_t launch_eval(const EvalArgs &a, const LatticeParams &p, cudaStream_t st) {
+template <int NX, int NT>
+cudaError_t launch_eval(const EvalArgs &a, const LatticeParams &p, int mode, cudaStream_t st) {
     const int threads = 128;
     const int64_t blocks = (a.npts + threads - 1) / threads;
-    if (blocks > 0) eval_kernel<NX, NT, Real><<<static_cast<unsigned>(blocks), threads, 0, st>>>(a, make_const<Real>(p));
+    if (blocks == 0) return cudaSuccess;
+    if (mode == 0)
+        eval_kernel<NX, NT, double><<<static_cast<unsigned>(blocks), threads, 0, st>>>(a, make_const<double>(p),
+                                                                                    make_const_df(p), false);
+    else
+        eval_kernel<NX, NT, float><<<static_cast<unsigned>(blocks), threads, 0, st>>>(a, make_const<float>(p),
+                                                                                   make_const_df(p), mode == 2);
     return cudaGetLastError();
 }
 
@@ -375,7 +549,7 @@ cudaError_t launch_eval(const EvalArgs &a, const LatticeParams &p, cudaStream_t 
     {NX, NT,                                                                                            \
      {launch_integrand<NX, NT, double>, launch_integrand<NX, NT, float>},                               \
      {occupancy_integrand<NX, NT, double>, occupancy_integrand<NX, NT, float>},                         \
-     {launch_eval<NX, NT, double>, launch_eval<NX, NT, float>}},
+     launch_eval<NX, NT>},
 
 static const ShapeKernels kShapes[] = {BFI_COMPILED_SHAPES(BFI_SHAPE_ENTRY)};
 

@@ -4,9 +4,12 @@ Tolerances.  FP64 mode: every sum within 1e-12 relative of the oracle, where
 sums that can cancel (those with P_r, |P_r| <= P_0 per sample) are measured
 against their P_0 counterpart; C(r) within 1e-12 of C(0).  FP32 mode is
 compared with the oracle's FP32-points mode (the identical float points
-evaluated in FP64), within FP32_RTOL, the bound the FP32 path states.
-Statistical error estimates (variances, which cancel) are compared at 1e-9
-(FP64) and 1e-3 (FP32).
+evaluated in FP64), within FP32_RTOL = 1e-6, the bound the FP32 path states.
+The records of the two sides may use different shifts m_s (FP32 starts from
+a hint), so sums are compared after moving them to the oracle's shift.
+Statistical error estimates are variances that cancel (to ~0 when one sample
+dominates); they are compared at 1e-9 (FP64) / 1e-4 (FP32) relative, or
+absolutely at that fraction of C(0).
 """
 import numpy as np
 import pytest
@@ -18,7 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_RTOL = 1e-12
-FP32_RTOL = 1e-5
+FP32_RTOL = 1e-6
 SHAPES = [(2, 1), (3, 1), (4, 1), (2, 2), (3, 2), (4, 2), (10, 2)]
 
 
@@ -50,11 +53,12 @@ def run_oracle(job, fp32_points=False, nonlinear=1.0, mass2=0.0):
                             sub_id=job.sub_id, fp32_points=fp32_points)
 
 
-def assert_slots_close(g, o, R, rtol, rtol_var):
+def assert_slots_close(g, o, R, rtol, rtol_var, same_shift=True):
     assert np.array_equal(g[:, 0], o[:, 0]), "sample counts differ"
     used = o[:, 0] > 0
     g, o = g[used], o[used]
-    np.testing.assert_allclose(g[:, 1], o[:, 1], rtol=rtol)                 # m_s
+    if same_shift:  # FP64: both shifts are the smallest action of the subvolume
+        np.testing.assert_allclose(g[:, 1], o[:, 1], rtol=rtol, atol=rtol)
     np.testing.assert_allclose(g[:, 2], o[:, 2], rtol=1e-14, atol=1e-14)    # log V_s
     dm = g[:, 1] - o[:, 1]                                                  # express GPU sums in the oracle's shift
     f1, f2 = np.exp(-dm)[:, None], np.exp(-2 * dm)[:, None]
@@ -75,7 +79,7 @@ def assert_totals_close(g, o, R, rtol, rtol_var):
     assert abs(g[0] - o[0]) <= rtol * max(1.0, abs(o[0])) + rtol            # log Z  ->  Z within rtol
     assert np.all(np.abs(g[4:4 + R] - o[4:4 + R]) <= rtol * o[4])          # C(r), |C(r)| <= C(0)
     np.testing.assert_allclose(g[1], o[1], rtol=rtol_var)
-    np.testing.assert_allclose(g[4 + R:], o[4 + R:], rtol=rtol_var)
+    np.testing.assert_allclose(g[4 + R:], o[4 + R:], rtol=rtol_var, atol=rtol_var * o[4])
 
 
 # ---------------------------------------------------------------------------
@@ -114,6 +118,9 @@ def test_eval_matches_oracle(bfi, dev, nx, nt, params):
     S32, P32 = bfi.evaluate(bfi.lattice(nx, nt, **params), torch.tensor(y32, device=dev), 1)
     np.testing.assert_allclose(S32.cpu().numpy(), S_o32, rtol=2e-5)
     assert np.all(np.abs(P32.cpu().numpy() - P_o32) <= 2e-6 * P_o32[:, :1])
+    # the compensated FP32 action used near the minimum: ~2^-44 relative to the terms
+    Sc, _ = bfi.evaluate(bfi.lattice(nx, nt, **params), torch.tensor(y32, device=dev), 2)
+    np.testing.assert_allclose(Sc.cpu().numpy(), S_o32, rtol=1e-11, atol=1e-11)
 
 
 # ---------------------------------------------------------------------------
@@ -150,8 +157,8 @@ def test_integrate_fp32_against_fp32_points(bfi, dev, nx, nt):
     g_s, g_t, _ = run_gpu(bfi, dev, job, 1)
     o_s, o_t = run_oracle(job, fp32_points=True)
     R = nx // 2 + 1
-    assert_slots_close(g_s, o_s, R, FP32_RTOL, 1e-3)
-    assert_totals_close(g_t, o_t, R, FP32_RTOL, 1e-3)
+    assert_slots_close(g_s, o_s, R, FP32_RTOL, 1e-4, same_shift=False)
+    assert_totals_close(g_t, o_t, R, FP32_RTOL, 1e-4)
 
 
 def test_edge_cases_empty_single_and_tiny(bfi, dev):
@@ -175,7 +182,10 @@ def test_device_merge_equals_host_merge_and_is_deterministic(bfi, dev):
     g_s, g_t, _ = run_gpu(bfi, dev, job, 0)
     g_s2, g_t2, _ = run_gpu(bfi, dev, job, 0)
     assert np.array_equal(g_s, g_s2) and np.array_equal(g_t, g_t2)
-    np.testing.assert_allclose(bfi.merge_host(10, g_s), g_t, rtol=1e-13)
+    h_t = bfi.merge_host(10, g_s)
+    R = 6
+    np.testing.assert_allclose(h_t[:4 + R], g_t[:4 + R], rtol=1e-13, atol=1e-13 * abs(g_t[4]))
+    np.testing.assert_allclose(h_t[4 + R:], g_t[4 + R:], rtol=1e-9, atol=1e-9 * g_t[4])
 
 
 def test_host_buffer_path_equals_device_path(bfi, dev):
@@ -215,7 +225,7 @@ def test_paper_10x2_full_size_sampled(bfi, dev, precision):
     pick = [0, 517, 1023]
     o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision))
     tol = FP64_RTOL if precision == 0 else FP32_RTOL
-    assert_slots_close(g_s[pick], o_s, 6, tol, 1e-9 if precision == 0 else 1e-3)
+    assert_slots_close(g_s[pick], o_s, 6, tol, 1e-9 if precision == 0 else 1e-4, same_shift=precision == 0)
     # totals: the device merge of all 1024 records equals the oracle's merge of them
     o_t = oracle.merge(10, g_s)
     assert_totals_close(g_t, o_t, 6, 1e-13, 1e-9)
