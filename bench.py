@@ -158,11 +158,12 @@ def run_reference(args):
     }), flush=True)
 
 
-def workload_config(world):
+def workload_config(world, per_sub=SAMPLES_PER_SUB):
     return {"workload": "10x2 lattice (d=20), nu=D=a=tau=1, box [-5,5]^20 bisected along coords "
-                        f"0..9 into 1024 subvolumes per GPU, 2^20 Philox4x32-10 points each (seed 2), FP64",
-            "model": None, "global_batch": world * NSUB_PER_RANK * SAMPLES_PER_SUB,
-            "subvolumes_per_gpu": NSUB_PER_RANK, "samples_per_subvolume": SAMPLES_PER_SUB,
+                        f"0..9 into 1024 subvolumes per GPU, 2^{int(math.log2(per_sub))} Philox4x32-10 "
+                        "points each (seed 2), FP64",
+            "model": None, "global_batch": world * NSUB_PER_RANK * per_sub,
+            "subvolumes_per_gpu": NSUB_PER_RANK, "samples_per_subvolume": per_sub,
             "parallelism": f"subvolume shards x{world}",
             "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)"}
 
@@ -225,7 +226,7 @@ def run_bfi(args):
     lat = bfi.lattice(NX, NT)
 
     # ---- headline: FP64, 2^20 points per subvolume ----
-    job = make_job(rank, world, SAMPLES_PER_SUB)
+    job = make_job(rank, world, 1 << args.samples_log2)
     lo = torch.tensor(job.lo, device=dev)
     hi = torch.tensor(job.hi, device=dev)
     sid = torch.tensor(job.sub_id.astype(np.int32), device=dev)
@@ -256,22 +257,38 @@ def run_bfi(args):
     # ---- FP32 form of the same job with 2^24 points per subvolume ----
     fp32 = None
     if not args.skip_fp32:
-        job32 = make_job(rank, world, FP32_SAMPLES_PER_SUB)
+        job32 = make_job(rank, world, 1 << (args.samples_log2 + 4))
         plan32 = bfi.Plan(lat, job32.samples, bfi.FP32, device=local_rank)
         ms32, kern32, _, tot32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
                                              max(1, args.warmup // 2), flush_buf, dist, stream)
         ach32 = job32.total_samples * ops_per_sample_fp32(NX, NT) / (kern32 * 1e-3)
         fp32 = {"value": world * job32.total_samples / (ms32 * 1e-3), "unit": "samples/s",
-                "ms_per_step": ms32, "samples_per_subvolume": FP32_SAMPLES_PER_SUB,
+                "ms_per_step": ms32, "samples_per_subvolume": int(job32.samples[0]),
                 "dtype": "f32 (compensated sums, f64 shift and merge)",
                 "roofline": {"bound": "alu", "achieved": ach32 / 1e9, "peak": ISSUE_PEAK_OPS / 1e9,
                              "unit": "Gop/s", "frac": ach32 / ISSUE_PEAK_OPS, "traffic": None,
-                             "kernel_ms": kern32,
+                             "kernel": "hint_f32<10,2> + integrand_f32<10,2>", "kernel_ms": kern32,
                              "ops_per_sample": ops_per_sample_fp32(NX, NT)},
                 "logZ": float(tot32[0].item())}
         plan32.close()
 
     # ---- end to end through the host-buffer C-ABI call ----
+    e2e = None
+    if not args.skip_e2e:
+        e2e = run_e2e(bfi, lat, job, local_rank, args, dist, dev, samples_all)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        samples, times, cores = time_oracle(1)
+        cpu = {"value": samples / times[0], "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": "32 of the 1024 subvolumes (every 32nd) x 2^20 points of the same job, FP64 oracle"}
+    report(args, rank, world, value, ms, achieved, kern_ms, cpu, e2e, clocks, info, merged, fp32, job)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_e2e(bfi, lat, job, local_rank, args, dist, dev, samples_all):
+    import torch
     ctx = bfi.Context(local_rank)
     lo_h = torch.empty(job.lo.shape, dtype=torch.float64, pin_memory=True).numpy()
     hi_h = torch.empty(job.hi.shape, dtype=torch.float64, pin_memory=True).numpy()
@@ -297,27 +314,24 @@ def run_bfi(args):
     ctx.close()
     h2d = lo_h.nbytes + hi_h.nbytes + sid_h.nbytes
     d2h = slots_h.nbytes + tot_h.nbytes
+    return {"value": samples_all / e2e_sec, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.skip_cpu:
-        samples, times, cores = time_oracle(1)
-        cpu = {"value": samples / times[0], "unit": "samples/s", "cores": cores, "kind": "oracle",
-               "sample": "32 of the 1024 subvolumes (every 32nd) x 2^20 points of the same job, FP64 oracle"}
 
+def report(args, rank, world, value, ms, achieved, kern_ms, cpu, e2e, clocks, info, merged, fp32, job):
     if rank == 0:
         line = {
             "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(world),
+            "config": workload_config(world, int(job.samples[0])),
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9,
                          "unit": "Gop/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
-                         "kernel": "integrand_tps<10,2,double>", "kernel_ms": kern_ms,
+                         "kernel": "integrand_f64<10,2>", "kernel_ms": kern_ms,
                          "ops_per_sample": ops_per_sample_fp64(NX, NT),
                          "peak_source": "nominal FP64 1.25 TFLOP/s (FMA = 2 flops)"},
             "cpu_baseline": cpu,
-            "e2e": {"value": samples_all / e2e_sec, "unit": "samples/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": e2e,
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
             "plan": {"grid": info.grid, "block": info.block, "chunks": info.chunks,
@@ -328,8 +342,6 @@ def run_bfi(args):
             "fp32": fp32,
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
 
 
 def main():
@@ -340,6 +352,9 @@ def main():
     ap.add_argument("--impl", default="bfi", choices=["bfi", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--samples-log2", type=int, default=20,
+                    help="points per subvolume of the FP64 job (the workload is 2^20; smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -58,6 +58,16 @@
  *    e^-28 of the largest.  The stated bound of the FP32 path, against the
  *    FP64 evaluation of the same float points, is 1e-6 relative on Z and on
  *    C(r) (relative to C(0)).
+ *  - Negligible weights: a sample whose action exceeds the subvolume's
+ *    smallest action by more than W = c + ln(n_max) (n_max the largest
+ *    budget of the plan; c = 34 in BFI_FP64, 20 in BFI_FP32) has weight below
+ *    e^-W of the largest, and all such samples together move any sum by less
+ *    than e^-c relative.  They are counted in n_s but left out of the sums.
+ *    BFI_FP64 decides this from the FP32 action of the FP32 point with a
+ *    margin of 1 + 1% of S (the FP32 error is ~1e-4).  The reference action
+ *    starts at the smallest FP32 action among each subvolume's first 4096
+ *    samples and follows the smallest evaluated action, shared within a CTA
+ *    at fixed points of the sample loop, so the outcome is reproducible.
  *  - Errors: every call returns a bfi_status; bfi_last_error() gives a
  *    message for the calling thread.  No call aborts the process.
  *  - Pointers: "host" pointers are ordinary CPU memory, "device" pointers
@@ -172,6 +182,11 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi,
  * ms[0] = integrand kernel, ms[1] = merges (milliseconds).  Off by default.
  * Errors: BFI_E_INVALID (NULL, or no timed execution yet), BFI_E_CUDA. */
 bfi_status bfi_plan_set_timing(bfi_plan *plan, int enable);
+/* Samples fully evaluated (point, action, products, weight) by the last
+ * execution, and the plan's negligible-weight window (see "Negligible
+ * weights").  Waits for the device.  Either pointer may be NULL.
+ * Errors: BFI_E_INVALID, BFI_E_CUDA. */
+bfi_status bfi_plan_get_stats(bfi_plan *plan, uint64_t *evaluated, float *skip_window);
 bfi_status bfi_plan_get_timing(bfi_plan *plan, float *ms);
 
 /* ------------------------------------------------------------------------ */

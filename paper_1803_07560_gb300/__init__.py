@@ -65,6 +65,7 @@ _SIGNATURES = {
                                         _vp, _vp, _vp]),
     "bfi_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bfi_plan_get_timing": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
+    "bfi_plan_get_stats": (ctypes.c_int, [_vp, _P(ctypes.c_uint64), _P(ctypes.c_float)]),
     "bfi_ctx_create": (ctypes.c_int, [_P(_vp), ctypes.c_int]),
     "bfi_ctx_destroy": (ctypes.c_int, [_vp]),
     "bfi_integrate": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, _vp,
@@ -177,6 +178,13 @@ class Plan:
         ms = (ctypes.c_float * 2)()
         _check(_lib.bfi_plan_get_timing(self._h, ms))
         return float(ms[0]), float(ms[1])
+
+    def stats(self):
+        """(samples fully evaluated by the last execution, negligible-weight window)."""
+        n = ctypes.c_uint64()
+        w = ctypes.c_float()
+        _check(_lib.bfi_plan_get_stats(self._h, ctypes.byref(n), ctypes.byref(w)))
+        return int(n.value), float(w.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -46,12 +46,17 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    """Compile the library.  BFI_NVCC_EXTRA (environment) adds nvcc flags,
+    e.g. -DBFI_INTEGRAND_MIN_BLOCKS=1 to compile for one CTA per SM."""
+    extra_env = os.environ.get("BFI_NVCC_EXTRA", "").split()
+    if extra_env:
+        force = True
     if not force and not ptxas_info and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
     objs = []
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + extra_env
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src).replace(".cu", ".o"))

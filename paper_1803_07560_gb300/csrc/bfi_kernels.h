@@ -26,10 +26,12 @@ struct IntegrandArgs {
     const uint64_t *samples;   // [nsub]
     const int64_t *chunk_off;  // [nsub + 1]
     double *partials;          // [nchunks * (K + 2)]
-    float *hint;               // [nsub] FP32 shift hints (FP32 plans only)
+    float *hint;               // [nsub] reference actions written by hint_f32
+    unsigned long long *stats; // [1] fully evaluated samples (zeroed per execution), or null
     int64_t nsub;
     int64_t nchunks;
     int64_t chunk_samples;
+    float skip_window;         // samples above (reference + skip_window) have negligible weight
 };
 
 struct MergeArgs {

@@ -7,7 +7,8 @@
 //                  shifted weight -> products -> per-thread sums; then a
 //                  warp / block merge of shifted records into one partial
 //                  record per chunk of samples
-//   hint_f32       per-subvolume starting shift of the FP32 kernel
+//   hint_f32       per-subvolume reference action (the smallest FP32 action
+//                  of the first samples), the starting point of both kernels
 //   merge_subvolumes   FP64 merge of each subvolume's chunk records, in chunk
 //                      order, into its slot
 //   merge_totals       FP64 merge of all slots into Z, C(r) and errors
@@ -18,6 +19,12 @@
 #include "bfi_kernels.h"
 
 #include <cmath>
+
+// Resident CTAs per SM the integrand kernels are compiled for (register cap
+// 65536 / (256 * this)).
+#ifndef BFI_INTEGRAND_MIN_BLOCKS
+#define BFI_INTEGRAND_MIN_BLOCKS 2
+#endif
 
 namespace bfi {
 
@@ -141,46 +148,140 @@ __device__ __forceinline__ void accumulate(ThreadSums<Real, K> &acc, Real w, con
     }
 }
 
+// S of Eq. (Gen2): the residual sum of squares plus the optional mass term.
+template <int NX, int NT, typename Real>
+__device__ __forceinline__ Real action(const Real (&u)[NX * NT], const LatticeConst<Real> &c) {
+    Real S = residual_sq_sum<NX, NT, Real>(u, c) * c.inv_2Dtau;
+    if (c.half_mass2 != Real(0)) {
+        Real s2 = Real(0);
+#pragma unroll
+        for (int j = 0; j < NX * NT; ++j) s2 = fma(u[j], u[j], s2);
+        S = fma(c.half_mass2, s2, S);
+    }
+    return S;
+}
+
+// Raw Philox words of sample i: block q = (q, i lo, i hi, sid), word j%4.
+template <int D>
+__device__ __forceinline__ void sample_words(uint64_t i, uint32_t sid, const RoundKeys &rk, uint32_t (&w)[D]) {
+    constexpr int NQ = (D + 3) / 4;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint4 b = philox4x32_10(
+            make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
+        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (4 * q + t < D) w[4 * q + t] = w4[t];
+    }
+}
+
+// Running minimum shared across the CTA at fixed points of the sample loop:
+// every thread contributes, then every thread reads the same value, so the
+// decisions that depend on it do not depend on timing.  S >= 0, so the float
+// order equals the order of the bit patterns as signed ints.
+__device__ __forceinline__ void share_min(int *s_min, float &m_ref) {
+    atomicMin(s_min, __float_as_int(m_ref));
+    __syncthreads();
+    m_ref = __int_as_float(*s_min);
+    __syncthreads();
+}
+
+// Count of fully evaluated samples of the chunk, added to the plan's stats.
+__device__ __forceinline__ void add_evaluated(unsigned long long *stats, unsigned n_eval, unsigned *s_cnt) {
+    if (!stats) return;
+    atomicAdd(s_cnt, n_eval);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(stats, static_cast<unsigned long long>(*s_cnt));
+}
+
+// ---------------------------------------------------------------------------
+// Negligible weights.  A sample whose action exceeds the subvolume's
+// smallest action by more than args.skip_window has weight below
+// e^-skip_window of the largest; with skip_window = c + ln(n_max) the n_s such
+// samples of a subvolume change every sum by less than e^-c relative (the
+// largest weight is 1).  Both kernels leave those samples out of the
+// products, the weight and the sums.  The reference point m_ref is the
+// per-subvolume hint (the smallest FP32 action among the first samples) and
+// then the smallest action evaluated so far, shared across the CTA every
+// kShareRows rows; it is always the action of an evaluated sample, so it is
+// never below the final shift.
+// ---------------------------------------------------------------------------
+constexpr int kShareRows = 16;
+
 // ---------------------------------------------------------------------------
 // FP64 integrand, thread per sample.  One CTA processes chunks blockIdx.x,
 // blockIdx.x + gridDim.x, ...; within a chunk thread t takes samples
-// first + t, first + t + B, ...  The shift is the thread's running minimum
-// of S; the sums are rescaled whenever it moves.
+// first + t, first + t + B, ...  Each sample is first screened with its FP32
+// action on the FP32 point (cheap pipes); only samples that may carry weight
+// (within skip_window of m_ref, plus a margin of 1 + 1% of S, far above the
+// FP32 error of ~1e-4) are evaluated in FP64: FP64 point, action, products,
+// weight.  The FP64 shift is the thread's running minimum of S.
 // ---------------------------------------------------------------------------
 template <int NX, int NT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) integrand_f64(const IntegrandArgs args, const LatticeConst<double> lc,
-                                                       const RoundKeys rk) {
+__global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64(const IntegrandArgs args, const LatticeConst<double> lc,
+                                                       const LatticeConst<float> lcf, const RoundKeys rk) {
     constexpr int D = NX * NT;
     constexpr int R = NX / 2 + 1;
     constexpr int K = sum_count(R);
     constexpr int WARPS = BLOCK / 32;
     __shared__ double s_rec[WARPS][K + 1];
+    __shared__ double s_lo[D], s_w[D];
+    __shared__ float2 s_box[D];  // the same bounds as floats, for the FP32 screen
+    __shared__ int s_min;
+    __shared__ unsigned s_cnt;
     const int tid = threadIdx.x;
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
         const ChunkView v = chunk_view(args, c, D);
-        double box_lo[D], box_w[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) BoxPair<double>::load(v.lo, v.hi, j, box_lo[j], box_w[j]);
+        if (tid < D) {
+            s_lo[tid] = v.lo[tid];
+            s_w[tid] = v.hi[tid] - v.lo[tid];
+            BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
+        }
+        float m_ref = args.hint[v.s];
+        if (tid == 0) {
+            s_min = __float_as_int(m_ref);
+            s_cnt = 0u;
+        }
+        __syncthreads();
 
         ThreadSums<double, K> acc;
         acc.zero();
         double m_t = INFINITY;
-        for (uint64_t k = tid; k < v.cnt; k += BLOCK) {
-            double u[D];
-            make_point<D, double>(v.first + k, v.sid, rk, box_lo, box_w, u);
-            double Q[R];
-            products<NX, NT, double>(u, Q);
-            const double S = fma(residual_sq_sum<NX, NT, double>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]);
-            if (S < m_t) {  // new smallest action: move the shift down
-                const double f = exp(S - m_t);
-                const double f2 = f * f;
+        unsigned n_eval = 0;
+        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
+        for (uint64_t row = 0; row < nrows; ++row) {
+            const uint64_t k = row * BLOCK + tid;
+            if (k < v.cnt) {
+                uint32_t w[D];
+                sample_words<D>(v.first + k, v.sid, rk, w);
+                float uf[D];
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
-                m_t = S;
+                for (int j = 0; j < D; ++j) uf[j] = Coord<float>::map(w[j], s_box[j].x, s_box[j].y);
+                const float S_f = action<NX, NT, float>(uf, lcf);
+                if (S_f <= m_ref + args.skip_window + 1.0f + 0.01f * S_f) {
+                    double u[D];
+#pragma unroll
+                    for (int j = 0; j < D; ++j) u[j] = Coord<double>::map(w[j], s_lo[j], s_w[j]);
+                    const double S = action<NX, NT, double>(u, lc);
+                    m_ref = fminf(m_ref, __double2float_rn(S));
+                    double Q[R];
+                    products<NX, NT, double>(u, Q);
+                    if (S < m_t) {  // new smallest action: move the shift down
+                        const double f = exp(S - m_t);
+                        const double f2 = f * f;
+#pragma unroll
+                        for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
+                        m_t = S;
+                    }
+                    accumulate<double, K, R>(acc, exp(m_t - S), Q);
+                    ++n_eval;
+                }
             }
-            accumulate<double, K, R>(acc, exp(m_t - S), Q);
+            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&s_min, m_ref);
         }
+        add_evaluated(args.stats, n_eval, &s_cnt);
         double rec[K];
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) rec[kk] = acc.value(kk);
@@ -190,76 +291,78 @@ __global__ void __launch_bounds__(BLOCK) integrand_f64(const IntegrandArgs args,
 
 // ---------------------------------------------------------------------------
 // FP32 integrand.  Points, action, products and weights in float; per-thread
-// Kahan sums; merges in double.  Two things keep it within ~1e-7 of the FP64
-// result on the same points:
-//  * the shift m_acc starts at a per-subvolume hint (the smallest FP32 action
-//    of the subvolume's first samples) and moves only when a sample beats it
-//    by more than kRescaleMargin, so the sums are rescaled a handful of times;
-//  * a sample whose FP32 action lies within kRefineWindow of the running
-//    minimum m_ref (the weights that matter) gets its action recomputed in
-//    compensated FP32 (action_df); all others have weights below
-//    e^-kRefineWindow of the largest, where the FP32 action error is harmless.
-//    m_ref is shared across the CTA every kShareRows rows of samples, at
-//    fixed points, so every refinement decision is reproducible.
+// Kahan sums; merges in double.  Besides the negligible-weight rule above, two
+// things keep it within ~1e-7 of the FP64 result on the same points:
+//  * the shift m_acc starts at the per-subvolume hint and moves only when a
+//    sample beats it by more than kRescaleMargin, so the sums are rescaled a
+//    handful of times;
+//  * a sample whose FP32 action lies within kRefineWindow of m_ref (the
+//    weights that matter) gets its action recomputed in compensated FP32
+//    (action_df); all others have weights below e^-kRefineWindow of the
+//    largest, where the ~1e-5 FP32 action error is harmless.
 // ---------------------------------------------------------------------------
 constexpr float kRefineWindow = 28.f;
 constexpr float kRescaleMargin = 16.f;
-constexpr int kShareRows = 16;
 
 template <int NX, int NT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) integrand_f32(const IntegrandArgs args, const LatticeConst<float> lc,
+__global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f32(const IntegrandArgs args, const LatticeConst<float> lc,
                                                        const LatticeConstDF lcd, const RoundKeys rk) {
     constexpr int D = NX * NT;
     constexpr int R = NX / 2 + 1;
     constexpr int K = sum_count(R);
     constexpr int WARPS = BLOCK / 32;
     __shared__ double s_rec[WARPS][K + 1];
+    __shared__ float2 s_box[D];  // (lo, width) as floats; every thread reads the same word
     __shared__ int s_min;
+    __shared__ unsigned s_cnt;
     const int tid = threadIdx.x;
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
         const ChunkView v = chunk_view(args, c, D);
-        float box_lo[D], box_w[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) BoxPair<float>::load(v.lo, v.hi, j, box_lo[j], box_w[j]);
+        if (tid < D) BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
         const float hint = args.hint[v.s];
         float m_acc = hint, m_ref = hint;
-        if (tid == 0) s_min = __float_as_int(hint);  // S >= 0: float order = int order
+        if (tid == 0) {
+            s_min = __float_as_int(hint);
+            s_cnt = 0u;
+        }
         __syncthreads();
 
         ThreadSums<float, K> acc;
         acc.zero();
+        unsigned n_eval = 0;
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
             if (k < v.cnt) {
+                uint32_t w[D];
+                sample_words<D>(v.first + k, v.sid, rk, w);
                 float u[D];
-                make_point<D, float>(v.first + k, v.sid, rk, box_lo, box_w, u);
-                float Q[R];
-                products<NX, NT, float>(u, Q);
-                const float S_f = fmaf(residual_sq_sum<NX, NT, float>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]);
-                DF S{S_f, 0.f};
-                if (S_f < m_ref + kRefineWindow) {
-                    S = action_df<NX, NT>(u, lcd);
-                    m_ref = fminf(m_ref, S.h);
-                }
-                if (S.h < m_acc - kRescaleMargin) {  // rare: move the shift down
-                    const float f = expf(S.h - m_acc);
-                    const float f2 = f * f;
 #pragma unroll
-                    for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
-                    m_acc = S.h;
+                for (int j = 0; j < D; ++j) u[j] = Coord<float>::map(w[j], s_box[j].x, s_box[j].y);
+                const float S_f = action<NX, NT, float>(u, lc);
+                if (S_f <= m_ref + args.skip_window) {
+                    DF S{S_f, 0.f};
+                    if (S_f < m_ref + kRefineWindow) {
+                        S = action_df<NX, NT>(u, lcd);
+                        m_ref = fminf(m_ref, S.h);
+                    }
+                    if (S.h < m_acc - kRescaleMargin) {  // rare: move the shift down
+                        const float f = expf(S.h - m_acc);
+                        const float f2 = f * f;
+#pragma unroll
+                        for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
+                        m_acc = S.h;
+                    }
+                    float Q[R];
+                    products<NX, NT, float>(u, Q);
+                    accumulate<float, K, R>(acc, expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l)), Q);
+                    ++n_eval;
                 }
-                const float w = expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l));
-                accumulate<float, K, R>(acc, w, Q);
             }
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
-                atomicMin(&s_min, __float_as_int(m_ref));
-                __syncthreads();
-                m_ref = __int_as_float(s_min);
-                __syncthreads();
-            }
+            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&s_min, m_ref);
         }
+        add_evaluated(args.stats, n_eval, &s_cnt);
         double rec[K];
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) rec[kk] = acc.value(kk);
@@ -267,15 +370,14 @@ __global__ void __launch_bounds__(BLOCK) integrand_f32(const IntegrandArgs args,
     }
 }
 
-// Per-subvolume hint for the FP32 shift: the smallest FP32 action among the
-// first min(n_s, kHintSamples) samples.  One CTA per subvolume.
+// Per-subvolume hint: the smallest FP32 action among the first
+// min(n_s, kHintSamples) samples.  One CTA per subvolume.
 constexpr int kHintSamples = 4096;
 
 template <int NX, int NT>
 __global__ void __launch_bounds__(kBlock) hint_f32(const IntegrandArgs args, const LatticeConst<float> lc,
                                                    const RoundKeys rk) {
     constexpr int D = NX * NT;
-    constexpr int R = NX / 2 + 1;
     __shared__ int s_min;
     const int64_t s = blockIdx.x;
     if (threadIdx.x == 0) s_min = __float_as_int(INFINITY);
@@ -289,9 +391,7 @@ __global__ void __launch_bounds__(kBlock) hint_f32(const IntegrandArgs args, con
     for (uint64_t k = threadIdx.x; k < n; k += blockDim.x) {
         float u[D];
         make_point<D, float>(k, sid, rk, box_lo, box_w, u);
-        float Q[R];
-        products<NX, NT, float>(u, Q);
-        mn = fminf(mn, fmaf(residual_sq_sum<NX, NT, float>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]));
+        mn = fminf(mn, action<NX, NT, float>(u, lc));
     }
     atomicMin(&s_min, __float_as_int(mn));
     __syncthreads();
@@ -313,9 +413,14 @@ __global__ void merge_subvolumes(const MergeArgs a) {
         const double *p = a.partials + c * (K + 2);
         n += p[0];
         const double mb = p[1];
+        if (mb == INFINITY) continue;  // no evaluated samples in the chunk
+        if (mb == m) {
+            for (int k = 0; k < K; ++k) slot[3 + k] = __dadd_rn(slot[3 + k], p[2 + k]);
+            continue;
+        }
         const double mn = fmin(m, mb);
         const double fa = (m == INFINITY) ? 0.0 : exp(mn - m);
-        const double fb = (mb == INFINITY) ? 0.0 : exp(mn - mb);
+        const double fb = exp(mn - mb);
         for (int k = 0; k < K; ++k) {
             const bool sq = (k == 1) || (k >= 2 + R);
             slot[3 + k] = __dadd_rn(__dmul_rn(slot[3 + k], sq ? fa * fa : fa), __dmul_rn(p[2 + k], sq ? fb * fb : fb));
@@ -469,7 +574,7 @@ __global__ void eval_kernel(const EvalArgs a, const LatticeConst<Real> lc, const
     for (int j = 0; j < D; ++j) u[j] = static_cast<Real>(a.y[i * D + j]);
     Real Q[R];
     products<NX, NT, Real>(u, Q);
-    double S = static_cast<double>(fma(residual_sq_sum<NX, NT, Real>(u, lc), lc.inv_2Dtau, lc.half_mass2 * Q[0]));
+    double S = static_cast<double>(action<NX, NT, Real>(u, lc));
     if constexpr (sizeof(Real) == 4) {
         if (compensated) {
             const DF Sd = action_df<NX, NT>(u, lcd);
@@ -512,14 +617,13 @@ template <int NX, int NT, typename Real>
 cudaError_t launch_integrand(const IntegrandArgs &args, const LatticeParams &p, uint32_t seed, uint32_t job,
                              int grid, cudaStream_t st) {
     const RoundKeys rk = make_round_keys(seed, job);
-    if constexpr (sizeof(Real) == 8) {
-        integrand_f64<NX, NT, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<double>(p), rk);
-    } else {
-        hint_f32<NX, NT><<<static_cast<unsigned>(args.nsub), kBlock, 0, st>>>(args, make_const<float>(p), rk);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+    hint_f32<NX, NT><<<static_cast<unsigned>(args.nsub), kBlock, 0, st>>>(args, make_const<float>(p), rk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if constexpr (sizeof(Real) == 8)
+        integrand_f64<NX, NT, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<double>(p), make_const<float>(p), rk);
+    else
         integrand_f32<NX, NT, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<float>(p), make_const_df(p), rk);
-    }
     return cudaGetLastError();
 }
 

@@ -8,8 +8,10 @@ evaluated in FP64), within FP32_RTOL = 1e-6, the bound the FP32 path states.
 The records of the two sides may use different shifts m_s (FP32 starts from
 a hint), so sums are compared after moving them to the oracle's shift.
 Statistical error estimates are variances that cancel (to ~0 when one sample
-dominates); they are compared at 1e-9 (FP64) / 1e-4 (FP32) relative, or
-absolutely at that fraction of C(0).
+dominates); they are compared at 1e-9 relative (FP64), or absolutely at that
+fraction of C(0).  In FP32 the variance of C(r) is a difference of float
+sums of size ~C(0)^2, so its square root has an absolute floor of about
+sqrt(eps_32) C(0) ~ 3e-4 C(0): FP32 errors are compared at FP32_ERR_ATOL C(0).
 """
 import numpy as np
 import pytest
@@ -22,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_RTOL = 1e-12
 FP32_RTOL = 1e-6
+FP32_ERR_ATOL = 1e-3
 SHAPES = [(2, 1), (3, 1), (4, 1), (2, 2), (3, 2), (4, 2), (10, 2)]
 
 
@@ -74,12 +77,13 @@ def assert_slots_close(g, o, R, rtol, rtol_var, same_shift=True):
     assert np.all(np.abs(sw2p - o[:, 5 + R:5 + 2 * R]) <= rtol * o[:, 5 + R:5 + R + 1])
 
 
-def assert_totals_close(g, o, R, rtol, rtol_var):
+def assert_totals_close(g, o, R, rtol, rtol_var, err_atol=None):
     assert g[2] == o[2] and g[3] == o[3]
     assert abs(g[0] - o[0]) <= rtol * max(1.0, abs(o[0])) + rtol            # log Z  ->  Z within rtol
     assert np.all(np.abs(g[4:4 + R] - o[4:4 + R]) <= rtol * o[4])          # C(r), |C(r)| <= C(0)
     np.testing.assert_allclose(g[1], o[1], rtol=rtol_var)
-    np.testing.assert_allclose(g[4 + R:], o[4 + R:], rtol=rtol_var, atol=rtol_var * o[4])
+    atol = (rtol_var if err_atol is None else err_atol) * o[4]
+    np.testing.assert_allclose(g[4 + R:], o[4 + R:], rtol=rtol_var, atol=atol)
 
 
 # ---------------------------------------------------------------------------
@@ -158,7 +162,7 @@ def test_integrate_fp32_against_fp32_points(bfi, dev, nx, nt):
     o_s, o_t = run_oracle(job, fp32_points=True)
     R = nx // 2 + 1
     assert_slots_close(g_s, o_s, R, FP32_RTOL, 1e-4, same_shift=False)
-    assert_totals_close(g_t, o_t, R, FP32_RTOL, 1e-4)
+    assert_totals_close(g_t, o_t, R, FP32_RTOL, 1e-4, FP32_ERR_ATOL)
 
 
 def test_edge_cases_empty_single_and_tiny(bfi, dev):
