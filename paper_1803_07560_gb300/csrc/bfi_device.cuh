@@ -240,89 +240,4 @@ __device__ __forceinline__ DF action_df(const float (&u)[NX * NT], const Lattice
 __host__ __device__ constexpr int sum_count(int R) { return 2 + 3 * R; }
 __host__ __device__ constexpr bool second_order(int k, int R) { return k == 1 || k >= 2 + R; }
 
-// Per-thread accumulators.  Float: the first-order sums (w, w Q_r) are
-// Kahan-compensated, the second-order ones (which only feed the error
-// estimates) are plain; double: plain.
-template <typename Real, int K>
-struct ThreadSums;
-
-template <int K>
-struct ThreadSums<float, K> {
-    static constexpr int R = (K - 2) / 3;
-    static constexpr int NC = 1 + R;  // compensated: k = 0 and k = 2..1+R
-    float s[K];
-    float c[NC];
-    __device__ __forceinline__ static int comp_index(int k) { return k == 0 ? 0 : k - 1; }
-    __device__ __forceinline__ static bool compensated(int k) { return k == 0 || (k >= 2 && k < 2 + R); }
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int k = 0; k < K; ++k) s[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < NC; ++k) c[k] = 0.f;
-    }
-    __device__ __forceinline__ void add(int k, float x) {
-        if (compensated(k)) {
-            float &ck = c[comp_index(k)];
-            const float y = x - ck;
-            const float t = s[k] + y;
-            ck = (t - s[k]) - y;
-            s[k] = t;
-        } else {
-            s[k] += x;
-        }
-    }
-    __device__ __forceinline__ void scale(int k, float f) {
-        s[k] *= f;
-        if (compensated(k)) c[comp_index(k)] *= f;
-    }
-    __device__ __forceinline__ double value(int k) const {
-        return compensated(k) ? static_cast<double>(s[k]) - static_cast<double>(c[comp_index(k)])
-                              : static_cast<double>(s[k]);
-    }
-};
-
-template <int K>
-struct ThreadSums<double, K> {
-    double s[K];
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int k = 0; k < K; ++k) s[k] = 0.0;
-    }
-    __device__ __forceinline__ void add(int k, double x) { s[k] += x; }
-    __device__ __forceinline__ void scale(int k, double f) { s[k] *= f; }
-    __device__ __forceinline__ double value(int k) const { return s[k]; }
-};
-
-__device__ __forceinline__ float exp_real(float x) { return expf(x); }
-__device__ __forceinline__ double exp_real(double x) { return exp(x); }
-
-// Combine record b into record a (both in double).  Written without fused
-// multiply-adds so that it is commutative: a butterfly exchange then leaves
-// every lane with bit-identical values.
-template <int K, int R>
-__device__ __forceinline__ void merge_record(double &ma, double (&sa)[K], double mb, const double (&sb)[K]) {
-    if (mb == INFINITY) return;  // b holds no samples
-    if (ma == INFINITY) {        // a holds no samples
-#pragma unroll
-        for (int k = 0; k < K; ++k) sa[k] = sb[k];
-        ma = mb;
-        return;
-    }
-    if (ma == mb) {  // same shift (the FP32 kernel's common case): plain sums
-#pragma unroll
-        for (int k = 0; k < K; ++k) sa[k] = __dadd_rn(sa[k], sb[k]);
-        return;
-    }
-    const double mn = fmin(ma, mb);
-    const double fa = exp(mn - ma);
-    const double fb = exp(mn - mb);
-    const double fa2 = fa * fa, fb2 = fb * fb;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const bool sq = second_order(k, R);
-        sa[k] = __dadd_rn(__dmul_rn(sa[k], sq ? fa2 : fa), __dmul_rn(sb[k], sq ? fb2 : fb));
-    }
-    ma = mn;
-}
-
 }  // namespace bfi

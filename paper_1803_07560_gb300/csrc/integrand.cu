@@ -23,7 +23,7 @@
 // Resident CTAs per SM the integrand kernels are compiled for (register cap
 // 65536 / (256 * this)).
 #ifndef BFI_INTEGRAND_MIN_BLOCKS
-#define BFI_INTEGRAND_MIN_BLOCKS 2
+#define BFI_INTEGRAND_MIN_BLOCKS 4
 #endif
 
 namespace bfi {
@@ -80,74 +80,6 @@ __device__ __forceinline__ ChunkView chunk_view(const IntegrandArgs &args, int64
     return v;
 }
 
-// Coordinates of sample i (Philox blocks (q, i lo, i hi, sid), q < ceil(D/4)).
-template <int D, typename Real>
-__device__ __forceinline__ void make_point(uint64_t i, uint32_t sid, const RoundKeys &rk, const Real (&box_lo)[D],
-                                           const Real (&box_w)[D], Real (&u)[D]) {
-    constexpr int NQ = (D + 3) / 4;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const uint4 wd = philox4x32_10(
-            make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
-        const uint32_t w4[4] = {wd.x, wd.y, wd.z, wd.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-            if (4 * q + t < D) u[4 * q + t] = Coord<Real>::map(w4[t], box_lo[4 * q + t], box_w[4 * q + t]);
-    }
-}
-
-// Warp butterfly, then the warps in order; thread 0 writes [cnt, m, sums].
-template <int K, int R, int WARPS>
-__device__ __forceinline__ void write_chunk_record(double m, double (&rec)[K], double (*s_rec)[K + 1], double *out,
-                                                   uint64_t cnt) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        double other[K];
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) other[kk] = __shfl_xor_sync(0xffffffffu, rec[kk], off);
-        const double mo = __shfl_xor_sync(0xffffffffu, m, off);
-        merge_record<K, R>(m, rec, mo, other);
-    }
-    if (lane == 0) {
-        s_rec[warp][0] = m;
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) s_rec[warp][1 + kk] = rec[kk];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double mb = s_rec[0][0];
-        double rb[K];
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) rb[kk] = s_rec[0][1 + kk];
-        for (int wv = 1; wv < WARPS; ++wv) {
-            double ro[K];
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) ro[kk] = s_rec[wv][1 + kk];
-            merge_record<K, R>(mb, rb, s_rec[wv][0], ro);
-        }
-        out[0] = static_cast<double>(cnt);
-        out[1] = mb;
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) out[2 + kk] = rb[kk];
-    }
-    __syncthreads();
-}
-
-// Adds one weighted sample to the per-thread sums.
-template <typename Real, int K, int R>
-__device__ __forceinline__ void accumulate(ThreadSums<Real, K> &acc, Real w, const Real (&Q)[R]) {
-    acc.add(0, w);
-    acc.add(1, w * w);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const Real wq = w * Q[r];
-        acc.add(2 + r, wq);
-        acc.add(2 + R + r, w * wq);
-        acc.add(2 + 2 * R + r, wq * wq);
-    }
-}
-
 // S of Eq. (Gen2): the residual sum of squares plus the optional mass term.
 template <int NX, int NT, typename Real>
 __device__ __forceinline__ Real action(const Real (&u)[NX * NT], const LatticeConst<Real> &c) {
@@ -173,6 +105,27 @@ __device__ __forceinline__ void sample_words(uint64_t i, uint32_t sid, const Rou
 #pragma unroll
         for (int t = 0; t < 4; ++t)
             if (4 * q + t < D) w[4 * q + t] = w4[t];
+    }
+}
+
+// FP32 coordinates of sample i from the (lo, width) pairs in shared memory.
+template <int D>
+__device__ __forceinline__ void make_point_smem(uint64_t i, uint32_t sid, const RoundKeys &rk, const float2 *box,
+                                                float (&u)[D]) {
+    constexpr int NQ = (D + 3) / 4;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint4 b = philox4x32_10(
+            make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
+        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = 4 * q + t;
+            if (j < D) {
+                const float2 bw = box[j];
+                u[j] = Coord<float>::map(w4[t], bw.x, bw.y);
+            }
+        }
     }
 }
 
@@ -203,34 +156,176 @@ __device__ __forceinline__ void add_evaluated(unsigned long long *stats, unsigne
 // largest weight is 1).  Both kernels leave those samples out of the
 // products, the weight and the sums.  The reference point m_ref is the
 // per-subvolume hint (the smallest FP32 action among the first samples) and
-// then the smallest action evaluated so far, shared across the CTA every
-// kShareRows rows; it is always the action of an evaluated sample, so it is
-// never below the final shift.
+// then the smallest action evaluated so far: shared across the warp after
+// every row of samples and across the CTA every kShareRows rows, at fixed
+// points, so every decision is reproducible.  m_ref is always the action of
+// an evaluated sample (or within FP32 error of one), never far below the
+// final shift.
+//
+// Shift.  Both kernels accumulate w = exp(m_acc - S) with m_acc starting at
+// the hint and moving down only when a sample beats it by more than
+// kRescaleMargin, so the sums are rescaled a handful of times and the
+// threads of a CTA mostly share one shift (cheap merges).  w <= e^16.
+//
+// Sums.  The per-thread sums live in shared memory ([k][thread], no bank
+// conflicts); they are touched only by the few samples that pass the screen,
+// which keeps the registers of the hot loop (Philox, point, FP32 action) low
+// enough for three CTAs per SM.
 // ---------------------------------------------------------------------------
-constexpr int kShareRows = 16;
+constexpr int kShareRows = 64;
+constexpr float kRescaleMargin = 16.f;
+
+__device__ __forceinline__ float warp_min(float x) {
+    return __int_as_float(static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(__float_as_int(x)))));
+}
+
+// Per-thread sums in shared memory: element k of thread t at buf[k * BLOCK + t].
+template <typename Real, int K, int BLOCK>
+struct SmemSums;
+
+template <int K, int BLOCK>
+struct SmemSums<float, K, BLOCK> {  // first-order sums Kahan-compensated
+    static constexpr int R = (K - 2) / 3;
+    static constexpr int NC = 1 + R;
+    static constexpr int WORDS = K + NC;
+    float *b;
+    __device__ __forceinline__ static bool compensated(int k) { return k == 0 || (k >= 2 && k < 2 + R); }
+    __device__ __forceinline__ static int cidx(int k) { return K + (k == 0 ? 0 : k - 1); }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < WORDS; ++k) b[k * BLOCK] = 0.f;
+    }
+    __device__ __forceinline__ void add(int k, float x) {
+        if (compensated(k)) {
+            const float sk = b[k * BLOCK], ck = b[cidx(k) * BLOCK];
+            const float y = x - ck;
+            const float t = sk + y;
+            b[cidx(k) * BLOCK] = (t - sk) - y;
+            b[k * BLOCK] = t;
+        } else {
+            b[k * BLOCK] += x;
+        }
+    }
+    __device__ __forceinline__ void scale(int k, float f) {
+        b[k * BLOCK] *= f;
+        if (compensated(k)) b[cidx(k) * BLOCK] *= f;
+    }
+    __device__ __forceinline__ double value(int k) const {
+        return compensated(k) ? static_cast<double>(b[k * BLOCK]) - static_cast<double>(b[cidx(k) * BLOCK])
+                              : static_cast<double>(b[k * BLOCK]);
+    }
+};
+
+template <int K, int BLOCK>
+struct SmemSums<double, K, BLOCK> {
+    static constexpr int WORDS = K;
+    double *b;
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) b[k * BLOCK] = 0.0;
+    }
+    __device__ __forceinline__ void add(int k, double x) { b[k * BLOCK] += x; }
+    __device__ __forceinline__ void scale(int k, double f) { b[k * BLOCK] *= f; }
+    __device__ __forceinline__ double value(int k) const { return b[k * BLOCK]; }
+};
+
+// The CTA's record of a chunk, [cnt, m, sums...], reduced straight from the
+// shared-memory sums: the CTA shift m_b is the smallest thread shift; each
+// thread's factor exp(m_b - m_t) (1 when equal, the common case) goes to
+// s_f; then warp w sums elements k = w, w + WARPS, ... over all threads, lane
+// l taking threads l, l + 32, ... in order and the lanes combining in a fixed
+// butterfly.  Every order is fixed, so the record is reproducible.
+template <typename Real, int K, int R, int BLOCK>
+__device__ __forceinline__ void chunk_record(const SmemSums<Real, K, BLOCK> &acc, double m_t, double *s_f,
+                                             double *s_mb, double *out, uint64_t cnt) {
+    constexpr int WARPS = BLOCK / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_f[tid] = m_t;
+    __syncthreads();
+    if (warp == 0) {
+        double mn = INFINITY;
+        for (int t = lane; t < BLOCK; t += 32) mn = fmin(mn, s_f[t]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+        if (lane == 0) *s_mb = mn;
+    }
+    __syncthreads();
+    const double mb = *s_mb;
+    s_f[tid] = (m_t == INFINITY) ? 0.0 : (m_t == mb ? 1.0 : exp(mb - m_t));
+    __syncthreads();
+    const Real *base = acc.b - tid;  // element k of thread t: sums of thread t
+    for (int k = warp; k < K; k += WARPS) {
+        const bool sq = second_order(k, R);
+        double part = 0.0;
+        for (int t = lane; t < BLOCK; t += 32) {
+            SmemSums<Real, K, BLOCK> other{const_cast<Real *>(base) + t};
+            const double f = s_f[t];
+            part = __dadd_rn(part, __dmul_rn(other.value(k), sq ? f * f : f));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) part = __dadd_rn(part, __shfl_xor_sync(0xffffffffu, part, off));
+        if (lane == 0) out[2 + k] = part;
+    }
+    if (tid == 0) {
+        out[0] = static_cast<double>(cnt);
+        out[1] = mb;
+    }
+    __syncthreads();
+}
+
+template <typename Real, int K, int R, int BLOCK>
+__device__ __forceinline__ void accumulate(SmemSums<Real, K, BLOCK> &acc, Real w, const Real (&Q)[R]) {
+    acc.add(0, w);
+    acc.add(1, w * w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const Real wq = w * Q[r];
+        acc.add(2 + r, wq);
+        acc.add(2 + R + r, w * wq);
+        acc.add(2 + 2 * R + r, wq * wq);
+    }
+}
+
+template <typename Real, int K, int R, int BLOCK>
+__device__ __forceinline__ void rescale(SmemSums<Real, K, BLOCK> &acc, Real f) {
+    const Real f2 = f * f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc.scale(k, second_order(k, R) ? f2 : f);
+}
+
+// Shared state of one CTA for one chunk.
+template <int BLOCK>
+struct ChunkShared {
+    double f[BLOCK];  // per-thread shift factors of the chunk record
+    double mb;
+    int min_bits;
+    unsigned evaluated;
+};
 
 // ---------------------------------------------------------------------------
 // FP64 integrand, thread per sample.  One CTA processes chunks blockIdx.x,
 // blockIdx.x + gridDim.x, ...; within a chunk thread t takes samples
 // first + t, first + t + B, ...  Each sample is first screened with its FP32
-// action on the FP32 point (cheap pipes); only samples that may carry weight
+// action on the FP32 point (fast pipes); only samples that may carry weight
 // (within skip_window of m_ref, plus a margin of 1 + 1% of S, far above the
-// FP32 error of ~1e-4) are evaluated in FP64: FP64 point, action, products,
-// weight.  The FP64 shift is the thread's running minimum of S.
+// ~1e-4 FP32 error) are evaluated in FP64: the Philox words are drawn again,
+// then FP64 point, action, products and weight.
 // ---------------------------------------------------------------------------
 template <int NX, int NT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64(const IntegrandArgs args, const LatticeConst<double> lc,
-                                                       const LatticeConst<float> lcf, const RoundKeys rk) {
+__global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64(const IntegrandArgs args,
+                                                                                 const LatticeConst<double> lc,
+                                                                                 const LatticeConst<float> lcf,
+                                                                                 const RoundKeys rk) {
     constexpr int D = NX * NT;
     constexpr int R = NX / 2 + 1;
     constexpr int K = sum_count(R);
     constexpr int WARPS = BLOCK / 32;
-    __shared__ double s_rec[WARPS][K + 1];
+    __shared__ ChunkShared<BLOCK> sh;
     __shared__ double s_lo[D], s_w[D];
     __shared__ float2 s_box[D];  // the same bounds as floats, for the FP32 screen
-    __shared__ int s_min;
-    __shared__ unsigned s_cnt;
+    __shared__ double s_sums[K * BLOCK];
     const int tid = threadIdx.x;
+    SmemSums<double, K, BLOCK> acc{s_sums + tid};
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
         const ChunkView v = chunk_view(args, c, D);
@@ -239,28 +334,27 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64
             s_w[tid] = v.hi[tid] - v.lo[tid];
             BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
         }
-        float m_ref = args.hint[v.s];
+        const float hint = args.hint[v.s];
+        float m_ref = hint;
+        double m_acc = static_cast<double>(hint);
         if (tid == 0) {
-            s_min = __float_as_int(m_ref);
-            s_cnt = 0u;
+            sh.min_bits = __float_as_int(hint);
+            sh.evaluated = 0u;
         }
+        acc.zero();
         __syncthreads();
 
-        ThreadSums<double, K> acc;
-        acc.zero();
-        double m_t = INFINITY;
         unsigned n_eval = 0;
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
             if (k < v.cnt) {
-                uint32_t w[D];
-                sample_words<D>(v.first + k, v.sid, rk, w);
                 float uf[D];
-#pragma unroll
-                for (int j = 0; j < D; ++j) uf[j] = Coord<float>::map(w[j], s_box[j].x, s_box[j].y);
+                make_point_smem<D>(v.first + k, v.sid, rk, s_box, uf);
                 const float S_f = action<NX, NT, float>(uf, lcf);
                 if (S_f <= m_ref + args.skip_window + 1.0f + 0.01f * S_f) {
+                    uint32_t w[D];
+                    sample_words<D>(v.first + k, v.sid, rk, w);
                     double u[D];
 #pragma unroll
                     for (int j = 0; j < D; ++j) u[j] = Coord<double>::map(w[j], s_lo[j], s_w[j]);
@@ -268,54 +362,47 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64
                     m_ref = fminf(m_ref, __double2float_rn(S));
                     double Q[R];
                     products<NX, NT, double>(u, Q);
-                    if (S < m_t) {  // new smallest action: move the shift down
-                        const double f = exp(S - m_t);
-                        const double f2 = f * f;
-#pragma unroll
-                        for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
-                        m_t = S;
+                    if (S < m_acc - kRescaleMargin) {  // rare: move the shift down
+                        rescale<double, K, R, BLOCK>(acc, exp(S - m_acc));
+                        m_acc = S;
                     }
-                    accumulate<double, K, R>(acc, exp(m_t - S), Q);
+                    accumulate<double, K, R, BLOCK>(acc, exp(m_acc - S), Q);
                     ++n_eval;
                 }
             }
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&s_min, m_ref);
+            m_ref = warp_min(m_ref);
+            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&sh.min_bits, m_ref);
         }
-        add_evaluated(args.stats, n_eval, &s_cnt);
-        double rec[K];
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) rec[kk] = acc.value(kk);
-        write_chunk_record<K, R, WARPS>(m_t, rec, s_rec, args.partials + c * (K + 2), v.cnt);
+        add_evaluated(args.stats, n_eval, &sh.evaluated);
+        chunk_record<double, K, R, BLOCK>(acc, m_acc, sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
     }
 }
 
 // ---------------------------------------------------------------------------
 // FP32 integrand.  Points, action, products and weights in float; per-thread
-// Kahan sums; merges in double.  Besides the negligible-weight rule above, two
-// things keep it within ~1e-7 of the FP64 result on the same points:
-//  * the shift m_acc starts at the per-subvolume hint and moves only when a
-//    sample beats it by more than kRescaleMargin, so the sums are rescaled a
-//    handful of times;
-//  * a sample whose FP32 action lies within kRefineWindow of m_ref (the
-//    weights that matter) gets its action recomputed in compensated FP32
-//    (action_df); all others have weights below e^-kRefineWindow of the
-//    largest, where the ~1e-5 FP32 action error is harmless.
+// Kahan sums; merges in double.  Besides the rules above, a sample whose
+// FP32 action lies within kRefineWindow of m_ref (the weights that matter)
+// gets its action recomputed in compensated FP32 (action_df); all others have
+// weights below e^-kRefineWindow of the largest, where the ~1e-5 FP32 action
+// error is harmless.
 // ---------------------------------------------------------------------------
 constexpr float kRefineWindow = 28.f;
-constexpr float kRescaleMargin = 16.f;
 
 template <int NX, int NT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f32(const IntegrandArgs args, const LatticeConst<float> lc,
-                                                       const LatticeConstDF lcd, const RoundKeys rk) {
+__global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f32(const IntegrandArgs args,
+                                                                                 const LatticeConst<float> lc,
+                                                                                 const LatticeConstDF lcd,
+                                                                                 const RoundKeys rk) {
     constexpr int D = NX * NT;
     constexpr int R = NX / 2 + 1;
     constexpr int K = sum_count(R);
     constexpr int WARPS = BLOCK / 32;
-    __shared__ double s_rec[WARPS][K + 1];
+    using Sums = SmemSums<float, K, BLOCK>;
+    __shared__ ChunkShared<BLOCK> sh;
     __shared__ float2 s_box[D];  // (lo, width) as floats; every thread reads the same word
-    __shared__ int s_min;
-    __shared__ unsigned s_cnt;
+    __shared__ float s_sums[Sums::WORDS * BLOCK];
     const int tid = threadIdx.x;
+    Sums acc{s_sums + tid};
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
         const ChunkView v = chunk_view(args, c, D);
@@ -323,23 +410,19 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f32
         const float hint = args.hint[v.s];
         float m_acc = hint, m_ref = hint;
         if (tid == 0) {
-            s_min = __float_as_int(hint);
-            s_cnt = 0u;
+            sh.min_bits = __float_as_int(hint);
+            sh.evaluated = 0u;
         }
+        acc.zero();
         __syncthreads();
 
-        ThreadSums<float, K> acc;
-        acc.zero();
         unsigned n_eval = 0;
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
             if (k < v.cnt) {
-                uint32_t w[D];
-                sample_words<D>(v.first + k, v.sid, rk, w);
                 float u[D];
-#pragma unroll
-                for (int j = 0; j < D; ++j) u[j] = Coord<float>::map(w[j], s_box[j].x, s_box[j].y);
+                make_point_smem<D>(v.first + k, v.sid, rk, s_box, u);
                 const float S_f = action<NX, NT, float>(u, lc);
                 if (S_f <= m_ref + args.skip_window) {
                     DF S{S_f, 0.f};
@@ -348,25 +431,21 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f32
                         m_ref = fminf(m_ref, S.h);
                     }
                     if (S.h < m_acc - kRescaleMargin) {  // rare: move the shift down
-                        const float f = expf(S.h - m_acc);
-                        const float f2 = f * f;
-#pragma unroll
-                        for (int kk = 0; kk < K; ++kk) acc.scale(kk, second_order(kk, R) ? f2 : f);
+                        rescale<float, K, R, BLOCK>(acc, expf(S.h - m_acc));
                         m_acc = S.h;
                     }
                     float Q[R];
                     products<NX, NT, float>(u, Q);
-                    accumulate<float, K, R>(acc, expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l)), Q);
+                    accumulate<float, K, R, BLOCK>(acc, expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l)), Q);
                     ++n_eval;
                 }
             }
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&s_min, m_ref);
+            m_ref = warp_min(m_ref);
+            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&sh.min_bits, m_ref);
         }
-        add_evaluated(args.stats, n_eval, &s_cnt);
-        double rec[K];
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) rec[kk] = acc.value(kk);
-        write_chunk_record<K, R, WARPS>(static_cast<double>(m_acc), rec, s_rec, args.partials + c * (K + 2), v.cnt);
+        add_evaluated(args.stats, n_eval, &sh.evaluated);
+        chunk_record<float, K, R, BLOCK>(acc, static_cast<double>(m_acc), sh.f, &sh.mb, args.partials + c * (K + 2),
+                                         v.cnt);
     }
 }
 
@@ -379,18 +458,18 @@ __global__ void __launch_bounds__(kBlock) hint_f32(const IntegrandArgs args, con
                                                    const RoundKeys rk) {
     constexpr int D = NX * NT;
     __shared__ int s_min;
+    __shared__ float2 s_box[D];
     const int64_t s = blockIdx.x;
     if (threadIdx.x == 0) s_min = __float_as_int(INFINITY);
+    if (threadIdx.x < D) BoxPair<float>::load(args.lo + s * D, args.hi + s * D, threadIdx.x, s_box[threadIdx.x].x,
+                                              s_box[threadIdx.x].y);
     __syncthreads();
     const uint64_t n = min(args.samples[s], static_cast<uint64_t>(kHintSamples));
     const uint32_t sid = args.sub_id ? args.sub_id[s] : static_cast<uint32_t>(s);
-    float box_lo[D], box_w[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) BoxPair<float>::load(args.lo + s * D, args.hi + s * D, j, box_lo[j], box_w[j]);
     float mn = INFINITY;
     for (uint64_t k = threadIdx.x; k < n; k += blockDim.x) {
         float u[D];
-        make_point<D, float>(k, sid, rk, box_lo, box_w, u);
+        make_point_smem<D>(k, sid, rk, s_box, u);
         mn = fminf(mn, action<NX, NT, float>(u, lc));
     }
     atomicMin(&s_min, __float_as_int(mn));

@@ -5,7 +5,7 @@ sums that can cancel (those with P_r, |P_r| <= P_0 per sample) are measured
 against their P_0 counterpart; C(r) within 1e-12 of C(0).  FP32 mode is
 compared with the oracle's FP32-points mode (the identical float points
 evaluated in FP64), within FP32_RTOL = 1e-6, the bound the FP32 path states.
-The records of the two sides may use different shifts m_s (FP32 starts from
+The records of the two sides use different shifts m_s (the device starts from
 a hint), so sums are compared after moving them to the oracle's shift.
 Statistical error estimates are variances that cancel (to ~0 when one sample
 dominates); they are compared at 1e-9 relative (FP64), or absolutely at that
@@ -56,12 +56,13 @@ def run_oracle(job, fp32_points=False, nonlinear=1.0, mass2=0.0):
                             sub_id=job.sub_id, fp32_points=fp32_points)
 
 
-def assert_slots_close(g, o, R, rtol, rtol_var, same_shift=True):
+def assert_slots_close(g, o, R, rtol, rtol_var):
     assert np.array_equal(g[:, 0], o[:, 0]), "sample counts differ"
     used = o[:, 0] > 0
     g, o = g[used], o[used]
-    if same_shift:  # FP64: both shifts are the smallest action of the subvolume
-        np.testing.assert_allclose(g[:, 1], o[:, 1], rtol=rtol, atol=rtol)
+    # the device shift starts at a hint and moves only when beaten by more than
+    # 16: it lies within [min S - 1e-3, min S + 16] (the oracle's is min S)
+    assert np.all(g[:, 1] >= o[:, 1] - 1e-3) and np.all(g[:, 1] <= o[:, 1] + 16.0 + 1e-3)
     np.testing.assert_allclose(g[:, 2], o[:, 2], rtol=1e-14, atol=1e-14)    # log V_s
     dm = g[:, 1] - o[:, 1]                                                  # express GPU sums in the oracle's shift
     f1, f2 = np.exp(-dm)[:, None], np.exp(-2 * dm)[:, None]
@@ -161,7 +162,7 @@ def test_integrate_fp32_against_fp32_points(bfi, dev, nx, nt):
     g_s, g_t, _ = run_gpu(bfi, dev, job, 1)
     o_s, o_t = run_oracle(job, fp32_points=True)
     R = nx // 2 + 1
-    assert_slots_close(g_s, o_s, R, FP32_RTOL, 1e-4, same_shift=False)
+    assert_slots_close(g_s, o_s, R, FP32_RTOL, 1e-4)
     assert_totals_close(g_t, o_t, R, FP32_RTOL, 1e-4, FP32_ERR_ATOL)
 
 
@@ -229,7 +230,7 @@ def test_paper_10x2_full_size_sampled(bfi, dev, precision):
     pick = [0, 517, 1023]
     o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision))
     tol = FP64_RTOL if precision == 0 else FP32_RTOL
-    assert_slots_close(g_s[pick], o_s, 6, tol, 1e-9 if precision == 0 else 1e-4, same_shift=precision == 0)
+    assert_slots_close(g_s[pick], o_s, 6, tol, 1e-9 if precision == 0 else 1e-4)
     # totals: the device merge of all 1024 records equals the oracle's merge of them
     o_t = oracle.merge(10, g_s)
     assert_totals_close(g_t, o_t, 6, 1e-13, 1e-9)
