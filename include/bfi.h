@@ -189,6 +189,32 @@ bfi_status bfi_plan_set_timing(bfi_plan *plan, int enable);
 bfi_status bfi_plan_get_stats(bfi_plan *plan, uint64_t *evaluated, float *skip_window);
 bfi_status bfi_plan_get_timing(bfi_plan *plan, float *ms);
 
+/* The whole integration without allocating anything, for callers that
+ * cannot call cudaMalloc: for example a plugin inside a host application
+ * whose memory manager owns the device heap, or a latency-critical loop where
+ * an allocation and the synchronisation it may bring are not allowed after
+ * start-up.  The paper has no counterpart; this is a deployment variant of
+ * bfi_plan_create + bfi_plan_execute + bfi_plan_destroy with the same kernels,
+ * chunking and results.
+ *   samples          host [nsub]; keep it unchanged until 'stream' has passed
+ *                    the call (pageable memory is copied before the call returns)
+ *   lo, hi, sub_id, seed, job_id, slots, totals   as for bfi_plan_execute
+ *   stream           cudaStream_t of the current device
+ * The scratch is one 16 MiB device array that every device that loads the
+ * library holds until the process exits; a job whose chunk records, chunk
+ * table and hints need more is rejected with BFI_E_INVALID and a message
+ * giving both sizes.  The first call on a device looks up the array's device
+ * address (once per device); make that first call before any stream capture.
+ * Every call uses the same array and leaves its contents behind; each call
+ * clears what has to start at zero.  Calls whose work overlaps on the GPU
+ * (other streams, other threads) race on the array: serialise them.
+ * Asynchronous like bfi_plan_execute.  Errors: BFI_E_INVALID,
+ * BFI_E_UNSUPPORTED, BFI_E_CUDA. */
+bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, int64_t nsub, const uint64_t *samples,
+                                        const double *lo, const double *hi, const uint32_t *sub_id,
+                                        uint32_t seed, uint32_t job_id, bfi_precision precision,
+                                        double *slots, double *totals, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* One-call integration with host buffers (the end-to-end path).            */
 /* ------------------------------------------------------------------------ */

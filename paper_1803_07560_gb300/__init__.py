@@ -66,6 +66,9 @@ _SIGNATURES = {
     "bfi_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bfi_plan_get_timing": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "bfi_plan_get_stats": (ctypes.c_int, [_vp, _P(ctypes.c_uint64), _P(ctypes.c_float)]),
+    "bfi_integrate_static_scratch": (ctypes.c_int, [_P(Lattice), ctypes.c_int64, _P(ctypes.c_uint64), _vp,
+                                                    _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                                    _vp, _vp, _vp]),
     "bfi_ctx_create": (ctypes.c_int, [_P(_vp), ctypes.c_int]),
     "bfi_ctx_destroy": (ctypes.c_int, [_vp]),
     "bfi_integrate": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, _vp,
@@ -234,6 +237,28 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def integrate_static_scratch(lat: Lattice, samples, lo, hi, seed: int, job_id: int = 0, sub_id=None,
+                             precision: int = FP64, slots=None, totals=None, stream=None):
+    """The whole integration without any allocation by the library: its
+    scratch is a fixed 16 MiB device array, for callers that cannot allocate
+    device memory.  Inputs and outputs are the caller's CUDA tensors (allocated
+    here only if not given).  Calls that overlap on the GPU race on the
+    shared scratch; the first call on a device should precede stream capture."""
+    import torch
+    smp = np.ascontiguousarray(np.atleast_1d(samples), dtype=np.uint64)
+    nsub = int(smp.size)
+    if slots is None:
+        slots = torch.empty((nsub, slot_len(lat.nx)), dtype=torch.float64, device=lo.device)
+    if totals is None:
+        totals = torch.empty(totals_len(lat.nx), dtype=torch.float64, device=lo.device)
+    _check(_lib.bfi_integrate_static_scratch(
+        ctypes.byref(lat), nsub, smp.ctypes.data_as(_P(ctypes.c_uint64)), _dev_ptr(lo, torch.float64),
+        _dev_ptr(hi, torch.float64), _dev_ptr(sub_id, torch.int32) if sub_id is not None else None,
+        seed & 0xFFFFFFFF, job_id & 0xFFFFFFFF, precision, _dev_ptr(slots, torch.float64),
+        _dev_ptr(totals, torch.float64), _stream_ptr(stream)))
+    return slots, totals
 
 
 def merge_host(nx: int, slots) -> np.ndarray:

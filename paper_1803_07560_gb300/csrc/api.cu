@@ -3,6 +3,7 @@
 // host-buffer path, the host FP64 merge and the single-step entry points.
 #include "bfi.h"
 #include "bfi_device.cuh"
+#include "bfi_host.h"
 #include "bfi_kernels.h"
 
 #include <atomic>
@@ -88,6 +89,16 @@ float negligible_window(bfi_precision precision, uint64_t n_max) {
 }
 
 }  // namespace
+
+namespace bfi {
+bfi_status set_error(bfi_status status, const char *message) {
+    g_last_error = message;
+    return status;
+}
+bfi_status validate_lattice(const bfi_lattice *lattice) { return check_lattice(lattice); }
+int64_t plan_chunk_samples(uint64_t total) { return choose_chunk_samples(total); }
+float plan_negligible_window(bfi_precision precision, uint64_t n_max) { return negligible_window(precision, n_max); }
+}  // namespace bfi
 
 struct bfi_plan {
     int device = 0;
