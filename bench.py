@@ -39,26 +39,56 @@ R = NX // 2 + 1
 K = 2 + 3 * R
 FP32_SAMPLES_PER_SUB = 1 << 24      # the 2^34-point FP32 form of the same job
 
-# Peaks (derived from the unit counts and clocks of GB300).
+# Peaks, from GB300's unit counts (152 SMs; per SM and clock: 128 FP32/INT
+# lanes, i.e. 4 warp-instructions, and 2 FP64 FMA lanes, the figures ncu
+# reports as peak_sustained for ffma and dfma) at the 2070 MHz maximum clock.
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-FP64_PEAK_OPS = 1.25e12 / 2         # nominal 1.25 TFLOP/s FP64 = 6.25e11 FMA/s
-ISSUE_PEAK_OPS = 4 * 32 * SM_COUNT * SM_MAX_MHZ * 1e6   # thread-instructions/s
+ISSUE_PEAK_OPS = 128 * SM_COUNT * SM_MAX_MHZ * 1e6   # thread-instructions/s (FP32/INT lanes)
+FP64_PEAK_OPS = 2 * SM_COUNT * SM_MAX_MHZ * 1e6      # FP64 operations/s
 
 
-def ops_per_sample_fp64(nx, nt):
-    """Algorithmic FP64 operations per sample (Philox runs on the integer pipes)."""
+def screen_ops(nx, nt):
+    """Per sample, every sample: Philox words, FP32 point, FP32 action."""
+    d = nx * nt
+    return ((d + 3) // 4) * 10 * 4 + 2 * d + 8 * d
+
+
+def eval_ops_fp64(nx, nt):
+    """Per evaluated sample (FP64 mode): (FP64 operations, integer operations)."""
     d, r = nx * nt, nx // 2 + 1
     k = 2 + 3 * r
-    return d + 8 * d + d * r + 1 + 2 * k
+    return 2 * d + 8 * d + d * r + 1 + 2 * k, ((d + 3) // 4) * 10 * 4
 
 
-def ops_per_sample_fp32(nx, nt):
-    """Algorithmic thread operations per sample in the FP32 form."""
+def eval_ops_fp32(nx, nt):
+    """Per evaluated sample (FP32 mode): products, weight, compensated sums."""
     d, r = nx * nt, nx // 2 + 1
     k = 2 + 3 * r
-    philox = ((d + 3) // 4) * 10 * 4
-    return philox + 2 * d + 8 * d + d * r + 2 + 5 * k
+    return d * r + 2 + 4 * k
+
+
+def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2):
+    """Algorithmic work of one launch against the binding resource."""
+    t = kern_ms * 1e-3
+    if precision == "fp64":
+        dp, integer = eval_ops_fp64(nx, nt)
+        w_issue = n * screen_ops(nx, nt) + n_eval * integer
+        w_dp = n_eval * dp
+    else:
+        w_issue = n * screen_ops(nx, nt) + n_eval * eval_ops_fp32(nx, nt)
+        w_dp = 0
+    t_issue, t_dp = w_issue / ISSUE_PEAK_OPS, w_dp / FP64_PEAK_OPS
+    if t_issue >= t_dp:
+        bound, achieved, peak = "alu", w_issue / t, ISSUE_PEAK_OPS
+    else:
+        bound, achieved, peak = "alu-fp64", w_dp / t, FP64_PEAK_OPS
+    return {"bound": "alu", "resource": "FP32/INT issue" if bound == "alu" else "FP64 pipe",
+            "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
+            "traffic": None, "kernel_ms": kern_ms, "samples": n, "evaluated": n_eval,
+            "issue_frac": w_issue / t / ISSUE_PEAK_OPS, "fp64_frac": w_dp / t / FP64_PEAK_OPS,
+            "screen_ops_per_sample": screen_ops(nx, nt),
+            "peak_source": "unit counts x 2070 MHz (DESIGN.md)"}
 
 
 def rank_info():
@@ -204,7 +234,7 @@ def timed_steps(plan, lo, hi, sid, job, steps, warmup, flush_buf, dist, stream):
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    return total_ms / steps, kern_ms / steps, slots, totals
+    return total_ms / steps, kern_ms / steps, slots, totals, plan.stats()[0]
 
 
 def run_bfi(args):
@@ -233,8 +263,8 @@ def run_bfi(args):
     plan = bfi.Plan(lat, job.samples, bfi.FP64, device=local_rank)
     info = plan.info()
     sampler = ClockSampler(local_rank) if rank == 0 else None
-    ms, kern_ms, slots, totals = timed_steps(plan, lo, hi, sid, job, args.steps, args.warmup, flush_buf,
-                                             dist, stream)
+    ms, kern_ms, slots, totals, n_eval = timed_steps(plan, lo, hi, sid, job, args.steps, args.warmup,
+                                                     flush_buf, dist, stream)
     clocks = sampler.stop() if sampler else None
 
     # the exchange: gather every rank's subvolume records, merge on rank 0
@@ -251,26 +281,34 @@ def run_bfi(args):
 
     samples_all = world * job.total_samples
     value = samples_all / (ms * 1e-3)
-    kern_ops = job.total_samples * ops_per_sample_fp64(NX, NT)
-    achieved = kern_ops / (kern_ms * 1e-3)
+    roof = roofline(job.total_samples, n_eval, kern_ms, "fp64")
+    roof["kernel"] = "hint_f32<10,2> + integrand_f64<10,2>"
 
     # ---- FP32 form of the same job with 2^24 points per subvolume ----
     fp32 = None
     if not args.skip_fp32:
         job32 = make_job(rank, world, 1 << (args.samples_log2 + 4))
         plan32 = bfi.Plan(lat, job32.samples, bfi.FP32, device=local_rank)
-        ms32, kern32, _, tot32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
-                                             max(1, args.warmup // 2), flush_buf, dist, stream)
-        ach32 = job32.total_samples * ops_per_sample_fp32(NX, NT) / (kern32 * 1e-3)
+        ms32, kern32, _, tot32, n_eval32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
+                                                       max(1, args.warmup // 2), flush_buf, dist, stream)
+        roof32 = roofline(job32.total_samples, n_eval32, kern32, "fp32")
+        roof32["kernel"] = "hint_f32<10,2> + integrand_f32<10,2>"
+        plan32.close()
+        # the same 2^34-point job in FP64 mode (its own FP64 points): the FP32
+        # result's total difference, arithmetic plus point rounding
+        plan64 = bfi.Plan(lat, job32.samples, bfi.FP64, device=local_rank)
+        _, tot64 = plan64.execute(lo, hi, job32.seed, job32.job_id, sub_id=sid, stream=stream)
+        torch.cuda.synchronize()
+        plan64.close()
+        t32, t64 = tot32.cpu().numpy(), tot64.cpu().numpy()
         fp32 = {"value": world * job32.total_samples / (ms32 * 1e-3), "unit": "samples/s",
                 "ms_per_step": ms32, "samples_per_subvolume": int(job32.samples[0]),
-                "dtype": "f32 (compensated sums, f64 shift and merge)",
-                "roofline": {"bound": "alu", "achieved": ach32 / 1e9, "peak": ISSUE_PEAK_OPS / 1e9,
-                             "unit": "Gop/s", "frac": ach32 / ISSUE_PEAK_OPS, "traffic": None,
-                             "kernel": "hint_f32<10,2> + integrand_f32<10,2>", "kernel_ms": kern32,
-                             "ops_per_sample": ops_per_sample_fp32(NX, NT)},
-                "logZ": float(tot32[0].item())}
-        plan32.close()
+                "dtype": "f32 (compensated sums, f64 shift and merge)", "roofline": roof32,
+                "logZ": float(t32[0]), "C": [float(x) for x in t32[4:4 + R]],
+                "vs_fp64_mode": {"Z_rel": float(np.expm1(t32[0] - t64[0])),
+                                 "C_rel_to_C0": [float(x) for x in (t32[4:4 + R] - t64[4:4 + R]) / t64[4]],
+                                 "note": "FP64 mode draws FP64 points; the FP32 arithmetic bound (1e-6) is "
+                                         "checked against the oracle on the same float points in the tests"}}
 
     # ---- end to end through the host-buffer C-ABI call ----
     e2e = None
@@ -282,7 +320,7 @@ def run_bfi(args):
         samples, times, cores = time_oracle(1)
         cpu = {"value": samples / times[0], "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": "32 of the 1024 subvolumes (every 32nd) x 2^20 points of the same job, FP64 oracle"}
-    report(args, rank, world, value, ms, achieved, kern_ms, cpu, e2e, clocks, info, merged, fp32, job)
+    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -318,21 +356,17 @@ def run_e2e(bfi, lat, job, local_rank, args, dist, dev, samples_all):
             "d2h_bytes_per_step": d2h}
 
 
-def report(args, rank, world, value, ms, achieved, kern_ms, cpu, e2e, clocks, info, merged, fp32, job):
+def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job):
     if rank == 0:
         line = {
             "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(world, int(job.samples[0])),
-            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9,
-                         "unit": "Gop/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
-                         "kernel": "integrand_f64<10,2>", "kernel_ms": kern_ms,
-                         "ops_per_sample": ops_per_sample_fp64(NX, NT),
-                         "peak_source": "nominal FP64 1.25 TFLOP/s (FMA = 2 flops)"},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 4 * args.steps,
             "clocks": clocks,
             "plan": {"grid": info.grid, "block": info.block, "chunks": info.chunks,
                      "chunk_samples": info.chunk_samples},

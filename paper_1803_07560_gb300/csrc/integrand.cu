@@ -303,13 +303,50 @@ struct ChunkShared {
 };
 
 // ---------------------------------------------------------------------------
+// Candidate queues.  The few samples that pass the screen are not evaluated
+// where they are found (one or two lanes of a warp, which on GB300's FP64
+// pipe, 2 lanes per SM and clock, would hold the whole warp for the full
+// warp-width cost of every FP64 instruction).  Each warp appends its
+// candidates, in (row, lane) order, to its own queue in shared memory and
+// evaluates them 32 at a time with every lane busy; the remainder is
+// evaluated at the end of the chunk.  Lane l always takes queue entry l, so
+// which lane accumulates which sample, and in what order, is fixed.
+// ---------------------------------------------------------------------------
+constexpr int kQueueCap = 64;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Appends this lane's candidate (if any) to the warp's queue; returns the new
+// count.  Needs count < 32 on entry (then count < 64 = kQueueCap on exit).
+__device__ __forceinline__ int enqueue(uint32_t *q, int count, bool cand, uint32_t k) {
+    const unsigned mask = __ballot_sync(0xffffffffu, cand);
+    if (cand) q[count + __popc(mask & lanemask_lt())] = k;
+    __syncwarp();
+    return count + __popc(mask);
+}
+
+// Removes the first 32 entries after a full batch.
+__device__ __forceinline__ int dequeue32(uint32_t *q, int count) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t moved = (lane + 32 < count) ? q[lane + 32] : 0u;
+    __syncwarp();
+    if (lane + 32 < count) q[lane] = moved;
+    __syncwarp();
+    return count - 32;
+}
+
+// ---------------------------------------------------------------------------
 // FP64 integrand, thread per sample.  One CTA processes chunks blockIdx.x,
-// blockIdx.x + gridDim.x, ...; within a chunk thread t takes samples
-// first + t, first + t + B, ...  Each sample is first screened with its FP32
-// action on the FP32 point (fast pipes); only samples that may carry weight
-// (within skip_window of m_ref, plus a margin of 1 + 1% of S, far above the
-// ~1e-4 FP32 error) are evaluated in FP64: the Philox words are drawn again,
-// then FP64 point, action, products and weight.
+// blockIdx.x + gridDim.x, ...; within a chunk thread t screens samples
+// first + t, first + t + B, ... with the FP32 action of the FP32 point (fast
+// pipes).  Samples that may carry weight (within skip_window of m_ref, plus
+// a margin of 1 + 1% of S, far above the ~1e-4 FP32 error) go to the warp's
+// queue and are evaluated in FP64: Philox words drawn again, FP64 point,
+// action, products and weight.
 // ---------------------------------------------------------------------------
 template <int NX, int NT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64(const IntegrandArgs args,
@@ -324,7 +361,9 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64
     __shared__ double s_lo[D], s_w[D];
     __shared__ float2 s_box[D];  // the same bounds as floats, for the FP32 screen
     __shared__ double s_sums[K * BLOCK];
-    const int tid = threadIdx.x;
+    __shared__ uint32_t s_queue[WARPS][kQueueCap];
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint32_t *queue = s_queue[tid >> 5];
     SmemSums<double, K, BLOCK> acc{s_sums + tid};
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
@@ -345,34 +384,44 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64
         __syncthreads();
 
         unsigned n_eval = 0;
+        int count = 0;
+        // FP64 evaluation of queue entry 'lane' (a sample offset in the chunk)
+        auto evaluate = [&](uint32_t k) {
+            uint32_t w[D];
+            sample_words<D>(v.first + k, v.sid, rk, w);
+            double u[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) u[j] = Coord<double>::map(w[j], s_lo[j], s_w[j]);
+            const double S = action<NX, NT, double>(u, lc);
+            m_ref = fminf(m_ref, __double2float_rn(S));
+            double Q[R];
+            products<NX, NT, double>(u, Q);
+            if (S < m_acc - kRescaleMargin) {  // rare: move the shift down
+                rescale<double, K, R, BLOCK>(acc, exp(S - m_acc));
+                m_acc = S;
+            }
+            accumulate<double, K, R, BLOCK>(acc, exp(m_acc - S), Q);
+            ++n_eval;
+        };
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
+            bool cand = false;
             if (k < v.cnt) {
                 float uf[D];
                 make_point_smem<D>(v.first + k, v.sid, rk, s_box, uf);
                 const float S_f = action<NX, NT, float>(uf, lcf);
-                if (S_f <= m_ref + args.skip_window + 1.0f + 0.01f * S_f) {
-                    uint32_t w[D];
-                    sample_words<D>(v.first + k, v.sid, rk, w);
-                    double u[D];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) u[j] = Coord<double>::map(w[j], s_lo[j], s_w[j]);
-                    const double S = action<NX, NT, double>(u, lc);
-                    m_ref = fminf(m_ref, __double2float_rn(S));
-                    double Q[R];
-                    products<NX, NT, double>(u, Q);
-                    if (S < m_acc - kRescaleMargin) {  // rare: move the shift down
-                        rescale<double, K, R, BLOCK>(acc, exp(S - m_acc));
-                        m_acc = S;
-                    }
-                    accumulate<double, K, R, BLOCK>(acc, exp(m_acc - S), Q);
-                    ++n_eval;
-                }
+                cand = S_f <= m_ref + args.skip_window + 1.0f + 0.01f * S_f;
+            }
+            count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
+            if (count >= 32) {
+                evaluate(queue[lane]);
+                count = dequeue32(queue, count);
             }
             m_ref = warp_min(m_ref);
             if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&sh.min_bits, m_ref);
         }
+        if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         chunk_record<double, K, R, BLOCK>(acc, m_acc, sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
     }
@@ -380,11 +429,11 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64
 
 // ---------------------------------------------------------------------------
 // FP32 integrand.  Points, action, products and weights in float; per-thread
-// Kahan sums; merges in double.  Besides the rules above, a sample whose
-// FP32 action lies within kRefineWindow of m_ref (the weights that matter)
-// gets its action recomputed in compensated FP32 (action_df); all others have
-// weights below e^-kRefineWindow of the largest, where the ~1e-5 FP32 action
-// error is harmless.
+// Kahan sums; merges in double.  Candidates are queued as above; a candidate
+// whose FP32 action lies within kRefineWindow of m_ref (the weights that
+// matter) gets its action recomputed in compensated FP32 (action_df); all
+// others have weights below e^-kRefineWindow of the largest, where the ~1e-5
+// FP32 action error is harmless.
 // ---------------------------------------------------------------------------
 constexpr float kRefineWindow = 28.f;
 
@@ -401,7 +450,9 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f32
     __shared__ ChunkShared<BLOCK> sh;
     __shared__ float2 s_box[D];  // (lo, width) as floats; every thread reads the same word
     __shared__ float s_sums[Sums::WORDS * BLOCK];
-    const int tid = threadIdx.x;
+    __shared__ uint32_t s_queue[WARPS][kQueueCap];
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint32_t *queue = s_queue[tid >> 5];
     Sums acc{s_sums + tid};
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
@@ -417,32 +468,43 @@ __global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f32
         __syncthreads();
 
         unsigned n_eval = 0;
+        int count = 0;
+        auto evaluate = [&](uint32_t k) {
+            float u[D];
+            make_point_smem<D>(v.first + k, v.sid, rk, s_box, u);
+            const float S_f = action<NX, NT, float>(u, lc);
+            DF S{S_f, 0.f};
+            if (S_f < m_ref + kRefineWindow) {
+                S = action_df<NX, NT>(u, lcd);
+                m_ref = fminf(m_ref, S.h);
+            }
+            if (S.h < m_acc - kRescaleMargin) {  // rare: move the shift down
+                rescale<float, K, R, BLOCK>(acc, expf(S.h - m_acc));
+                m_acc = S.h;
+            }
+            float Q[R];
+            products<NX, NT, float>(u, Q);
+            accumulate<float, K, R, BLOCK>(acc, expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l)), Q);
+            ++n_eval;
+        };
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
+            bool cand = false;
             if (k < v.cnt) {
                 float u[D];
                 make_point_smem<D>(v.first + k, v.sid, rk, s_box, u);
-                const float S_f = action<NX, NT, float>(u, lc);
-                if (S_f <= m_ref + args.skip_window) {
-                    DF S{S_f, 0.f};
-                    if (S_f < m_ref + kRefineWindow) {
-                        S = action_df<NX, NT>(u, lcd);
-                        m_ref = fminf(m_ref, S.h);
-                    }
-                    if (S.h < m_acc - kRescaleMargin) {  // rare: move the shift down
-                        rescale<float, K, R, BLOCK>(acc, expf(S.h - m_acc));
-                        m_acc = S.h;
-                    }
-                    float Q[R];
-                    products<NX, NT, float>(u, Q);
-                    accumulate<float, K, R, BLOCK>(acc, expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l)), Q);
-                    ++n_eval;
-                }
+                cand = action<NX, NT, float>(u, lc) <= m_ref + args.skip_window;
+            }
+            count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
+            if (count >= 32) {
+                evaluate(queue[lane]);
+                count = dequeue32(queue, count);
             }
             m_ref = warp_min(m_ref);
             if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&sh.min_bits, m_ref);
         }
+        if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         chunk_record<float, K, R, BLOCK>(acc, static_cast<double>(m_acc), sh.f, &sh.mb, args.partials + c * (K + 2),
                                          v.cnt);
