@@ -202,7 +202,7 @@ bfi_status bfi_plan_get_timing(bfi_plan *plan, float *ms);
  *   stream           cudaStream_t of the current device
  * The scratch is one 16 MiB device array that every device that loads the
  * library holds until the process exits; a job whose chunk records, chunk
- * table and hints need more is rejected with BFI_E_INVALID and a message
+ * table, hints and merge factors need more is rejected with BFI_E_INVALID and a message
  * giving both sizes.  The first call on a device looks up the array's device
  * address (once per device); make that first call before any stream capture.
  * Every call uses the same array and leaves its contents behind; each call

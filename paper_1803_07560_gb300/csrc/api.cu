@@ -114,6 +114,7 @@ struct bfi_plan {
     double *d_partials = nullptr;
     float *d_hint = nullptr;
     unsigned long long *d_stats = nullptr;
+    double *d_fbuf = nullptr;
     float skip_window = 0.f;
     size_t scratch_bytes = 0;
     bool timing = false, timed = false;
@@ -136,6 +137,7 @@ bfi_status bfi_plan_destroy(bfi_plan *plan) {
         cudaFree(plan->d_partials);
         cudaFree(plan->d_hint);
         cudaFree(plan->d_stats);
+        cudaFree(plan->d_fbuf);
         for (auto &e : plan->ev)
             if (e) cudaEventDestroy(e);
     }
@@ -203,10 +205,11 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
     const size_t smp_bytes = sizeof(uint64_t) * nsub;
     const size_t par_bytes = sizeof(double) * static_cast<size_t>(std::max<int64_t>(p->nchunks, 1)) * (p->K + 2);
     const size_t hint_bytes = sizeof(float) * nsub;
-    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + sizeof(unsigned long long);
+    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + sizeof(unsigned long long) + sizeof(double) * nsub;
     if (cudaMalloc(&p->d_chunk_off, off_bytes) != cudaSuccess || cudaMalloc(&p->d_samples, smp_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_partials, par_bytes) != cudaSuccess || cudaMalloc(&p->d_hint, hint_bytes) != cudaSuccess ||
-        cudaMalloc(&p->d_stats, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&p->d_stats, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&p->d_fbuf, sizeof(double) * nsub) != cudaSuccess) {
         cudaGetLastError();
         bfi_plan_destroy(p);
         return fail(BFI_E_NOMEM, "device allocation of %zu bytes failed", p->scratch_bytes);
@@ -253,7 +256,7 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
     }
     if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[1], st));
     bfi::MergeArgs m{lo, hi, plan->d_chunk_off, plan->d_partials, slots, plan->nsub, plan->R, plan->d};
-    bfi::TotalsArgs t{slots, totals, plan->nsub, plan->R};
+    bfi::TotalsArgs t{slots, totals, plan->d_fbuf, plan->nsub, plan->R};
     BFI_CUDA(bfi::launch_merges(m, t, st));
     if (plan->timing) {
         BFI_CUDA(cudaEventRecord(plan->ev[2], st));

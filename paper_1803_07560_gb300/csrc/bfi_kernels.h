@@ -46,6 +46,7 @@ struct MergeArgs {
 struct TotalsArgs {
     const double *slots;
     double *totals;
+    double *f_buf;             // [nsub] scratch: per-subvolume scale factors
     int64_t nsub;
     int32_t R;
 };

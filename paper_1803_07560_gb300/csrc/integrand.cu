@@ -617,6 +617,7 @@ __device__ double block_max(double v, double *sh) {
 }
 
 __global__ void __launch_bounds__(kTotThreads) merge_totals(const TotalsArgs a) {
+    double *f_buf = a.f_buf;
     __shared__ double sh[kTotThreads];
     const int t = threadIdx.x;
     const int R = a.R, SL = 5 + 3 * R;
@@ -633,16 +634,21 @@ __global__ void __launch_bounds__(kTotThreads) merge_totals(const TotalsArgs a) 
     n_tot = block_sum(n_tot, sh);
     used = block_sum(used, sh);
 
-    // Z' and Var Z'
+    // f_s = exp(ls_s - L) once per subvolume (0 for subvolumes without weight)
     double z = 0.0, vz = 0.0, bad = 0.0;
     for (int64_t s = t; s < a.nsub; s += kTotThreads) {
         const double *q = a.slots + s * SL;
-        if (q[0] <= 0.0 || !(q[3] > 0.0)) continue;
-        const double n = q[0];
-        const double f = exp(q[2] - log(n) - q[1] - L);
-        z += f * q[3];
-        if (n < 2.0) { bad = 1.0; continue; }
-        vz += f * f * (n * q[4] - q[3] * q[3]) / (n - 1.0);
+        double f = 0.0;
+        if (q[0] > 0.0 && q[3] > 0.0) {
+            const double n = q[0];
+            f = exp(q[2] - log(n) - q[1] - L);
+            z += f * q[3];
+            if (n < 2.0)
+                bad = 1.0;
+            else
+                vz += f * f * (n * q[4] - q[3] * q[3]) / (n - 1.0);
+        }
+        f_buf[s] = f;
     }
     const double Z = block_sum(z, sh);
     const double VZ = block_sum(vz, sh);
@@ -655,19 +661,14 @@ __global__ void __launch_bounds__(kTotThreads) merge_totals(const TotalsArgs a) 
     }
     for (int r = 0; r < R; ++r) {
         double nr = 0.0;
-        for (int64_t s = t; s < a.nsub; s += kTotThreads) {
-            const double *q = a.slots + s * SL;
-            if (q[0] <= 0.0 || !(q[3] > 0.0)) continue;
-            nr += exp(q[2] - log(q[0]) - q[1] - L) * q[5 + r];
-        }
+        for (int64_t s = t; s < a.nsub; s += kTotThreads) nr += f_buf[s] * a.slots[s * SL + 5 + r];
         const double C = block_sum(nr, sh) / Z;
         double var = 0.0;
         for (int64_t s = t; s < a.nsub; s += kTotThreads) {
             const double *q = a.slots + s * SL;
-            if (q[0] <= 0.0 || !(q[3] > 0.0)) continue;
+            const double f = f_buf[s];
             const double n = q[0];
-            if (n < 2.0) continue;
-            const double f = exp(q[2] - log(n) - q[1] - L);
+            if (f == 0.0 || n < 2.0) continue;
             const double vN = (n * q[5 + 2 * R + r] - q[5 + r] * q[5 + r]) / (n - 1.0);
             const double cov = (n * q[5 + R + r] - q[3] * q[5 + r]) / (n - 1.0);
             const double vZ = (n * q[4] - q[3] * q[3]) / (n - 1.0);

@@ -6,7 +6,8 @@
 // allocations, or a latency-critical loop where an allocation (and the device
 // synchronisation it may imply) is not allowed after start-up.  For them this
 // file keeps the scratch the integration needs (chunk table, per-chunk partial
-// records, per-subvolume hints, the evaluated-samples counter) in one
+// records, per-subvolume hints and merge factors, the evaluated-samples
+// counter) in one
 // file-scope device array of fixed size, so a call allocates nothing; the
 // caller still passes its own inputs and outputs.  The kernels are the same
 // ones bfi_plan_execute runs.
@@ -121,8 +122,9 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
     const size_t smp_bytes = round_up(sizeof(uint64_t) * nsub);
     const size_t hint_bytes = round_up(sizeof(float) * nsub);
     const size_t stat_bytes = round_up(sizeof(unsigned long long));
+    const size_t fbuf_bytes = round_up(sizeof(double) * nsub);
     const size_t par_bytes = round_up(sizeof(double) * static_cast<size_t>(nchunks > 0 ? nchunks : 1) * (K + 2));
-    const size_t need = off_bytes + smp_bytes + hint_bytes + stat_bytes + par_bytes;
+    const size_t need = off_bytes + smp_bytes + hint_bytes + stat_bytes + fbuf_bytes + par_bytes;
     if (need > kStaticScratchBytes) {
         char msg[256];
         std::snprintf(msg, sizeof msg,
@@ -141,7 +143,8 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
     uint64_t *d_samples = reinterpret_cast<uint64_t *>(p + off_bytes);
     float *d_hint = reinterpret_cast<float *>(p + off_bytes + smp_bytes);
     unsigned long long *d_stats = reinterpret_cast<unsigned long long *>(p + off_bytes + smp_bytes + hint_bytes);
-    double *d_partials = reinterpret_cast<double *>(p + off_bytes + smp_bytes + hint_bytes + stat_bytes);
+    double *d_fbuf = reinterpret_cast<double *>(p + off_bytes + smp_bytes + hint_bytes + stat_bytes);
+    double *d_partials = reinterpret_cast<double *>(p + off_bytes + smp_bytes + hint_bytes + stat_bytes + fbuf_bytes);
 
     int sms = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
@@ -168,7 +171,7 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
             return cuda_fail("integrand launch", e);
     }
     const bfi::MergeArgs m{lo, hi, d_off, d_partials, slots, nsub, R, d};
-    const bfi::TotalsArgs t{slots, totals, nsub, R};
+    const bfi::TotalsArgs t{slots, totals, d_fbuf, nsub, R};
     if ((e = bfi::launch_merges(m, t, cs)) != cudaSuccess) return cuda_fail("merge launch", e);
     return BFI_OK;
 }
