@@ -193,7 +193,7 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
 
     int sms = 0, per_sm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = shape->occupancy[precision](&per_sm);
+    if (e == cudaSuccess) e = shape->occupancy[precision](lattice->nx, lattice->nt, &per_sm);
     if (e != cudaSuccess) {
         delete p;
         return fail(BFI_E_CUDA, "device query failed: %s", cudaGetErrorString(e));
@@ -232,7 +232,7 @@ bfi_status bfi_plan_get_info(const bfi_plan *plan, bfi_plan_info *info) {
     info->total_samples = plan->total;
     info->grid = plan->grid;
     info->block = bfi::kBlock;
-    info->kernel = 0;
+    info->kernel = plan->shape->kernel;
     info->slot_len = 5 + 3 * plan->R;
     info->totals_len = 4 + 2 * plan->R;
     info->scratch_bytes = plan->scratch_bytes;

@@ -10,9 +10,11 @@ namespace bfi {
 constexpr int kBlock = 256;   // threads per CTA of the integrand kernels
 constexpr int kMaxD = 512;    // largest lattice (d = nx * nt) the library accepts
 
-// Lattice shapes with a compiled thread-per-sample kernel (NX, NT).
-#define BFI_COMPILED_SHAPES(X) \
-    X(2, 1) X(3, 1) X(4, 1) X(2, 2) X(3, 2) X(4, 2) X(10, 2)
+// Lattice shapes with a compiled thread-per-sample kernel (NX, NT), in two
+// translation units that compile in parallel; every other shape with
+// d = NX NT <= kMaxD runs on the generic warp-per-sample kernel.
+#define BFI_SHAPES_SMALL(X) X(2, 1) X(3, 1) X(4, 1) X(2, 2) X(3, 2) X(4, 2) X(6, 2) X(8, 2) X(10, 2)
+#define BFI_SHAPES_CONFIG(X) X(16, 2) X(32, 2) X(4, 4) X(6, 4) X(8, 4) X(10, 4) X(16, 4)
 
 struct LatticeParams {
     int32_t nx, nt;
@@ -68,17 +70,24 @@ struct EvalArgs {
 
 using IntegrandLauncher = cudaError_t (*)(const IntegrandArgs &, const LatticeParams &, uint32_t, uint32_t, int,
                                           cudaStream_t);
-using OccupancyQuery = cudaError_t (*)(int *);
+using OccupancyQuery = cudaError_t (*)(int nx, int nt, int *blocks_per_sm);
 using EvalLauncher = cudaError_t (*)(const EvalArgs &, const LatticeParams &, int mode, cudaStream_t);
 
 // index 0 = FP64, 1 = FP32
 struct ShapeKernels {
     int nx, nt;
+    int kernel;   // 0 = thread-per-sample (compiled shape), 1 = generic warp-per-sample
     IntegrandLauncher integrand[2];
     OccupancyQuery occupancy[2];
     EvalLauncher eval;   // mode 0 = FP64, 1 = FP32, 2 = FP32 compensated action
 };
 
+// Compiled shape tables (shapes_small.cu, shapes_config.cu) and the generic
+// kernels (generic.cu); find_shape looks in the tables, then falls back to
+// the generic kernels (null if d > kMaxD).
+const ShapeKernels *shapes_small(int *n);
+const ShapeKernels *shapes_config(int *n);
+const ShapeKernels *generic_shape(int nx, int nt);
 const ShapeKernels *find_shape(int nx, int nt);
 cudaError_t launch_merges(const MergeArgs &m, const TotalsArgs &t, cudaStream_t st);
 cudaError_t launch_points(const PointsArgs &a, bool fp32, uint32_t seed, uint32_t job, cudaStream_t st);

@@ -1,0 +1,446 @@
+// generic.cu -- warp-per-sample integrand for any lattice shape with
+// d = Nx Nt <= kMaxD (Honkonen & Honkonen, arXiv:1803.07560, Eq. (Gen2),
+// Sec. 3 and Sec. 4), used for the shapes without a compiled thread-per-sample
+// kernel (large lattices such as 32x4 or 64x8, and any other shape).
+//
+// One warp evaluates one sample at a time: the lanes draw the Philox blocks
+// of the sample in parallel and write the coordinates to the warp's slice of
+// shared memory; each lane then takes sites j = lane, lane + 32, ... of the
+// stencil (neighbours through a per-CTA table: next time slice, and j +- Nt
+// for the spatial neighbours), and the lanes own the correlation distances
+// r = lane, lane + 32, ...  Sums across lanes are XOR butterflies, which give
+// every lane the bit-identical result, so every decision is warp-uniform and
+// reproducible.  The same screen / full-evaluation / shifted-weight rules as
+// the thread-per-sample kernels apply (integrand_kernels.cuh).
+#include "integrand_kernels.cuh"
+
+namespace bfi {
+namespace {
+
+constexpr int kGBlock = 128;
+constexpr int kGWarps = kGBlock / 32;
+
+struct GenShape {
+    int nx, nt, d, R, K, nq;
+};
+
+GenShape gen_shape(int nx, int nt) {
+    GenShape g;
+    g.nx = nx;
+    g.nt = nt;
+    g.d = nx * nt;
+    g.R = nx / 2 + 1;
+    g.K = 2 + 3 * g.R;
+    g.nq = (g.d + 3) / 4;
+    return g;
+}
+
+// Dynamic shared memory layout of one CTA (byte offsets, 16-aligned).
+struct GenLayout {
+    int next, box_f, lo_d, w_d, uf, ud, sums, mw, total;
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline GenLayout gen_layout(const GenShape &g) {
+    GenLayout L;
+    int o = 0;
+    L.next = o;  o = align16(o + 2 * g.d);                    // uint16 next-time-slice index per site
+    L.box_f = o; o = align16(o + 8 * g.d);                    // float2 (lo, width)
+    L.lo_d = o;  o = align16(o + 8 * g.d);                    // double lo
+    L.w_d = o;   o = align16(o + 8 * g.d);                    // double width
+    L.uf = o;    o = align16(o + 4 * g.d * kGWarps);          // float point per warp
+    L.ud = o;    o = align16(o + 8 * g.d * kGWarps);          // double point per warp
+    L.sums = o;  o = align16(o + 8 * (g.K + g.R + 1) * kGWarps);  // per-warp sums (FP64, or FP32 sums + comps)
+    L.mw = o;    o = align16(o + 8 * kGWarps + 8);             // per-warp shift, counter
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__device__ __forceinline__ DF warp_sum_df(DF v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const DF o{__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
+        v = df_add(v, o);
+    }
+    return v;
+}
+
+__device__ __forceinline__ int wrap(int j, int d) { return j >= d ? j - d : (j < 0 ? j + d : j); }
+
+// S at the point u (shared memory), every lane gets the same value.
+template <typename Real>
+__device__ Real warp_action(const Real *u, const uint16_t *next, const GenShape &g, const LatticeConst<Real> &c) {
+    const int lane = threadIdx.x & 31;
+    Real acc = Real(0), s2 = Real(0);
+    for (int j = lane; j < g.d; j += 32) {
+        const Real here = u[j];
+        const Real right = u[wrap(j + g.nt, g.d)];
+        const Real left = u[wrap(j - g.nt, g.d)];
+        const Real t = fma(c.c_adv, right - left, c.k1);
+        Real R = fma(here, t, u[next[j]]);
+        R = fma(c.neg_c_dif, right + left, R);
+        acc = fma(R, R, acc);
+        s2 = fma(here, here, s2);
+    }
+    acc = warp_sum(acc);
+    Real S = acc * c.inv_2Dtau;
+    if (c.half_mass2 != Real(0)) S = fma(c.half_mass2, warp_sum(s2), S);
+    return S;
+}
+
+// The same in compensated FP32 (see action_df).
+__device__ DF warp_action_df(const float *u, const uint16_t *next, const GenShape &g, const LatticeConstDF &c) {
+    const int lane = threadIdx.x & 31;
+    DF acc{0.f, 0.f}, mass{0.f, 0.f};
+    for (int j = lane; j < g.d; j += 32) {
+        const float here = u[j];
+        const float right = u[wrap(j + g.nt, g.d)];
+        const float left = u[wrap(j - g.nt, g.d)];
+        const DF dx = two_sum(right, -left);
+        const DF t = df_add(df_mul(c.c_adv, dx), c.k1);
+        const DF q = df_add_f(df_mul_f(t, here), u[next[j]]);
+        const DF lr = two_sum(right, left);
+        const DF R = df_add(q, df_mul(c.c_dif, DF{-lr.h, -lr.l}));
+        DF sq = two_prod(R.h, R.h);
+        sq.l = __fmaf_rn(2.f * R.h, R.l, sq.l);
+        acc = df_add(acc, sq);
+        mass = df_add(mass, two_prod(here, here));
+    }
+    acc = warp_sum_df(acc);
+    DF S = df_mul(acc, c.inv_2Dtau);
+    if (c.half_mass2.h != 0.f) S = df_add(S, df_mul(warp_sum_df(mass), c.half_mass2));
+    return S;
+}
+
+// Q_r = sum_j u_j u_{j + r Nt (mod d)} for the distances r this lane owns
+// (r = lane + 32 i), handed to f(r, Q_r).  FP32 sums are compensated.
+template <typename F>
+__device__ __forceinline__ void lane_products(const double *u, const GenShape &g, F f) {
+    for (int r = threadIdx.x & 31; r < g.R; r += 32) {
+        double q = 0.0;
+        for (int j = 0; j < g.d; ++j) q = fma(u[j], u[wrap(j + r * g.nt, g.d)], q);
+        f(r, q);
+    }
+}
+
+template <typename F>
+__device__ __forceinline__ void lane_products(const float *u, const GenShape &g, F f) {
+    for (int r = threadIdx.x & 31; r < g.R; r += 32) {
+        DF q{0.f, 0.f};
+        for (int j = 0; j < g.d; ++j) q = df_add(q, two_prod(u[j], u[wrap(j + r * g.nt, g.d)]));
+        f(r, q.h + q.l);
+    }
+}
+
+// Philox blocks q = lane, lane + 32, ... of sample i mapped into u.
+template <typename Real, typename Box>
+__device__ __forceinline__ void warp_point(uint64_t i, uint32_t sid, const RoundKeys &rk, const GenShape &g, Box box,
+                                           Real *u) {
+    for (int q = threadIdx.x & 31; q < g.nq; q += 32) {
+        const uint4 b = philox4x32_10(
+            make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
+        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = 4 * q + t;
+            if (j < g.d) u[j] = box(j, w4[t]);
+        }
+    }
+    __syncwarp();
+}
+
+// Per-CTA set-up shared by the kernels: neighbour table (once) and box.
+__device__ void load_box(unsigned char *sm, const GenLayout &L, const GenShape &g, const double *lo,
+                         const double *hi) {
+    float2 *bf = reinterpret_cast<float2 *>(sm + L.box_f);
+    double *ld = reinterpret_cast<double *>(sm + L.lo_d);
+    double *wd = reinterpret_cast<double *>(sm + L.w_d);
+    for (int j = threadIdx.x; j < g.d; j += blockDim.x) {
+        bf[j] = make_float2(__double2float_rn(lo[j]), __double2float_rn(hi[j] - lo[j]));
+        ld[j] = lo[j];
+        wd[j] = hi[j] - lo[j];
+    }
+}
+
+__device__ void build_next(unsigned char *sm, const GenLayout &L, const GenShape &g) {
+    uint16_t *next = reinterpret_cast<uint16_t *>(sm + L.next);
+    for (int j = threadIdx.x; j < g.d; j += blockDim.x) {
+        const int l = j % g.nt;
+        next[j] = static_cast<uint16_t>(l + 1 < g.nt ? j + 1 : j + 1 - g.nt);
+    }
+}
+
+struct GenArgs {
+    IntegrandArgs a;
+    GenShape g;
+    GenLayout L;
+    LatticeConst<float> cf;
+    LatticeConst<double> cd;
+    LatticeConstDF cdf;
+    RoundKeys rk;
+};
+
+// ---------------------------------------------------------------------------
+// The integrand.  FP64 = true: FP32 screen, FP64 evaluation; false: FP32
+// screen and evaluation with the compensated action near the minimum.
+// ---------------------------------------------------------------------------
+template <bool FP64>
+__global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const IntegrandArgs &args = ga.a;
+    const GenShape &g = ga.g;
+    const GenLayout &L = ga.L;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint16_t *next = reinterpret_cast<const uint16_t *>(sm + L.next);
+    const float2 *bf = reinterpret_cast<const float2 *>(sm + L.box_f);
+    const double *ld = reinterpret_cast<const double *>(sm + L.lo_d);
+    const double *wd = reinterpret_cast<const double *>(sm + L.w_d);
+    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.d;
+    double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.d;
+    double *mw = reinterpret_cast<double *>(sm + L.mw);
+    unsigned *cnt_all = reinterpret_cast<unsigned *>(mw + kGWarps);
+    // per-warp sums: FP64 -> double[K]; FP32 -> float[K] then float comps[1 + R]
+    double *sd = reinterpret_cast<double *>(sm + L.sums) + warp * (g.K + g.R + 1);
+    float *sf = reinterpret_cast<float *>(sm + L.sums) + warp * 2 * (g.K + g.R + 1);
+    float *cf = sf + g.K;
+    build_next(sm, L, g);
+
+    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+        const ChunkView v = chunk_view(args, c, g.d);
+        __syncthreads();  // the previous chunk's readers of box and sums are done
+        load_box(sm, L, g, v.lo, v.hi);
+        for (int k = lane; k < g.K + g.R + 1; k += 32) {
+            if (FP64) sd[k] = 0.0; else { sf[2 * k] = 0.f; sf[2 * k + 1] = 0.f; }
+        }
+        if (tid == 0) *cnt_all = 0u;
+        __syncthreads();
+        const float hint = args.hint[v.s];
+        float m_ref = hint;
+        double m_acc = static_cast<double>(hint);
+        float m_acc_f = hint;
+        unsigned n_eval = 0;
+        for (uint64_t k = warp; k < v.cnt; k += kGWarps) {
+            const uint64_t i = v.first + k;
+            warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
+            const float S_f = warp_action<float>(uf, next, g, ga.cf);
+            if (FP64) {
+                if (!(S_f <= m_ref + args.skip_window + 1.0f + 0.01f * S_f)) continue;
+                warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<double>::map(w, ld[j], wd[j]); }, ud);
+                const double S = warp_action<double>(ud, next, g, ga.cd);
+                m_ref = fminf(m_ref, __double2float_rn(S));
+                if (S < m_acc - kRescaleMargin) {
+                    const double f = exp(S - m_acc), f2 = f * f;
+                    for (int kk = lane; kk < g.K; kk += 32) sd[kk] *= second_order(kk, g.R) ? f2 : f;
+                    m_acc = S;
+                    __syncwarp();  // another lane owns some of the sums it rescaled
+                }
+                const double w = exp(m_acc - S);
+                if (lane == 0) {
+                    sd[0] += w;
+                    sd[1] += w * w;
+                }
+                lane_products(ud, g, [&](int r, double q) {
+                    const double wq = w * q;
+                    sd[2 + r] += wq;
+                    sd[2 + g.R + r] += w * wq;
+                    sd[2 + 2 * g.R + r] += wq * wq;
+                });
+            } else {
+                if (!(S_f <= m_ref + args.skip_window)) continue;
+                DF S{S_f, 0.f};
+                if (S_f < m_ref + kRefineWindow) {
+                    S = warp_action_df(uf, next, g, ga.cdf);
+                    m_ref = fminf(m_ref, S.h);
+                }
+                if (S.h < m_acc_f - kRescaleMargin) {
+                    const float f = expf(S.h - m_acc_f), f2 = f * f;
+                    for (int kk = lane; kk < g.K; kk += 32) sf[kk] *= second_order(kk, g.R) ? f2 : f;
+                    for (int kk = lane; kk < 1 + g.R; kk += 32) cf[kk] *= f;
+                    m_acc_f = S.h;
+                    __syncwarp();  // another lane owns some of the sums it rescaled
+                }
+                const float w = expf(__fsub_rn(__fsub_rn(m_acc_f, S.h), S.l));
+                auto kahan = [&](int k, int ci, float x) {
+                    const float y = x - cf[ci];
+                    const float t = sf[k] + y;
+                    cf[ci] = (t - sf[k]) - y;
+                    sf[k] = t;
+                };
+                if (lane == 0) {
+                    kahan(0, 0, w);
+                    sf[1] += w * w;
+                }
+                lane_products(uf, g, [&](int r, float q) {
+                    const float wq = w * q;
+                    kahan(2 + r, 1 + r, wq);
+                    sf[2 + g.R + r] += w * wq;
+                    sf[2 + 2 * g.R + r] += wq * wq;
+                });
+                m_acc = static_cast<double>(m_acc_f);
+            }
+            ++n_eval;
+            __syncwarp();
+        }
+        if (lane == 0) {
+            mw[warp] = m_acc;
+            atomicAdd(cnt_all, n_eval);
+        }
+        __syncthreads();
+        // chunk record: warps merged in order at the smallest warp shift
+        double mb = mw[0];
+        for (int w = 1; w < kGWarps; ++w) mb = fmin(mb, mw[w]);
+        double *out = args.partials + c * (g.K + 2);
+        for (int k = tid; k < g.K; k += kGBlock) {
+            const bool sq = second_order(k, g.R);
+            double acc = 0.0;
+            for (int w = 0; w < kGWarps; ++w) {
+                const double f = mw[w] == mb ? 1.0 : exp(mb - mw[w]);
+                double val;
+                if (FP64) {
+                    val = reinterpret_cast<const double *>(sm + L.sums)[w * (g.K + g.R + 1) + k];
+                } else {
+                    const float *s = reinterpret_cast<const float *>(sm + L.sums) + w * 2 * (g.K + g.R + 1);
+                    const bool comp = k == 0 || (k >= 2 && k < 2 + g.R);
+                    val = static_cast<double>(s[k]);
+                    if (comp) val -= static_cast<double>(s[g.K + (k == 0 ? 0 : k - 1)]);
+                }
+                acc = __dadd_rn(acc, __dmul_rn(val, sq ? f * f : f));
+            }
+            out[2 + k] = acc;
+        }
+        if (tid == 0) {
+            out[0] = static_cast<double>(v.cnt);
+            out[1] = mb;
+            if (args.stats) atomicAdd(args.stats, static_cast<unsigned long long>(*cnt_all));
+        }
+    }
+}
+
+// Per-subvolume reference action: the smallest FP32 action among the first
+// min(n_s, 4096) samples.  One CTA per subvolume, warp per sample.
+__global__ void __launch_bounds__(kGBlock) generic_hint(const GenArgs ga) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const IntegrandArgs &args = ga.a;
+    const GenShape &g = ga.g;
+    const GenLayout &L = ga.L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t s = blockIdx.x;
+    int *s_min = reinterpret_cast<int *>(sm + L.mw);
+    build_next(sm, L, g);
+    load_box(sm, L, g, args.lo + s * g.d, args.hi + s * g.d);
+    if (threadIdx.x == 0) *s_min = __float_as_int(INFINITY);
+    __syncthreads();
+    const uint16_t *next = reinterpret_cast<const uint16_t *>(sm + L.next);
+    const float2 *bf = reinterpret_cast<const float2 *>(sm + L.box_f);
+    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.d;
+    const uint32_t sid = args.sub_id ? args.sub_id[s] : static_cast<uint32_t>(s);
+    const uint64_t n = min(args.samples[s], static_cast<uint64_t>(4096));
+    float mn = INFINITY;
+    for (uint64_t k = warp; k < n; k += kGWarps) {
+        warp_point<float>(k, sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
+        mn = fminf(mn, warp_action<float>(uf, next, g, ga.cf));
+        __syncwarp();
+    }
+    if (lane == 0) atomicMin(s_min, __float_as_int(mn));
+    __syncthreads();
+    if (threadIdx.x == 0) args.hint[s] = __int_as_float(*s_min);
+}
+
+// Action and products at given points, one warp per point.
+__global__ void __launch_bounds__(kGBlock) generic_eval(const EvalArgs a, const GenArgs ga, int mode) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const GenShape &g = ga.g;
+    const GenLayout &L = ga.L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    build_next(sm, L, g);
+    __syncthreads();
+    const int64_t i = blockIdx.x * static_cast<int64_t>(kGWarps) + warp;
+    if (i >= a.npts) return;  // warp-uniform
+    const uint16_t *next = reinterpret_cast<const uint16_t *>(sm + L.next);
+    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.d;
+    double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.d;
+    for (int j = lane; j < g.d; j += 32) {
+        ud[j] = a.y[i * g.d + j];
+        uf[j] = static_cast<float>(a.y[i * g.d + j]);
+    }
+    __syncwarp();
+    double S;
+    if (mode == 0) {
+        S = warp_action<double>(ud, next, g, ga.cd);
+        lane_products(ud, g, [&](int r, double q) { a.P[i * g.R + r] = q / g.d; });
+    } else {
+        if (mode == 2) {
+            const DF Sd = warp_action_df(uf, next, g, ga.cdf);
+            S = static_cast<double>(Sd.h) + static_cast<double>(Sd.l);
+        } else {
+            S = static_cast<double>(warp_action<float>(uf, next, g, ga.cf));
+        }
+        lane_products(uf, g, [&](int r, float q) { a.P[i * g.R + r] = static_cast<double>(q) / g.d; });
+    }
+    if (lane == 0) a.S[i] = S;
+}
+
+GenArgs make_gen_args(const IntegrandArgs &a, const LatticeParams &p, uint32_t seed, uint32_t job) {
+    GenArgs ga;
+    ga.a = a;
+    ga.g = gen_shape(p.nx, p.nt);
+    ga.L = gen_layout(ga.g);
+    ga.cf = make_const<float>(p);
+    ga.cd = make_const<double>(p);
+    ga.cdf = make_const_df(p);
+    ga.rk = make_round_keys(seed, job);
+    return ga;
+}
+
+template <bool FP64>
+cudaError_t gen_integrand_launcher(const IntegrandArgs &args, const LatticeParams &p, uint32_t seed, uint32_t job,
+                                   int grid, cudaStream_t st) {
+    const GenArgs ga = make_gen_args(args, p, seed, job);
+    cudaError_t e = cudaFuncSetAttribute(generic_hint, cudaFuncAttributeMaxDynamicSharedMemorySize, ga.L.total);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(generic_integrand<FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, ga.L.total);
+    if (e != cudaSuccess) return e;
+    generic_hint<<<static_cast<unsigned>(args.nsub), kGBlock, ga.L.total, st>>>(ga);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    generic_integrand<FP64><<<grid, kGBlock, ga.L.total, st>>>(ga);
+    return cudaGetLastError();
+}
+
+template <bool FP64>
+cudaError_t gen_occupancy(int nx, int nt, int *blocks_per_sm) {
+    const GenLayout L = gen_layout(gen_shape(nx, nt));
+    cudaError_t e = cudaFuncSetAttribute(generic_integrand<FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, generic_integrand<FP64>, kGBlock, L.total);
+}
+
+cudaError_t gen_eval(const EvalArgs &a, const LatticeParams &p, int mode, cudaStream_t st) {
+    if (a.npts == 0) return cudaSuccess;
+    IntegrandArgs none{};
+    const GenArgs ga = make_gen_args(none, p, 0, 0);
+    cudaError_t e = cudaFuncSetAttribute(generic_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, ga.L.total);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (a.npts + kGWarps - 1) / kGWarps;
+    generic_eval<<<static_cast<unsigned>(blocks), kGBlock, ga.L.total, st>>>(a, ga, mode);
+    return cudaGetLastError();
+}
+
+const ShapeKernels kGeneric = {0, 0, 1, {gen_integrand_launcher<true>, gen_integrand_launcher<false>},
+                               {gen_occupancy<true>, gen_occupancy<false>}, gen_eval};
+
+}  // namespace
+
+const ShapeKernels *generic_shape(int nx, int nt) {
+    if (nx < 2 || nt < 1 || nx * nt > kMaxD) return nullptr;
+    return &kGeneric;
+}
+
+}  // namespace bfi

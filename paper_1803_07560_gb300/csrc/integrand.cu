@@ -15,530 +15,11 @@
 //
 // Every reduction has a fixed order, so results are bitwise reproducible and do
 // not depend on what else runs on the device.
-#include "bfi_device.cuh"
-#include "bfi_kernels.h"
+#include "integrand_kernels.cuh"
 
 #include <cmath>
 
-// Resident CTAs per SM the integrand kernels are compiled for (register cap
-// 65536 / (256 * this)).
-#ifndef BFI_INTEGRAND_MIN_BLOCKS
-#define BFI_INTEGRAND_MIN_BLOCKS 4
-#endif
-
 namespace bfi {
-
-// ---------------------------------------------------------------------------
-// Chunk lookup: chunks of subvolume s are [chunk_off[s], chunk_off[s+1]).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int64_t find_subvolume(const int64_t *chunk_off, int64_t nsub, int64_t c) {
-    int64_t lo = 0, hi = nsub;  // invariant: chunk_off[lo] <= c < chunk_off[hi]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (chunk_off[mid] <= c) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-template <typename Real>
-struct BoxPair;
-template <>
-struct BoxPair<float> {
-    __device__ __forceinline__ static void load(const double *lo, const double *hi, int j, float &b, float &w) {
-        b = __double2float_rn(lo[j]);
-        w = __double2float_rn(hi[j] - lo[j]);
-    }
-};
-template <>
-struct BoxPair<double> {
-    __device__ __forceinline__ static void load(const double *lo, const double *hi, int j, double &b, double &w) {
-        b = lo[j];
-        w = hi[j] - lo[j];
-    }
-};
-
-// ---------------------------------------------------------------------------
-// Chunk set-up shared by the integrand kernels.
-// ---------------------------------------------------------------------------
-struct ChunkView {
-    int64_t s;          // subvolume
-    uint64_t first;     // first sample index of the chunk
-    uint64_t cnt;       // samples in the chunk
-    uint32_t sid;       // Philox counter word 3
-    const double *lo, *hi;
-};
-
-__device__ __forceinline__ ChunkView chunk_view(const IntegrandArgs &args, int64_t c, int d) {
-    ChunkView v;
-    v.s = find_subvolume(args.chunk_off, args.nsub, c);
-    const uint64_t n_s = args.samples[v.s];
-    v.first = static_cast<uint64_t>(c - args.chunk_off[v.s]) * static_cast<uint64_t>(args.chunk_samples);
-    v.cnt = min(static_cast<uint64_t>(args.chunk_samples), n_s - v.first);
-    v.sid = args.sub_id ? args.sub_id[v.s] : static_cast<uint32_t>(v.s);
-    v.lo = args.lo + v.s * d;
-    v.hi = args.hi + v.s * d;
-    return v;
-}
-
-// S of Eq. (Gen2): the residual sum of squares plus the optional mass term.
-template <int NX, int NT, typename Real>
-__device__ __forceinline__ Real action(const Real (&u)[NX * NT], const LatticeConst<Real> &c) {
-    Real S = residual_sq_sum<NX, NT, Real>(u, c) * c.inv_2Dtau;
-    if (c.half_mass2 != Real(0)) {
-        Real s2 = Real(0);
-#pragma unroll
-        for (int j = 0; j < NX * NT; ++j) s2 = fma(u[j], u[j], s2);
-        S = fma(c.half_mass2, s2, S);
-    }
-    return S;
-}
-
-// Raw Philox words of sample i: block q = (q, i lo, i hi, sid), word j%4.
-template <int D>
-__device__ __forceinline__ void sample_words(uint64_t i, uint32_t sid, const RoundKeys &rk, uint32_t (&w)[D]) {
-    constexpr int NQ = (D + 3) / 4;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const uint4 b = philox4x32_10(
-            make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
-        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-            if (4 * q + t < D) w[4 * q + t] = w4[t];
-    }
-}
-
-// FP32 coordinates of sample i from the (lo, width) pairs in shared memory.
-template <int D>
-__device__ __forceinline__ void make_point_smem(uint64_t i, uint32_t sid, const RoundKeys &rk, const float2 *box,
-                                                float (&u)[D]) {
-    constexpr int NQ = (D + 3) / 4;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const uint4 b = philox4x32_10(
-            make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
-        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int j = 4 * q + t;
-            if (j < D) {
-                const float2 bw = box[j];
-                u[j] = Coord<float>::map(w4[t], bw.x, bw.y);
-            }
-        }
-    }
-}
-
-// Running minimum shared across the CTA at fixed points of the sample loop:
-// every thread contributes, then every thread reads the same value, so the
-// decisions that depend on it do not depend on timing.  S >= 0, so the float
-// order equals the order of the bit patterns as signed ints.
-__device__ __forceinline__ void share_min(int *s_min, float &m_ref) {
-    atomicMin(s_min, __float_as_int(m_ref));
-    __syncthreads();
-    m_ref = __int_as_float(*s_min);
-    __syncthreads();
-}
-
-// Count of fully evaluated samples of the chunk, added to the plan's stats.
-__device__ __forceinline__ void add_evaluated(unsigned long long *stats, unsigned n_eval, unsigned *s_cnt) {
-    if (!stats) return;
-    atomicAdd(s_cnt, n_eval);
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(stats, static_cast<unsigned long long>(*s_cnt));
-}
-
-// ---------------------------------------------------------------------------
-// Negligible weights.  A sample whose action exceeds the subvolume's
-// smallest action by more than args.skip_window has weight below
-// e^-skip_window of the largest; with skip_window = c + ln(n_max) the n_s such
-// samples of a subvolume change every sum by less than e^-c relative (the
-// largest weight is 1).  Both kernels leave those samples out of the
-// products, the weight and the sums.  The reference point m_ref is the
-// per-subvolume hint (the smallest FP32 action among the first samples) and
-// then the smallest action evaluated so far: shared across the warp after
-// every row of samples and across the CTA every kShareRows rows, at fixed
-// points, so every decision is reproducible.  m_ref is always the action of
-// an evaluated sample (or within FP32 error of one), never far below the
-// final shift.
-//
-// Shift.  Both kernels accumulate w = exp(m_acc - S) with m_acc starting at
-// the hint and moving down only when a sample beats it by more than
-// kRescaleMargin, so the sums are rescaled a handful of times and the
-// threads of a CTA mostly share one shift (cheap merges).  w <= e^16.
-//
-// Sums.  The per-thread sums live in shared memory ([k][thread], no bank
-// conflicts); they are touched only by the few samples that pass the screen,
-// which keeps the registers of the hot loop (Philox, point, FP32 action) low
-// enough for three CTAs per SM.
-// ---------------------------------------------------------------------------
-constexpr int kShareRows = 64;
-constexpr float kRescaleMargin = 16.f;
-
-__device__ __forceinline__ float warp_min(float x) {
-    return __int_as_float(static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(__float_as_int(x)))));
-}
-
-// Per-thread sums in shared memory: element k of thread t at buf[k * BLOCK + t].
-template <typename Real, int K, int BLOCK>
-struct SmemSums;
-
-template <int K, int BLOCK>
-struct SmemSums<float, K, BLOCK> {  // first-order sums Kahan-compensated
-    static constexpr int R = (K - 2) / 3;
-    static constexpr int NC = 1 + R;
-    static constexpr int WORDS = K + NC;
-    float *b;
-    __device__ __forceinline__ static bool compensated(int k) { return k == 0 || (k >= 2 && k < 2 + R); }
-    __device__ __forceinline__ static int cidx(int k) { return K + (k == 0 ? 0 : k - 1); }
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int k = 0; k < WORDS; ++k) b[k * BLOCK] = 0.f;
-    }
-    __device__ __forceinline__ void add(int k, float x) {
-        if (compensated(k)) {
-            const float sk = b[k * BLOCK], ck = b[cidx(k) * BLOCK];
-            const float y = x - ck;
-            const float t = sk + y;
-            b[cidx(k) * BLOCK] = (t - sk) - y;
-            b[k * BLOCK] = t;
-        } else {
-            b[k * BLOCK] += x;
-        }
-    }
-    __device__ __forceinline__ void scale(int k, float f) {
-        b[k * BLOCK] *= f;
-        if (compensated(k)) b[cidx(k) * BLOCK] *= f;
-    }
-    __device__ __forceinline__ double value(int k) const {
-        return compensated(k) ? static_cast<double>(b[k * BLOCK]) - static_cast<double>(b[cidx(k) * BLOCK])
-                              : static_cast<double>(b[k * BLOCK]);
-    }
-};
-
-template <int K, int BLOCK>
-struct SmemSums<double, K, BLOCK> {
-    static constexpr int WORDS = K;
-    double *b;
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int k = 0; k < K; ++k) b[k * BLOCK] = 0.0;
-    }
-    __device__ __forceinline__ void add(int k, double x) { b[k * BLOCK] += x; }
-    __device__ __forceinline__ void scale(int k, double f) { b[k * BLOCK] *= f; }
-    __device__ __forceinline__ double value(int k) const { return b[k * BLOCK]; }
-};
-
-// The CTA's record of a chunk, [cnt, m, sums...], reduced straight from the
-// shared-memory sums: the CTA shift m_b is the smallest thread shift; each
-// thread's factor exp(m_b - m_t) (1 when equal, the common case) goes to
-// s_f; then warp w sums elements k = w, w + WARPS, ... over all threads, lane
-// l taking threads l, l + 32, ... in order and the lanes combining in a fixed
-// butterfly.  Every order is fixed, so the record is reproducible.
-template <typename Real, int K, int R, int BLOCK>
-__device__ __forceinline__ void chunk_record(const SmemSums<Real, K, BLOCK> &acc, double m_t, double *s_f,
-                                             double *s_mb, double *out, uint64_t cnt) {
-    constexpr int WARPS = BLOCK / 32;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_f[tid] = m_t;
-    __syncthreads();
-    if (warp == 0) {
-        double mn = INFINITY;
-        for (int t = lane; t < BLOCK; t += 32) mn = fmin(mn, s_f[t]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, off));
-        if (lane == 0) *s_mb = mn;
-    }
-    __syncthreads();
-    const double mb = *s_mb;
-    s_f[tid] = (m_t == INFINITY) ? 0.0 : (m_t == mb ? 1.0 : exp(mb - m_t));
-    __syncthreads();
-    const Real *base = acc.b - tid;  // element k of thread t: sums of thread t
-    for (int k = warp; k < K; k += WARPS) {
-        const bool sq = second_order(k, R);
-        double part = 0.0;
-        for (int t = lane; t < BLOCK; t += 32) {
-            SmemSums<Real, K, BLOCK> other{const_cast<Real *>(base) + t};
-            const double f = s_f[t];
-            part = __dadd_rn(part, __dmul_rn(other.value(k), sq ? f * f : f));
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) part = __dadd_rn(part, __shfl_xor_sync(0xffffffffu, part, off));
-        if (lane == 0) out[2 + k] = part;
-    }
-    if (tid == 0) {
-        out[0] = static_cast<double>(cnt);
-        out[1] = mb;
-    }
-    __syncthreads();
-}
-
-template <typename Real, int K, int R, int BLOCK>
-__device__ __forceinline__ void accumulate(SmemSums<Real, K, BLOCK> &acc, Real w, const Real (&Q)[R]) {
-    acc.add(0, w);
-    acc.add(1, w * w);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const Real wq = w * Q[r];
-        acc.add(2 + r, wq);
-        acc.add(2 + R + r, w * wq);
-        acc.add(2 + 2 * R + r, wq * wq);
-    }
-}
-
-template <typename Real, int K, int R, int BLOCK>
-__device__ __forceinline__ void rescale(SmemSums<Real, K, BLOCK> &acc, Real f) {
-    const Real f2 = f * f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc.scale(k, second_order(k, R) ? f2 : f);
-}
-
-// Shared state of one CTA for one chunk.
-template <int BLOCK>
-struct ChunkShared {
-    double f[BLOCK];  // per-thread shift factors of the chunk record
-    double mb;
-    int min_bits;
-    unsigned evaluated;
-};
-
-// ---------------------------------------------------------------------------
-// Candidate queues.  The few samples that pass the screen are not evaluated
-// where they are found (one or two lanes of a warp, which on GB300's FP64
-// pipe, 2 lanes per SM and clock, would hold the whole warp for the full
-// warp-width cost of every FP64 instruction).  Each warp appends its
-// candidates, in (row, lane) order, to its own queue in shared memory and
-// evaluates them 32 at a time with every lane busy; the remainder is
-// evaluated at the end of the chunk.  Lane l always takes queue entry l, so
-// which lane accumulates which sample, and in what order, is fixed.
-// ---------------------------------------------------------------------------
-constexpr int kQueueCap = 64;
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// Appends this lane's candidate (if any) to the warp's queue; returns the new
-// count.  Needs count < 32 on entry (then count < 64 = kQueueCap on exit).
-__device__ __forceinline__ int enqueue(uint32_t *q, int count, bool cand, uint32_t k) {
-    const unsigned mask = __ballot_sync(0xffffffffu, cand);
-    if (cand) q[count + __popc(mask & lanemask_lt())] = k;
-    __syncwarp();
-    return count + __popc(mask);
-}
-
-// Removes the first 32 entries after a full batch.
-__device__ __forceinline__ int dequeue32(uint32_t *q, int count) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t moved = (lane + 32 < count) ? q[lane + 32] : 0u;
-    __syncwarp();
-    if (lane + 32 < count) q[lane] = moved;
-    __syncwarp();
-    return count - 32;
-}
-
-// ---------------------------------------------------------------------------
-// FP64 integrand, thread per sample.  One CTA processes chunks blockIdx.x,
-// blockIdx.x + gridDim.x, ...; within a chunk thread t screens samples
-// first + t, first + t + B, ... with the FP32 action of the FP32 point (fast
-// pipes).  Samples that may carry weight (within skip_window of m_ref, plus
-// a margin of 1 + 1% of S, far above the ~1e-4 FP32 error) go to the warp's
-// queue and are evaluated in FP64: Philox words drawn again, FP64 point,
-// action, products and weight.
-// ---------------------------------------------------------------------------
-template <int NX, int NT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f64(const IntegrandArgs args,
-                                                                                 const LatticeConst<double> lc,
-                                                                                 const LatticeConst<float> lcf,
-                                                                                 const RoundKeys rk) {
-    constexpr int D = NX * NT;
-    constexpr int R = NX / 2 + 1;
-    constexpr int K = sum_count(R);
-    constexpr int WARPS = BLOCK / 32;
-    __shared__ ChunkShared<BLOCK> sh;
-    __shared__ double s_lo[D], s_w[D];
-    __shared__ float2 s_box[D];  // the same bounds as floats, for the FP32 screen
-    __shared__ double s_sums[K * BLOCK];
-    __shared__ uint32_t s_queue[WARPS][kQueueCap];
-    const int tid = threadIdx.x, lane = tid & 31;
-    uint32_t *queue = s_queue[tid >> 5];
-    SmemSums<double, K, BLOCK> acc{s_sums + tid};
-
-    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
-        const ChunkView v = chunk_view(args, c, D);
-        if (tid < D) {
-            s_lo[tid] = v.lo[tid];
-            s_w[tid] = v.hi[tid] - v.lo[tid];
-            BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
-        }
-        const float hint = args.hint[v.s];
-        float m_ref = hint;
-        double m_acc = static_cast<double>(hint);
-        if (tid == 0) {
-            sh.min_bits = __float_as_int(hint);
-            sh.evaluated = 0u;
-        }
-        acc.zero();
-        __syncthreads();
-
-        unsigned n_eval = 0;
-        int count = 0;
-        // FP64 evaluation of queue entry 'lane' (a sample offset in the chunk)
-        auto evaluate = [&](uint32_t k) {
-            uint32_t w[D];
-            sample_words<D>(v.first + k, v.sid, rk, w);
-            double u[D];
-#pragma unroll
-            for (int j = 0; j < D; ++j) u[j] = Coord<double>::map(w[j], s_lo[j], s_w[j]);
-            const double S = action<NX, NT, double>(u, lc);
-            m_ref = fminf(m_ref, __double2float_rn(S));
-            double Q[R];
-            products<NX, NT, double>(u, Q);
-            if (S < m_acc - kRescaleMargin) {  // rare: move the shift down
-                rescale<double, K, R, BLOCK>(acc, exp(S - m_acc));
-                m_acc = S;
-            }
-            accumulate<double, K, R, BLOCK>(acc, exp(m_acc - S), Q);
-            ++n_eval;
-        };
-        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
-        for (uint64_t row = 0; row < nrows; ++row) {
-            const uint64_t k = row * BLOCK + tid;
-            bool cand = false;
-            if (k < v.cnt) {
-                float uf[D];
-                make_point_smem<D>(v.first + k, v.sid, rk, s_box, uf);
-                const float S_f = action<NX, NT, float>(uf, lcf);
-                cand = S_f <= m_ref + args.skip_window + 1.0f + 0.01f * S_f;
-            }
-            count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
-            if (count >= 32) {
-                evaluate(queue[lane]);
-                count = dequeue32(queue, count);
-            }
-            m_ref = warp_min(m_ref);
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&sh.min_bits, m_ref);
-        }
-        if (lane < count) evaluate(queue[lane]);
-        add_evaluated(args.stats, n_eval, &sh.evaluated);
-        chunk_record<double, K, R, BLOCK>(acc, m_acc, sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// FP32 integrand.  Points, action, products and weights in float; per-thread
-// Kahan sums; merges in double.  Candidates are queued as above; a candidate
-// whose FP32 action lies within kRefineWindow of m_ref (the weights that
-// matter) gets its action recomputed in compensated FP32 (action_df); all
-// others have weights below e^-kRefineWindow of the largest, where the ~1e-5
-// FP32 action error is harmless.
-// ---------------------------------------------------------------------------
-constexpr float kRefineWindow = 28.f;
-
-template <int NX, int NT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, BFI_INTEGRAND_MIN_BLOCKS) integrand_f32(const IntegrandArgs args,
-                                                                                 const LatticeConst<float> lc,
-                                                                                 const LatticeConstDF lcd,
-                                                                                 const RoundKeys rk) {
-    constexpr int D = NX * NT;
-    constexpr int R = NX / 2 + 1;
-    constexpr int K = sum_count(R);
-    constexpr int WARPS = BLOCK / 32;
-    using Sums = SmemSums<float, K, BLOCK>;
-    __shared__ ChunkShared<BLOCK> sh;
-    __shared__ float2 s_box[D];  // (lo, width) as floats; every thread reads the same word
-    __shared__ float s_sums[Sums::WORDS * BLOCK];
-    __shared__ uint32_t s_queue[WARPS][kQueueCap];
-    const int tid = threadIdx.x, lane = tid & 31;
-    uint32_t *queue = s_queue[tid >> 5];
-    Sums acc{s_sums + tid};
-
-    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
-        const ChunkView v = chunk_view(args, c, D);
-        if (tid < D) BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
-        const float hint = args.hint[v.s];
-        float m_acc = hint, m_ref = hint;
-        if (tid == 0) {
-            sh.min_bits = __float_as_int(hint);
-            sh.evaluated = 0u;
-        }
-        acc.zero();
-        __syncthreads();
-
-        unsigned n_eval = 0;
-        int count = 0;
-        auto evaluate = [&](uint32_t k) {
-            float u[D];
-            make_point_smem<D>(v.first + k, v.sid, rk, s_box, u);
-            const float S_f = action<NX, NT, float>(u, lc);
-            DF S{S_f, 0.f};
-            if (S_f < m_ref + kRefineWindow) {
-                S = action_df<NX, NT>(u, lcd);
-                m_ref = fminf(m_ref, S.h);
-            }
-            if (S.h < m_acc - kRescaleMargin) {  // rare: move the shift down
-                rescale<float, K, R, BLOCK>(acc, expf(S.h - m_acc));
-                m_acc = S.h;
-            }
-            float Q[R];
-            products<NX, NT, float>(u, Q);
-            accumulate<float, K, R, BLOCK>(acc, expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l)), Q);
-            ++n_eval;
-        };
-        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
-        for (uint64_t row = 0; row < nrows; ++row) {
-            const uint64_t k = row * BLOCK + tid;
-            bool cand = false;
-            if (k < v.cnt) {
-                float u[D];
-                make_point_smem<D>(v.first + k, v.sid, rk, s_box, u);
-                cand = action<NX, NT, float>(u, lc) <= m_ref + args.skip_window;
-            }
-            count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
-            if (count >= 32) {
-                evaluate(queue[lane]);
-                count = dequeue32(queue, count);
-            }
-            m_ref = warp_min(m_ref);
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&sh.min_bits, m_ref);
-        }
-        if (lane < count) evaluate(queue[lane]);
-        add_evaluated(args.stats, n_eval, &sh.evaluated);
-        chunk_record<float, K, R, BLOCK>(acc, static_cast<double>(m_acc), sh.f, &sh.mb, args.partials + c * (K + 2),
-                                         v.cnt);
-    }
-}
-
-// Per-subvolume hint: the smallest FP32 action among the first
-// min(n_s, kHintSamples) samples.  One CTA per subvolume.
-constexpr int kHintSamples = 4096;
-
-template <int NX, int NT>
-__global__ void __launch_bounds__(kBlock) hint_f32(const IntegrandArgs args, const LatticeConst<float> lc,
-                                                   const RoundKeys rk) {
-    constexpr int D = NX * NT;
-    __shared__ int s_min;
-    __shared__ float2 s_box[D];
-    const int64_t s = blockIdx.x;
-    if (threadIdx.x == 0) s_min = __float_as_int(INFINITY);
-    if (threadIdx.x < D) BoxPair<float>::load(args.lo + s * D, args.hi + s * D, threadIdx.x, s_box[threadIdx.x].x,
-                                              s_box[threadIdx.x].y);
-    __syncthreads();
-    const uint64_t n = min(args.samples[s], static_cast<uint64_t>(kHintSamples));
-    const uint32_t sid = args.sub_id ? args.sub_id[s] : static_cast<uint32_t>(s);
-    float mn = INFINITY;
-    for (uint64_t k = threadIdx.x; k < n; k += blockDim.x) {
-        float u[D];
-        make_point_smem<D>(k, sid, rk, s_box, u);
-        mn = fminf(mn, action<NX, NT, float>(u, lc));
-    }
-    atomicMin(&s_min, __float_as_int(mn));
-    __syncthreads();
-    if (threadIdx.x == 0) args.hint[s] = __int_as_float(s_min);
-}
-
 // ---------------------------------------------------------------------------
 // Per-subvolume FP64 merge of chunk records, in chunk order.  Also scales the
 // unscaled products Q_r = d P_r back to P_r and records log V_s.
@@ -705,104 +186,14 @@ __global__ void points_kernel(const PointsArgs a, const RoundKeys rk) {
     }
 }
 
-template <int NX, int NT, typename Real>
-__global__ void eval_kernel(const EvalArgs a, const LatticeConst<Real> lc, const LatticeConstDF lcd, bool compensated) {
-    constexpr int D = NX * NT;
-    constexpr int R = NX / 2 + 1;
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= a.npts) return;
-    Real u[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) u[j] = static_cast<Real>(a.y[i * D + j]);
-    Real Q[R];
-    products<NX, NT, Real>(u, Q);
-    double S = static_cast<double>(action<NX, NT, Real>(u, lc));
-    if constexpr (sizeof(Real) == 4) {
-        if (compensated) {
-            const DF Sd = action_df<NX, NT>(u, lcd);
-            S = static_cast<double>(Sd.h) + static_cast<double>(Sd.l);
-        }
-    }
-    a.S[i] = S;
-#pragma unroll
-    for (int r = 0; r < R; ++r) a.P[i * R + r] = static_cast<double>(Q[r]) / static_cast<double>(D);
-}
-
-// ---------------------------------------------------------------------------
-// Host-side launchers and the table of compiled shapes.
-// ---------------------------------------------------------------------------
-template <typename Real>
-LatticeConst<Real> make_const(const LatticeParams &p) {
-    LatticeConst<Real> c;
-    const double c_adv = p.nonlinear * p.tau / (2.0 * p.a);
-    const double c_dif = p.nu * p.tau / (p.a * p.a);
-    c.c_adv = static_cast<Real>(c_adv);
-    c.k1 = static_cast<Real>(2.0 * c_dif - 1.0);
-    c.neg_c_dif = static_cast<Real>(-c_dif);
-    c.inv_2Dtau = static_cast<Real>(1.0 / (2.0 * p.D * p.tau));
-    c.half_mass2 = static_cast<Real>(0.5 * p.mass2);
-    return c;
-}
-
-LatticeConstDF make_const_df(const LatticeParams &p) {
-    LatticeConstDF c;
-    const double c_dif = p.nu * p.tau / (p.a * p.a);
-    c.c_adv = split_df(p.nonlinear * p.tau / (2.0 * p.a));
-    c.k1 = split_df(2.0 * c_dif - 1.0);
-    c.c_dif = split_df(c_dif);
-    c.inv_2Dtau = split_df(1.0 / (2.0 * p.D * p.tau));
-    c.half_mass2 = split_df(0.5 * p.mass2);
-    return c;
-}
-
-template <int NX, int NT, typename Real>
-cudaError_t launch_integrand(const IntegrandArgs &args, const LatticeParams &p, uint32_t seed, uint32_t job,
-                             int grid, cudaStream_t st) {
-    const RoundKeys rk = make_round_keys(seed, job);
-    hint_f32<NX, NT><<<static_cast<unsigned>(args.nsub), kBlock, 0, st>>>(args, make_const<float>(p), rk);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if constexpr (sizeof(Real) == 8)
-        integrand_f64<NX, NT, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<double>(p), make_const<float>(p), rk);
-    else
-        integrand_f32<NX, NT, kBlock><<<grid, kBlock, 0, st>>>(args, make_const<float>(p), make_const_df(p), rk);
-    return cudaGetLastError();
-}
-
-template <int NX, int NT, typename Real>
-cudaError_t occupancy_integrand(int *blocks_per_sm) {
-    if constexpr (sizeof(Real) == 8)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrand_f64<NX, NT, kBlock>, kBlock, 0);
-    else
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrand_f32<NX, NT, kBlock>, kBlock, 0);
-}
-
-template <int NX, int NT>
-cudaError_t launch_eval(const EvalArgs &a, const LatticeParams &p, int mode, cudaStream_t st) {
-    const int threads = 128;
-    const int64_t blocks = (a.npts + threads - 1) / threads;
-    if (blocks == 0) return cudaSuccess;
-    if (mode == 0)
-        eval_kernel<NX, NT, double><<<static_cast<unsigned>(blocks), threads, 0, st>>>(a, make_const<double>(p),
-                                                                                    make_const_df(p), false);
-    else
-        eval_kernel<NX, NT, float><<<static_cast<unsigned>(blocks), threads, 0, st>>>(a, make_const<float>(p),
-                                                                                   make_const_df(p), mode == 2);
-    return cudaGetLastError();
-}
-
-#define BFI_SHAPE_ENTRY(NX, NT)                                                                         \
-    {NX, NT,                                                                                            \
-     {launch_integrand<NX, NT, double>, launch_integrand<NX, NT, float>},                               \
-     {occupancy_integrand<NX, NT, double>, occupancy_integrand<NX, NT, float>},                         \
-     launch_eval<NX, NT>},
-
-static const ShapeKernels kShapes[] = {BFI_COMPILED_SHAPES(BFI_SHAPE_ENTRY)};
-
 const ShapeKernels *find_shape(int nx, int nt) {
-    for (const auto &s : kShapes)
-        if (s.nx == nx && s.nt == nt) return &s;
-    return nullptr;
+    for (auto table : {shapes_small, shapes_config}) {
+        int n = 0;
+        const ShapeKernels *t = table(&n);
+        for (int i = 0; i < n; ++i)
+            if (t[i].nx == nx && t[i].nt == nt) return &t[i];
+    }
+    return generic_shape(nx, nt);
 }
 
 cudaError_t launch_merges(const MergeArgs &m, const TotalsArgs &t, cudaStream_t st) {

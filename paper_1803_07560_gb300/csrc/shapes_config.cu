@@ -1,0 +1,20 @@
+// shapes_config.cu -- instantiates the thread-per-sample integrand kernels for the
+// lattice shapes listed in BFI_SHAPES_CONFIG (bfi_kernels.h).
+#include "integrand_kernels.cuh"
+
+namespace bfi {
+
+#define BFI_SHAPE_ENTRY(NX, NT)                                                   \
+    {NX, NT, 0,                                                                   \
+     {launch_integrand<NX, NT, double>, launch_integrand<NX, NT, float>},         \
+     {occupancy_integrand<NX, NT, double>, occupancy_integrand<NX, NT, float>},   \
+     launch_eval<NX, NT>},
+
+static const ShapeKernels kTable[] = {BFI_SHAPES_CONFIG(BFI_SHAPE_ENTRY)};
+
+const ShapeKernels *shapes_config(int *n) {
+    *n = static_cast<int>(sizeof(kTable) / sizeof(kTable[0]));
+    return kTable;
+}
+
+}  // namespace bfi

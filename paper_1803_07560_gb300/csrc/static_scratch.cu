@@ -149,7 +149,7 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
     int sms = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
         return cuda_fail("cudaDeviceGetAttribute", e);
-    if ((e = shape->occupancy[precision](&per_sm)) != cudaSuccess) return cuda_fail("occupancy query", e);
+    if ((e = shape->occupancy[precision](lattice->nx, lattice->nt, &per_sm)) != cudaSuccess) return cuda_fail("occupancy query", e);
     int64_t grid = static_cast<int64_t>(sms) * (per_sm > 0 ? per_sm : 1);
     grid = grid < nchunks ? grid : (nchunks > 0 ? nchunks : 1);
 

@@ -8,10 +8,13 @@ evaluated in FP64), within FP32_RTOL = 1e-6, the bound the FP32 path states.
 The records of the two sides use different shifts m_s (the device starts from
 a hint), so sums are compared after moving them to the oracle's shift.
 Statistical error estimates are variances that cancel (to ~0 when one sample
-dominates); they are compared at 1e-9 relative (FP64), or absolutely at that
-fraction of C(0).  In FP32 the variance of C(r) is a difference of float
-sums of size ~C(0)^2, so its square root has an absolute floor of about
-sqrt(eps_32) C(0) ~ 3e-4 C(0): FP32 errors are compared at FP32_ERR_ATOL C(0).
+dominates): the variance of C(r) is a difference of sums of size ~C(0)^2, so
+its square root has an absolute floor of about sqrt(eps) C(0); errors are
+compared at 1e-9 relative or FP64_ERR_ATOL C(0) (FP64), FP32_ERR_ATOL C(0)
+(FP32).  The second-order sums (w^2, w^2 P, w^2 P^2) only feed those errors
+and are compared at the errors' tolerance.  For lattices whose smallest
+action S is large, exp(-S) cannot be reproduced to better than ~eps S
+relative by any FP64 evaluation: the FP64 bound is max(1e-12, 16 eps S).
 """
 import numpy as np
 import pytest
@@ -25,7 +28,17 @@ pytestmark = pytest.mark.gpu
 FP64_RTOL = 1e-12
 FP32_RTOL = 1e-6
 FP32_ERR_ATOL = 1e-3
-SHAPES = [(2, 1), (3, 1), (4, 1), (2, 2), (3, 2), (4, 2), (10, 2)]
+FP64_ERR_ATOL = 1e-7
+# compiled thread-per-sample shapes, and shapes that run on the generic warp-per-sample kernel
+SHAPES = [(2, 1), (3, 1), (4, 1), (2, 2), (3, 2), (4, 2), (6, 2), (8, 2), (10, 2), (16, 2), (32, 2),
+          (4, 4), (6, 4), (8, 4), (10, 4), (16, 4)]
+GENERIC = [(5, 3), (7, 1), (12, 3), (32, 4), (64, 8)]
+
+
+def budget(nx, nt, base):
+    """Smaller budgets for big lattices, where the oracle is slow."""
+    d = nx * nt
+    return base if d <= 64 else max(3000, base // (d // 16))
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +69,14 @@ def run_oracle(job, fp32_points=False, nonlinear=1.0, mass2=0.0):
                             sub_id=job.sub_id, fp32_points=fp32_points)
 
 
-def assert_slots_close(g, o, R, rtol, rtol_var):
+def cond_rtol(rtol, m, eps):
+    """exp(-S) has relative error at least the absolute error of S, ~eps S:
+    for big lattices (S in the thousands) no two FP64 evaluations agree to
+    1e-12, so the bound grows to 16 eps S there."""
+    return np.maximum(rtol, 16.0 * eps * np.abs(m))
+
+
+def assert_slots_close(g, o, R, rtol, rtol_var, eps=2.0 ** -52):
     assert np.array_equal(g[:, 0], o[:, 0]), "sample counts differ"
     used = o[:, 0] > 0
     g, o = g[used], o[used]
@@ -64,27 +84,31 @@ def assert_slots_close(g, o, R, rtol, rtol_var):
     # 16: it lies within [min S - 1e-3, min S + 16] (the oracle's is min S)
     assert np.all(g[:, 1] >= o[:, 1] - 1e-3) and np.all(g[:, 1] <= o[:, 1] + 16.0 + 1e-3)
     np.testing.assert_allclose(g[:, 2], o[:, 2], rtol=1e-14, atol=1e-14)    # log V_s
+    rt = cond_rtol(rtol, o[:, 1], eps)[:, None]
     dm = g[:, 1] - o[:, 1]                                                  # express GPU sums in the oracle's shift
     f1, f2 = np.exp(-dm)[:, None], np.exp(-2 * dm)[:, None]
     sw, sw2 = g[:, 3:4] * f1, g[:, 4:5] * f2
     swp = g[:, 5:5 + R] * f1
     sw2p = g[:, 5 + R:5 + 2 * R] * f2
     sw2p2 = g[:, 5 + 2 * R:] * f2
-    np.testing.assert_allclose(sw, o[:, 3:4], rtol=rtol)
-    np.testing.assert_allclose(sw2, o[:, 4:5], rtol=rtol)
-    np.testing.assert_allclose(sw2p2, o[:, 5 + 2 * R:], rtol=rtol)
-    # |P_r| <= P_0 per sample: scale the cancelling sums by their r = 0 member
-    assert np.all(np.abs(swp - o[:, 5:5 + R]) <= rtol * o[:, 5:6])
-    assert np.all(np.abs(sw2p - o[:, 5 + R:5 + 2 * R]) <= rtol * o[:, 5 + R:5 + R + 1])
+    assert np.all(np.abs(sw - o[:, 3:4]) <= rt * o[:, 3:4])
+    # |P_r| <= P_0 per sample: scale the sums with P_r by their r = 0 member
+    assert np.all(np.abs(swp - o[:, 5:5 + R]) <= rt * o[:, 5:6])
+    # second-order sums only feed the error estimates
+    rv = np.maximum(rt, rtol_var)
+    assert np.all(np.abs(sw2 - o[:, 4:5]) <= rv * o[:, 4:5])
+    assert np.all(np.abs(sw2p - o[:, 5 + R:5 + 2 * R]) <= rv * o[:, 5 + R:5 + R + 1])
+    assert np.all(np.abs(sw2p2 - o[:, 5 + 2 * R:]) <= rv * o[:, 5 + 2 * R:5 + 2 * R + 1])
 
 
-def assert_totals_close(g, o, R, rtol, rtol_var, err_atol=None):
+def assert_totals_close(g, o, R, rtol, rtol_var, err_atol=None, m=0.0, eps=2.0 ** -52):
+    rtol = float(cond_rtol(rtol, m, eps))
     assert g[2] == o[2] and g[3] == o[3]
     assert abs(g[0] - o[0]) <= rtol * max(1.0, abs(o[0])) + rtol            # log Z  ->  Z within rtol
     assert np.all(np.abs(g[4:4 + R] - o[4:4 + R]) <= rtol * o[4])          # C(r), |C(r)| <= C(0)
-    np.testing.assert_allclose(g[1], o[1], rtol=rtol_var)
-    atol = (rtol_var if err_atol is None else err_atol) * o[4]
-    np.testing.assert_allclose(g[4 + R:], o[4 + R:], rtol=rtol_var, atol=atol)
+    np.testing.assert_allclose(g[1], o[1], rtol=max(rtol_var, rtol))
+    atol = (FP64_ERR_ATOL if err_atol is None else err_atol) * o[4]
+    np.testing.assert_allclose(g[4 + R:], o[4 + R:], rtol=max(rtol_var, rtol), atol=atol)
 
 
 # ---------------------------------------------------------------------------
@@ -106,13 +130,13 @@ def test_points_bit_exact(bfi, dev, precision, d, first):
 # ---------------------------------------------------------------------------
 # steps 2 and 4: action and products at given points
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("nx,nt", SHAPES)
+@pytest.mark.parametrize("nx,nt", SHAPES + GENERIC)
 @pytest.mark.parametrize("params", [dict(), dict(nu=0.3, D=2.0, a=0.7, tau=0.5, nonlinear=1.0, mass2=0.4),
                                     dict(nonlinear=0.0, mass2=1.0)])
 def test_eval_matches_oracle(bfi, dev, nx, nt, params):
     d = nx * nt
     rng = np.random.default_rng(nx * 10 + nt)
-    y = rng.uniform(-5, 5, (4096, d))
+    y = rng.uniform(-5, 5, (4096 if d <= 64 else 512, d))
     S_o, P_o = oracle.eval_points(oracle.lattice(nx, nt, **params), y)
     S, P = bfi.evaluate(bfi.lattice(nx, nt, **params), torch.tensor(y, device=dev), 0)
     np.testing.assert_allclose(S.cpu().numpy(), S_o, rtol=1e-13)
@@ -121,7 +145,7 @@ def test_eval_matches_oracle(bfi, dev, nx, nt, params):
     y32 = y.astype(np.float32).astype(np.float64)
     S_o32, P_o32 = oracle.eval_points(oracle.lattice(nx, nt, **params), y32)
     S32, P32 = bfi.evaluate(bfi.lattice(nx, nt, **params), torch.tensor(y32, device=dev), 1)
-    np.testing.assert_allclose(S32.cpu().numpy(), S_o32, rtol=2e-5)
+    np.testing.assert_allclose(S32.cpu().numpy(), S_o32, rtol=2e-5 * max(1, d // 32))
     assert np.all(np.abs(P32.cpu().numpy() - P_o32) <= 2e-6 * P_o32[:, :1])
     # the compensated FP32 action used near the minimum: ~2^-44 relative to the terms
     Sc, _ = bfi.evaluate(bfi.lattice(nx, nt, **params), torch.tensor(y32, device=dev), 2)
@@ -131,16 +155,17 @@ def test_eval_matches_oracle(bfi, dev, nx, nt, params):
 # ---------------------------------------------------------------------------
 # the whole path
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("nx,nt", SHAPES)
+@pytest.mark.parametrize("nx,nt", SHAPES + GENERIC)
 def test_integrate_fp64_ragged(bfi, dev, nx, nt):
-    job = workloads.small_ragged(nx, nt, seed=5 + nx, nsub=3, base=30_000)
+    job = workloads.small_ragged(nx, nt, seed=5 + nx, nsub=3, base=budget(nx, nt, 30_000))
     g_s, g_t, plan = run_gpu(bfi, dev, job, 0)
     info = plan.info()
-    assert info.chunks > 3 * 8  # several chunks per subvolume, ragged last ones
+    assert info.chunks >= 3 * 2  # several chunks per subvolume, ragged last ones
+    assert info.kernel == (1 if (nx, nt) in GENERIC else 0)
     o_s, o_t = run_oracle(job)
     R = nx // 2 + 1
     assert_slots_close(g_s, o_s, R, FP64_RTOL, 1e-9)
-    assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9)
+    assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9, m=o_s[:, 1].max())
 
 
 @pytest.mark.parametrize("nonlinear,mass2,params", [(0.0, 1.0, {}), (1.0, 0.5, dict(nu=0.4, a=0.8, tau=0.6, D=1.7))])
@@ -156,9 +181,9 @@ def test_integrate_fp64_parameters(bfi, dev, nonlinear, mass2, params):
     assert_totals_close(g_t, o_t, 3, FP64_RTOL, 1e-9)
 
 
-@pytest.mark.parametrize("nx,nt", [(3, 1), (4, 2), (10, 2)])
+@pytest.mark.parametrize("nx,nt", [(3, 1), (4, 2), (10, 2), (16, 4), (32, 2), (5, 3), (32, 4), (64, 8)])
 def test_integrate_fp32_against_fp32_points(bfi, dev, nx, nt):
-    job = workloads.small_ragged(nx, nt, seed=21 + nx, nsub=3, base=30_000)
+    job = workloads.small_ragged(nx, nt, seed=21 + nx, nsub=3, base=budget(nx, nt, 30_000))
     g_s, g_t, _ = run_gpu(bfi, dev, job, 1)
     o_s, o_t = run_oracle(job, fp32_points=True)
     R = nx // 2 + 1
@@ -206,10 +231,12 @@ def test_host_buffer_path_equals_device_path(bfi, dev):
     ctx.close()
 
 
-def test_unsupported_shape_is_an_error(bfi, dev):
+def test_every_shape_up_to_512_sites_is_supported(bfi, dev):
+    for nx, nt in [(5, 5), (2, 256), (512, 1), (3, 170)]:
+        assert bfi.Plan(bfi.lattice(nx, nt), [100]).info().kernel == 1
     with pytest.raises(bfi.BfiError) as e:
-        bfi.Plan(bfi.lattice(5, 5), [100])
-    assert e.value.status == 7
+        bfi.Plan(bfi.lattice(33, 16), [100])
+    assert e.value.status == 1
 
 
 # ---------------------------------------------------------------------------
