@@ -310,6 +310,11 @@ def run_bfi(args):
                                  "note": "FP64 mode draws FP64 points; the FP32 arithmetic bound (1e-6) is "
                                          "checked against the oracle on the same float points in the tests"}}
 
+    # ---- the batching workload: 256 uneven jobs in one CUDA graph (FP32) ----
+    batch = None
+    if not args.skip_batch and world == 1:
+        batch = run_batch(bfi, dev, stream)
+
     # ---- end to end through the host-buffer C-ABI call ----
     e2e = None
     if not args.skip_e2e:
@@ -320,7 +325,7 @@ def run_bfi(args):
         samples, times, cores = time_oracle(1)
         cpu = {"value": samples / times[0], "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": "32 of the 1024 subvolumes (every 32nd) x 2^20 points of the same job, FP64 oracle"}
-    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job)
+    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -356,7 +361,45 @@ def run_e2e(bfi, lat, job, local_rank, args, dist, dev, samples_all):
             "d2h_bytes_per_step": d2h}
 
 
-def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job):
+def run_batch(bfi, dev, stream, njobs=256):
+    """The batching workload: 256 jobs (Nx from {4,6,8,10,16,32}, Nt from
+    {2,4}, nu log-uniform in [0.1,10], 64-1024 subvolumes, 2^20-2^28 points,
+    seed 3) captured into one CUDA graph, FP32 evaluation and FP64 merge,
+    grid autotuned per shape; timed over graph replays with CUDA events."""
+    import torch
+    import workloads
+    jobs = workloads.batch_jobs(njobs, seed=3)
+    descs = []
+    for j in jobs:
+        descs.append(dict(lattice=bfi.lattice(j.nx, j.nt, j.nu, j.D, j.a, j.tau), samples=j.samples,
+                          lo=torch.tensor(j.lo, device=dev), hi=torch.tensor(j.hi, device=dev),
+                          seed=j.seed, job_id=j.job_id))
+    t0 = time.perf_counter()
+    b = bfi.Batch(descs, precision=bfi.FP32, nstreams=8, autotune=True)
+    create_s = time.perf_counter() - t0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.launch(stream)
+    torch.cuda.synchronize()
+    reps, total = 2, 0.0
+    for _ in range(reps):
+        ev0.record(stream)
+        b.launch(stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        total += ev0.elapsed_time(ev1)
+    ms = total / reps
+    samples = sum(j.total_samples for j in jobs)
+    shapes = sorted({(j.nx, j.nt) for j in jobs})
+    tuned = {f"{nx}x{nt}": bfi.autotune_grid(bfi.lattice(nx, nt), bfi.FP32) for nx, nt in shapes}
+    ok = all(bool(torch.isfinite(t[0]).item()) for t in b.totals)
+    b.close()
+    return {"workload": f"{njobs} jobs, Nx in {{4,6,8,10,16,32}}, Nt in {{2,4}}, nu log-uniform [0.1,10], "
+                        "64-1024 subvolumes, 2^20-2^28 points (seed 3), FP32 eval / FP64 merge, one CUDA graph",
+            "value": samples / (ms * 1e-3), "unit": "samples/s", "ms_per_launch": ms, "samples": samples,
+            "jobs": njobs, "graph_create_s": create_s, "ctas_per_sm": tuned, "all_finite": ok}
+
+
+def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch=None):
     if rank == 0:
         line = {
             "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
@@ -374,6 +417,7 @@ def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, f
                        "C": [float(x) for x in merged[4:4 + R]],
                        "C_err": [float(x) for x in merged[4 + R:4 + 2 * R]]},
             "fp32": fp32,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
 
@@ -387,6 +431,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--samples-log2", type=int, default=20,
                     help="points per subvolume of the FP64 job (the workload is 2^20; smaller for profiling)")
     args = ap.parse_args()

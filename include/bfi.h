@@ -156,6 +156,8 @@ typedef struct {
     int32_t slot_len;
     int32_t totals_len;
     size_t scratch_bytes;      /* device scratch owned by the plan */
+    int32_t ctas_per_sm_max;   /* occupancy limit of the integrand kernel */
+    int32_t ctas_per_sm;       /* CTAs per SM the grid uses now */
 } bfi_plan_info;
 
 bfi_status bfi_plan_get_info(const bfi_plan *plan, bfi_plan_info *info);
@@ -174,6 +176,12 @@ bfi_status bfi_plan_get_info(const bfi_plan *plan, bfi_plan_info *info);
 bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi,
                             const uint32_t *sub_id, uint32_t seed, uint32_t job_id,
                             double *slots, double *totals, void *stream);
+
+/* Persistent grid of the plan's integrand kernel: ctas_per_sm CTAs on each SM
+ * (1 .. the occupancy limit; 0 restores the default, the occupancy limit).
+ * The grid never changes the results (each chunk's record depends on the
+ * chunk only), only the speed.  Errors: BFI_E_INVALID. */
+bfi_status bfi_plan_set_grid(bfi_plan *plan, int32_t ctas_per_sm);
 
 /* Per-stage timing of bfi_plan_execute with CUDA events recorded on the
  * execution stream.  After bfi_plan_set_timing(plan, 1), each execution
@@ -214,6 +222,45 @@ bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, int64_t nsub
                                         const double *lo, const double *hi, const uint32_t *sub_id,
                                         uint32_t seed, uint32_t job_id, bfi_precision precision,
                                         double *slots, double *totals, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batches: many uneven jobs in one CUDA graph.                              */
+/* ------------------------------------------------------------------------ */
+
+/* One job of a batch (Sec. 3: a lattice, the extents of its subvolumes and
+ * their sample budgets).  Device arrays stay owned by the caller and must
+ * outlive the batch; 'samples' is read during bfi_batch_create only. */
+typedef struct {
+    bfi_lattice lattice;
+    int64_t nsub;
+    const uint64_t *samples;   /* host [nsub] */
+    const double *lo, *hi;     /* device [nsub * d] */
+    const uint32_t *sub_id;    /* device [nsub] or NULL */
+    uint32_t seed, job_id;
+    double *slots;             /* device [nsub * slot_len] out */
+    double *totals;            /* device [totals_len] out */
+} bfi_job;
+
+typedef struct bfi_batch bfi_batch;
+
+/* Plans every job (allocating its scratch) and captures all of their kernels
+ * into one CUDA graph whose branches run on 'nstreams' forked streams, so that
+ * small jobs overlap on the device.  With autotune != 0 the persistent grid of
+ * each lattice shape is first chosen by timing (bfi_autotune_grid, cached per
+ * process).  Results are those of bfi_plan_execute on each job alone.
+ * Errors: as bfi_plan_create, BFI_E_CUDA (capture). */
+bfi_status bfi_batch_create(bfi_batch **out, const bfi_job *jobs, int32_t njobs, bfi_precision precision,
+                            int device, int32_t nstreams, int32_t autotune);
+/* Replays the graph on 'stream' (asynchronous). */
+bfi_status bfi_batch_launch(bfi_batch *batch, void *stream);
+bfi_status bfi_batch_destroy(bfi_batch *batch);
+
+/* Autotuner of the persistent grid: times the integrand of a synthetic job of
+ * this lattice shape ([-5,5]^d, 64 subvolumes) at every CTAs-per-SM value up
+ * to the occupancy limit and returns the fastest; the choice is cached per
+ * (shape, precision, device) for the process.  Errors: as bfi_plan_create. */
+bfi_status bfi_autotune_grid(const bfi_lattice *lattice, bfi_precision precision, int device,
+                             int32_t *ctas_per_sm);
 
 /* ------------------------------------------------------------------------ */
 /* One-call integration with host buffers (the end-to-end path).            */

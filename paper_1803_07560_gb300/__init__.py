@@ -44,7 +44,17 @@ class PlanInfo(ctypes.Structure):
                 ("chunk_samples", ctypes.c_int64), ("total_samples", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("slot_len", ctypes.c_int32), ("totals_len", ctypes.c_int32),
-                ("scratch_bytes", ctypes.c_size_t)]
+                ("scratch_bytes", ctypes.c_size_t), ("ctas_per_sm_max", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+class Job(ctypes.Structure):
+    """One job of a batch (device arrays; host budgets)."""
+
+    _fields_ = [("lattice", Lattice), ("nsub", ctypes.c_int64), ("samples", ctypes.POINTER(ctypes.c_uint64)),
+                ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("sub_id", ctypes.c_void_p),
+                ("seed", ctypes.c_uint32), ("job_id", ctypes.c_uint32), ("slots", ctypes.c_void_p),
+                ("totals", ctypes.c_void_p)]
 
 
 def lattice(nx, nt, nu=1.0, D=1.0, a=1.0, tau=1.0, nonlinear=1.0, mass2=0.0) -> Lattice:
@@ -63,7 +73,13 @@ _SIGNATURES = {
     "bfi_plan_get_info": (ctypes.c_int, [_vp, _P(PlanInfo)]),
     "bfi_plan_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32,
                                         _vp, _vp, _vp]),
+    "bfi_plan_set_grid": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "bfi_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "bfi_batch_create": (ctypes.c_int, [_P(_vp), _vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int32, ctypes.c_int32]),
+    "bfi_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "bfi_batch_destroy": (ctypes.c_int, [_vp]),
+    "bfi_autotune_grid": (ctypes.c_int, [_P(Lattice), ctypes.c_int, ctypes.c_int, _P(ctypes.c_int32)]),
     "bfi_plan_get_timing": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "bfi_plan_get_stats": (ctypes.c_int, [_vp, _P(ctypes.c_uint64), _P(ctypes.c_float)]),
     "bfi_integrate_static_scratch": (ctypes.c_int, [_P(Lattice), ctypes.c_int64, _P(ctypes.c_uint64), _vp,
@@ -173,6 +189,10 @@ class Plan:
                                      _stream_ptr(stream)))
         return slots, totals
 
+    def set_grid(self, ctas_per_sm: int):
+        """Persistent grid: CTAs per SM (0 = occupancy limit); never changes results."""
+        _check(_lib.bfi_plan_set_grid(self._h, ctas_per_sm))
+
     def set_timing(self, enable: bool = True):
         _check(_lib.bfi_plan_set_timing(self._h, int(enable)))
 
@@ -259,6 +279,70 @@ def integrate_static_scratch(lat: Lattice, samples, lo, hi, seed: int, job_id: i
         seed & 0xFFFFFFFF, job_id & 0xFFFFFFFF, precision, _dev_ptr(slots, torch.float64),
         _dev_ptr(totals, torch.float64), _stream_ptr(stream)))
     return slots, totals
+
+
+def autotune_grid(lat: Lattice, precision: int = FP64, device: int = 0) -> int:
+    """CTAs per SM chosen by timing for this lattice shape (cached per process)."""
+    c = ctypes.c_int32()
+    _check(_lib.bfi_autotune_grid(ctypes.byref(lat), precision, device, ctypes.byref(c)))
+    return int(c.value)
+
+
+class Batch:
+    """Many jobs captured into one CUDA graph (one plan per job).
+
+    jobs: list of dicts with keys lattice, samples (host), lo, hi (CUDA float64
+    [nsub, d]), optional sub_id (CUDA int32), seed, job_id; outputs are
+    allocated here (self.slots[i], self.totals[i]) unless given."""
+
+    def __init__(self, jobs, precision: int = FP32, device: int = 0, nstreams: int = 8,
+                 autotune: bool = True):
+        import torch
+        arr = (Job * len(jobs))()
+        self._keep = []
+        self.slots, self.totals = [], []
+        for i, j in enumerate(jobs):
+            lat = j["lattice"]
+            smp = np.ascontiguousarray(np.atleast_1d(j["samples"]), dtype=np.uint64)
+            lo, hi = j["lo"], j["hi"]
+            slots = j.get("slots")
+            if slots is None:
+                slots = torch.empty((smp.size, slot_len(lat.nx)), dtype=torch.float64, device=lo.device)
+            totals = j.get("totals")
+            if totals is None:
+                totals = torch.empty(totals_len(lat.nx), dtype=torch.float64, device=lo.device)
+            sid = j.get("sub_id")
+            arr[i].lattice = lat
+            arr[i].nsub = smp.size
+            arr[i].samples = smp.ctypes.data_as(_P(ctypes.c_uint64))
+            arr[i].lo = _dev_ptr(lo, torch.float64)
+            arr[i].hi = _dev_ptr(hi, torch.float64)
+            arr[i].sub_id = None if sid is None else _dev_ptr(sid, torch.int32)
+            arr[i].seed = j.get("seed", 0) & 0xFFFFFFFF
+            arr[i].job_id = j.get("job_id", i) & 0xFFFFFFFF
+            arr[i].slots = _dev_ptr(slots, torch.float64)
+            arr[i].totals = _dev_ptr(totals, torch.float64)
+            self._keep += [smp, lo, hi, sid]
+            self.slots.append(slots)
+            self.totals.append(totals)
+        handle = ctypes.c_void_p()
+        _check(_lib.bfi_batch_create(ctypes.byref(handle), ctypes.cast(arr, ctypes.c_void_p), len(jobs),
+                                     precision, device, nstreams, int(autotune)))
+        self._h = handle
+
+    def launch(self, stream=None):
+        _check(_lib.bfi_batch_launch(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.bfi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def merge_host(nx: int, slots) -> np.ndarray:

@@ -107,6 +107,7 @@ struct bfi_plan {
     const bfi::ShapeKernels *shape = nullptr;
     int64_t nsub = 0, nchunks = 0, chunk_samples = 0, total = 0;
     int grid = 1;
+    int sms = 1, per_sm_max = 1, per_sm = 1;
     int R = 0, K = 0, d = 0;
     std::vector<uint64_t> samples;
     int64_t *d_chunk_off = nullptr;
@@ -198,7 +199,10 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
         delete p;
         return fail(BFI_E_CUDA, "device query failed: %s", cudaGetErrorString(e));
     }
-    const int64_t resident = static_cast<int64_t>(sms) * (per_sm > 0 ? per_sm : 1);
+    p->sms = sms;
+    p->per_sm_max = per_sm > 0 ? per_sm : 1;
+    p->per_sm = p->per_sm_max;
+    const int64_t resident = static_cast<int64_t>(sms) * p->per_sm_max;
     p->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(p->nchunks, resident)));
 
     const size_t off_bytes = sizeof(int64_t) * (nsub + 1);
@@ -236,6 +240,8 @@ bfi_status bfi_plan_get_info(const bfi_plan *plan, bfi_plan_info *info) {
     info->slot_len = 5 + 3 * plan->R;
     info->totals_len = 4 + 2 * plan->R;
     info->scratch_bytes = plan->scratch_bytes;
+    info->ctas_per_sm_max = plan->per_sm_max;
+    info->ctas_per_sm = plan->per_sm;
     return BFI_OK;
 }
 
@@ -262,6 +268,17 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
         BFI_CUDA(cudaEventRecord(plan->ev[2], st));
         plan->timed = true;
     }
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_set_grid(bfi_plan *plan, int32_t ctas_per_sm) {
+    if (!plan) return fail(BFI_E_INVALID, "plan is NULL");
+    if (ctas_per_sm < 0 || ctas_per_sm > plan->per_sm_max)
+        return fail(BFI_E_INVALID, "ctas_per_sm = %d outside 0..%d", ctas_per_sm, plan->per_sm_max);
+    const int per_sm = ctas_per_sm == 0 ? plan->per_sm_max : ctas_per_sm;
+    plan->per_sm = per_sm;
+    const int64_t resident = static_cast<int64_t>(plan->sms) * per_sm;
+    plan->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(plan->nchunks, resident)));
     return BFI_OK;
 }
 

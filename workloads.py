@@ -90,3 +90,30 @@ def small_ragged(nx: int, nt: int, seed: int = 5, nsub: int = 3, base: int = 40_
     lo, hi = lo[:nsub], hi[:nsub]
     samples = np.array([base + 1237 * s + 3 for s in range(nsub)], dtype=np.uint64)
     return Job(nx, nt, lo, hi, samples, seed=seed, name=f"{nx}x{nt} ragged")
+
+
+def batch_jobs(njobs: int = 256, seed: int = 3, extra_64x8: float = 0.0, rng=None):
+    """Uneven jobs: Nx from {4,6,8,10,16,32}, Nt from {2,4}, nu log-uniform in
+    [0.1,10], D = 1, box [-5,5]^d bisected along its first coordinates into
+    2^k subvolumes with k uniform in 6..10 (64-1024), a total budget
+    log-uniform in [2^20, 2^28] points split evenly; job k has job_id k and
+    Philox seed 'seed'.  A fraction extra_64x8 of the jobs are 64x8 lattices
+    instead.  The parameters are drawn with numpy's PCG64 seeded by 'seed'."""
+    rng = np.random.default_rng(seed) if rng is None else rng
+    jobs = []
+    for k in range(njobs):
+        if extra_64x8 > 0 and rng.uniform() < extra_64x8:
+            nx, nt = 64, 8
+        else:
+            nx = int(rng.choice([4, 6, 8, 10, 16, 32]))
+            nt = int(rng.choice([2, 4]))
+        nu = float(np.exp(rng.uniform(np.log(0.1), np.log(10.0))))
+        kk = int(rng.integers(6, 11))
+        total = float(np.exp(rng.uniform(20 * np.log(2), 28 * np.log(2))))
+        d = nx * nt
+        lo, hi = bisected_boxes(d, min(kk, d))
+        nsub = lo.shape[0]
+        per = max(1, int(total) // nsub)
+        jobs.append(Job(nx, nt, lo, hi, np.full(nsub, per, dtype=np.uint64), seed=seed, job_id=k, nu=nu,
+                        name=f"batch job {k}: {nx}x{nt}, nu={nu:.3g}, {nsub} x {per}"))
+    return jobs
