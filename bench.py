@@ -315,6 +315,11 @@ def run_bfi(args):
     if not args.skip_batch and world == 1:
         batch = run_batch(bfi, dev, stream)
 
+    # ---- the serving workload: jobs arriving while others run ----
+    serving = None
+    if args.serving_seconds > 0 and world == 1:
+        serving = run_serving(bfi, args.serving_seconds)
+
     # ---- end to end through the host-buffer C-ABI call ----
     e2e = None
     if not args.skip_e2e:
@@ -325,7 +330,7 @@ def run_bfi(args):
         samples, times, cores = time_oracle(1)
         cpu = {"value": samples / times[0], "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": "32 of the 1024 subvolumes (every 32nd) x 2^20 points of the same job, FP64 oracle"}
-    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch)
+    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch, serving)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -399,7 +404,55 @@ def run_batch(bfi, dev, stream, njobs=256):
             "jobs": njobs, "graph_create_s": create_s, "ctas_per_sm": tuned, "all_finite": ok}
 
 
-def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch=None):
+def run_serving(bfi, seconds, rate=200.0, seed=5):
+    """The serving workload: Poisson arrivals at 'rate' jobs/s for 'seconds',
+    sizes from the batching distribution plus 5% 64x8 lattices (numpy PCG64,
+    seed 5), FP32, 8 stream slots, 40 GB admission budget, subvolumes split
+    once when their relative variance exceeds 1e-2.  Latency = submit to
+    result; throughput = samples of all passes / wall time until the last
+    result."""
+    import workloads
+    rng = np.random.default_rng(seed)
+    srv = bfi.Server(slots=8, precision=bfi.FP32, memory_budget=40 << 30, split_rel_var=1e-2,
+                     max_split_rounds=1)
+    reqs, offered = [], 0
+    t0 = time.perf_counter()
+    t_next = 0.0
+    while True:
+        t_next += float(rng.exponential(1.0 / rate))
+        if t_next > seconds:
+            break
+        job = workloads.batch_jobs(1, seed=3, extra_64x8=0.05, rng=rng)[0]
+        job.job_id = len(reqs)
+        delay = t0 + t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        reqs.append(srv.submit(bfi.lattice(job.nx, job.nt, job.nu, job.D, job.a, job.tau), job.lo, job.hi,
+                               job.samples, job.seed, job.job_id))
+        offered += job.total_samples
+    t_submit_end = time.perf_counter()
+    infos = []
+    for r in reqs:
+        r.wait(600_000)
+        infos.append(r.info())
+        r.release()
+    t_end = time.perf_counter()
+    lat = np.array([i.latency_ms for i in infos])
+    samples = sum(int(i.samples) for i in infos)
+    st = srv.stats()
+    srv.close()
+    return {"workload": f"Poisson {rate:g} jobs/s for {seconds:g} s, batching sizes + 5% 64x8 (seed 5), FP32, "
+                        "8 slots, 40 GB budget, split at Var(Z_s)/Z_s^2 > 1e-2 (1 round)",
+            "jobs": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "samples_per_s": samples / (t_end - t0), "samples": samples,
+            "offered_samples_per_s_first_pass": offered / (t_submit_end - t0),
+            "wall_s": t_end - t0, "passes": int(sum(i.passes for i in infos)),
+            "leaves": int(sum(i.nsub_final for i in infos)), "completed": int(st.completed),
+            "failed": int(st.failed), "peak_device_bytes": int(st.bytes_peak)}
+
+
+def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch=None,
+           serving=None):
     if rank == 0:
         line = {
             "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
@@ -418,6 +471,7 @@ def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, f
                        "C_err": [float(x) for x in merged[4 + R:4 + 2 * R]]},
             "fp32": fp32,
             "batch": batch,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
 
@@ -432,6 +486,8 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
+                    help="arrival window of the serving workload (the full workload is 60 s; 0 skips it)")
     ap.add_argument("--samples-log2", type=int, default=20,
                     help="points per subvolume of the FP64 job (the workload is 2^20; smaller for profiling)")
     args = ap.parse_args()

@@ -263,6 +263,83 @@ bfi_status bfi_autotune_grid(const bfi_lattice *lattice, bfi_precision precision
                              int32_t *ctas_per_sm);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: jobs admitted as they arrive, with adaptive splitting.           */
+/* ------------------------------------------------------------------------ */
+
+/* A server runs submitted jobs concurrently on one device: a scheduler thread
+ * admits the next pass of a job whenever one of 'slots' streams is free and
+ * the job's device memory fits in what remains of 'memory_budget'; passes of
+ * different jobs overlap on the GPU.  After a pass, every subvolume whose
+ * relative variance Var(Z_s)/Z_s^2 exceeds 'split_rel_var' is bisected along
+ * its widest side and both halves are evaluated again with the parent's
+ * budget (Sec. 3: subdivision of non-converged subvolumes; the paper's
+ * re-evaluation doubles the samples of a region), for at most
+ * 'max_split_rounds' rounds and at most 16 times the initial subvolume count;
+ * the result merges the final (leaf) subvolumes.  Children draw Philox
+ * streams with new sub_ids, numbered on from the job's largest, in subvolume
+ * order, so a job's result does not depend on what else runs.  No call waits
+ * without a bound. */
+typedef struct {
+    int32_t device;
+    int32_t slots;              /* jobs on the GPU at once (one stream each), >= 1 */
+    uint64_t memory_budget;     /* device bytes the server may hold for admitted jobs */
+    bfi_precision precision;    /* BFI_FP64 or BFI_FP32 */
+    double split_rel_var;       /* <= 0: never split */
+    int32_t max_split_rounds;
+} bfi_server_config;
+
+typedef struct bfi_server bfi_server;
+typedef struct bfi_request bfi_request;
+
+typedef struct {
+    int32_t state;              /* 0 queued, 1 running, 2 done, 3 cancelled, 4 failed */
+    bfi_status status;          /* of a failed job */
+    int64_t nsub_final;         /* leaf subvolumes of the result */
+    int32_t passes;             /* evaluation passes run */
+    uint64_t samples;           /* samples over all passes */
+    double queued_ms;           /* submit -> first pass admitted */
+    double latency_ms;          /* submit -> result ready */
+} bfi_request_info;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled;
+    uint64_t samples;           /* over completed passes */
+    uint64_t bytes_in_use, bytes_peak;
+    int32_t running, queued;
+} bfi_server_stats;
+
+/* Errors: BFI_E_INVALID, BFI_E_CUDA (no such device, stream or pool creation). */
+bfi_status bfi_server_create(bfi_server **out, const bfi_server_config *config);
+/* Cancels queued jobs, waits for running passes, stops the scheduler.  Release
+ * every request handle of the server before destroying it. */
+bfi_status bfi_server_destroy(bfi_server *server);
+bfi_status bfi_server_get_stats(bfi_server *server, bfi_server_stats *stats);
+
+/* Queues a job; host arrays (lo, hi [nsub * d], samples [nsub]) are copied
+ * before the call returns.  *out is the caller's handle (release it with
+ * bfi_request_release).  Errors: BFI_E_INVALID, BFI_E_UNSUPPORTED, BFI_E_BUSY
+ * (server stopping). */
+bfi_status bfi_submit(bfi_server *server, const bfi_lattice *lattice, int64_t nsub, const double *lo,
+                      const double *hi, const uint64_t *samples, uint32_t seed, uint32_t job_id,
+                      bfi_request **out);
+/* *done = 1 once the request is done, cancelled or failed. */
+bfi_status bfi_poll(bfi_request *request, int32_t *done);
+/* Waits at most timeout_ms (< 0: no limit) for the request to end.  Returns
+ * BFI_OK when done, BFI_E_TIMEOUT, BFI_E_CANCELLED, or the failure status. */
+bfi_status bfi_wait(bfi_request *request, int64_t timeout_ms);
+/* Cancels a queued or running job (a running pass finishes; its results are dropped). */
+bfi_status bfi_cancel(bfi_request *request);
+bfi_status bfi_request_get_info(bfi_request *request, bfi_request_info *info);
+/* Result of a done request: totals [totals_len]; optionally the leaf
+ * subvolumes: slots [nsub_final * slot_len], lo and hi [nsub_final * d],
+ * sub_id [nsub_final] (any of them NULL to skip).  Errors: BFI_E_BUSY (not
+ * done), BFI_E_CANCELLED, the failure status. */
+bfi_status bfi_request_get_result(bfi_request *request, double *totals, double *slots, double *lo, double *hi,
+                                  uint32_t *sub_id);
+/* Drops the caller's handle (a job still queued or running is cancelled). */
+bfi_status bfi_request_release(bfi_request *request);
+
+/* ------------------------------------------------------------------------ */
 /* One-call integration with host buffers (the end-to-end path).            */
 /* ------------------------------------------------------------------------ */
 

@@ -48,6 +48,24 @@ class PlanInfo(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32), ("memory_budget", ctypes.c_uint64),
+                ("precision", ctypes.c_int), ("split_rel_var", ctypes.c_double),
+                ("max_split_rounds", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int), ("nsub_final", ctypes.c_int64),
+                ("passes", ctypes.c_int32), ("samples", ctypes.c_uint64), ("queued_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("samples", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64),
+                ("bytes_peak", ctypes.c_uint64), ("running", ctypes.c_int32), ("queued", ctypes.c_int32)]
+
+
 class Job(ctypes.Structure):
     """One job of a batch (device arrays; host budgets)."""
 
@@ -85,6 +103,17 @@ _SIGNATURES = {
     "bfi_integrate_static_scratch": (ctypes.c_int, [_P(Lattice), ctypes.c_int64, _P(ctypes.c_uint64), _vp,
                                                     _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
                                                     _vp, _vp, _vp]),
+    "bfi_server_create": (ctypes.c_int, [_P(_vp), _P(ServerConfig)]),
+    "bfi_server_destroy": (ctypes.c_int, [_vp]),
+    "bfi_server_get_stats": (ctypes.c_int, [_vp, _P(ServerStats)]),
+    "bfi_submit": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, ctypes.c_uint32,
+                                  ctypes.c_uint32, _P(_vp)]),
+    "bfi_poll": (ctypes.c_int, [_vp, _P(ctypes.c_int32)]),
+    "bfi_wait": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "bfi_cancel": (ctypes.c_int, [_vp]),
+    "bfi_request_get_info": (ctypes.c_int, [_vp, _P(RequestInfo)]),
+    "bfi_request_get_result": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "bfi_request_release": (ctypes.c_int, [_vp]),
     "bfi_ctx_create": (ctypes.c_int, [_P(_vp), ctypes.c_int]),
     "bfi_ctx_destroy": (ctypes.c_int, [_vp]),
     "bfi_integrate": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, _vp,
@@ -336,6 +365,106 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             _lib.bfi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Request:
+    """A job submitted to a Server."""
+
+    def __init__(self, handle, server, lat: Lattice):
+        self._h = handle
+        self._server = server
+        self.lattice = lat
+
+    def poll(self) -> bool:
+        done = ctypes.c_int32()
+        _check(_lib.bfi_poll(self._h, ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, timeout_ms: int = -1):
+        """Returns when done; raises BfiError (status 4 on timeout, 5 if cancelled)."""
+        _check(_lib.bfi_wait(self._h, int(timeout_ms)))
+
+    def cancel(self):
+        _check(_lib.bfi_cancel(self._h))
+
+    def info(self) -> RequestInfo:
+        info = RequestInfo()
+        _check(_lib.bfi_request_get_info(self._h, ctypes.byref(info)))
+        return info
+
+    def result(self, leaves: bool = False):
+        """totals, or (totals, slots, lo, hi, sub_id) of the leaf subvolumes."""
+        lat = self.lattice
+        totals = np.empty(totals_len(lat.nx))
+        if not leaves:
+            _check(_lib.bfi_request_get_result(self._h, ctypes.c_void_p(totals.ctypes.data), None, None, None,
+                                               None))
+            return totals
+        n = self.info().nsub_final
+        d = lat.nx * lat.nt
+        slots = np.empty((n, slot_len(lat.nx)))
+        lo = np.empty((n, d))
+        hi = np.empty((n, d))
+        sid = np.empty(n, dtype=np.uint32)
+        _check(_lib.bfi_request_get_result(self._h, ctypes.c_void_p(totals.ctypes.data),
+                                           ctypes.c_void_p(slots.ctypes.data), ctypes.c_void_p(lo.ctypes.data),
+                                           ctypes.c_void_p(hi.ctypes.data), ctypes.c_void_p(sid.ctypes.data)))
+        return totals, slots, lo, hi, sid
+
+    def release(self):
+        if getattr(self, "_h", None):
+            _lib.bfi_request_release(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Server:
+    """Jobs admitted as they arrive (streams x memory budget), adaptive splitting."""
+
+    def __init__(self, device: int = 0, slots: int = 8, memory_budget: int = 40 << 30,
+                 precision: int = FP32, split_rel_var: float = 0.0, max_split_rounds: int = 0):
+        cfg = ServerConfig(device, slots, memory_budget, precision, split_rel_var, max_split_rounds)
+        handle = ctypes.c_void_p()
+        _check(_lib.bfi_server_create(ctypes.byref(handle), ctypes.byref(cfg)))
+        self._h = handle
+        self._requests = []
+
+    def submit(self, lat: Lattice, lo, hi, samples, seed: int, job_id: int = 0) -> Request:
+        d = lat.nx * lat.nt
+        lo_a, lo_p = _host(np.reshape(lo, (-1, d)), np.float64)
+        hi_a, hi_p = _host(np.reshape(hi, (-1, d)), np.float64)
+        nsub = lo_a.shape[0]
+        smp_a, smp_p = _host(np.broadcast_to(np.asarray(samples, dtype=np.uint64), (nsub,)), np.uint64)
+        h = ctypes.c_void_p()
+        _check(_lib.bfi_submit(self._h, ctypes.byref(lat), nsub, lo_p, hi_p, smp_p, seed & 0xFFFFFFFF,
+                               job_id & 0xFFFFFFFF, ctypes.byref(h)))
+        req = Request(h, self, lat)
+        self._requests.append(req)
+        return req
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(_lib.bfi_server_get_stats(self._h, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for r in self._requests:
+                r.release()
+            self._requests = []
+            _lib.bfi_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
