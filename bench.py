@@ -267,17 +267,15 @@ def run_bfi(args):
                                                      flush_buf, dist, stream)
     clocks = sampler.stop() if sampler else None
 
-    # the exchange: gather every rank's subvolume records, merge on rank 0
+    # the exchange: gather every rank's subvolume records, merge in FP64
+    from paper_1803_07560_gb300 import shard
     if dist is not None:
-        gathered = [torch.empty_like(slots) for _ in range(world)]
-        dist.all_gather(gathered, slots)
-        all_slots = torch.cat(gathered).cpu().numpy()
+        merged = shard.merge_across_ranks(NX, slots)
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     else:
-        all_slots = slots.cpu().numpy()
-    merged = bfi.merge_host(NX, all_slots)
+        merged = bfi.merge_host(NX, slots.cpu().numpy())
 
     samples_all = world * job.total_samples
     value = samples_all / (ms * 1e-3)
