@@ -313,6 +313,11 @@ def run_bfi(args):
     if not args.skip_batch and world == 1:
         batch = run_batch(bfi, dev, stream)
 
+    # ---- stated error of C(r) against the budget (time to 1e-3) ----
+    tte = None
+    if not args.skip_tte and world == 1:
+        tte = run_time_to_error(bfi, dev, stream)
+
     # ---- the serving workload: jobs arriving while others run ----
     serving = None
     if args.serving_seconds > 0 and world == 1:
@@ -328,7 +333,7 @@ def run_bfi(args):
         samples, times, cores = time_oracle(1)
         cpu = {"value": samples / times[0], "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": "32 of the 1024 subvolumes (every 32nd) x 2^20 points of the same job, FP64 oracle"}
-    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch, serving)
+    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch, serving, tte)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -402,6 +407,40 @@ def run_batch(bfi, dev, stream, njobs=256):
             "jobs": njobs, "graph_create_s": create_s, "ctas_per_sm": tuned, "all_finite": ok}
 
 
+def run_time_to_error(bfi, dev, stream, log2_budgets=range(10, 25, 2), target=1e-3):
+    """Stated error of C(r) against the sample budget on the 10x2 job (FP32,
+    1024 subvolumes x 2^k points), the time of each run (CUDA events), and the
+    1/sqrt(n) extrapolation of the budget and time that reach 'target'."""
+    import torch
+    import workloads
+    lat = bfi.lattice(NX, NT)
+    curve = []
+    for k in log2_budgets:
+        job = workloads.paper_10x2(1 << k)
+        lo, hi = torch.tensor(job.lo, device=dev), torch.tensor(job.hi, device=dev)
+        plan = bfi.Plan(lat, job.samples, bfi.FP32)
+        plan.execute(lo, hi, job.seed, stream=stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, tot = plan.execute(lo, hi, job.seed, stream=stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        t = tot.cpu().numpy()
+        C, Ce = t[4:4 + R], t[4 + R:4 + 2 * R]
+        curve.append({"samples": job.total_samples, "ms": ev0.elapsed_time(ev1),
+                      "C_err_rel_max": float(np.max(Ce / np.abs(C))), "C_err_over_C0_max": float(np.max(Ce) / C[0]),
+                      "Z_err_rel": float(t[1])})
+        plan.close()
+    last = curve[-1]
+    rate = last["samples"] / (last["ms"] * 1e-3)
+    out = {"workload": "10x2 job (1024 subvolumes), FP32, budgets 2^20..2^34", "target": target, "curve": curve}
+    for key in ("C_err_rel_max", "C_err_over_C0_max"):
+        need = last["samples"] * (last[key] / target) ** 2
+        out[f"samples_to_target_{key}"] = need
+        out[f"seconds_to_target_{key}"] = need / rate
+    return out
+
+
 def run_serving(bfi, seconds, rate=200.0, seed=5):
     """The serving workload: Poisson arrivals at 'rate' jobs/s for 'seconds',
     sizes from the batching distribution plus 5% 64x8 lattices (numpy PCG64,
@@ -450,7 +489,7 @@ def run_serving(bfi, seconds, rate=200.0, seed=5):
 
 
 def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch=None,
-           serving=None):
+           serving=None, tte=None):
     if rank == 0:
         line = {
             "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
@@ -470,6 +509,7 @@ def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, f
             "fp32": fp32,
             "batch": batch,
             "serving": serving,
+            "time_to_error": tte,
         }
         print(json.dumps(line), flush=True)
 
@@ -484,6 +524,7 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-tte", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="arrival window of the serving workload (the full workload is 60 s; 0 skips it)")
     ap.add_argument("--samples-log2", type=int, default=20,
