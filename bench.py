@@ -48,6 +48,13 @@ ISSUE_PEAK_OPS = 128 * SM_COUNT * SM_MAX_MHZ * 1e6   # thread-instructions/s (FP
 FP64_PEAK_OPS = 2 * SM_COUNT * SM_MAX_MHZ * 1e6      # FP64 operations/s
 
 
+# DRAM bytes (read + write) of one full-size launch of the FP64 10x2 integrand
+# kernel, from ncu's dram__bytes_read.sum + dram__bytes_write.sum (a 1-pass
+# capture; profiles/integrand_f64_10x2.md).  Must be reset to None whenever
+# that kernel changes.
+TRAFFIC_FP64_10x2 = 596220
+
+
 def screen_ops(nx, nt):
     """Per sample, every sample: Philox words, FP32 point, FP32 action."""
     d = nx * nt
@@ -189,9 +196,10 @@ def run_reference(args):
 
 
 def workload_config(world, per_sub=SAMPLES_PER_SUB):
-    return {"workload": "10x2 lattice (d=20), nu=D=a=tau=1, box [-5,5]^20 bisected along coords "
-                        f"0..9 into 1024 subvolumes per GPU, 2^{int(math.log2(per_sub))} Philox4x32-10 "
-                        "points each (seed 2), FP64",
+    d = NX * NT
+    return {"workload": f"{NX}x{NT} lattice (d={d}), nu=D=a=tau=1, box [-5,5]^{d} bisected along coords "
+                        f"0..{min(10, d) - 1} into 1024 subvolumes per GPU, 2^{int(math.log2(per_sub))} "
+                        "Philox4x32-10 points each (seed 2), FP64",
             "model": None, "global_batch": world * NSUB_PER_RANK * per_sub,
             "subvolumes_per_gpu": NSUB_PER_RANK, "samples_per_subvolume": per_sub,
             "parallelism": f"subvolume shards x{world}",
@@ -201,7 +209,7 @@ def workload_config(world, per_sub=SAMPLES_PER_SUB):
 def make_job(rank, world, samples_per_sub):
     import workloads
     k = 10 + int(round(math.log2(world)))
-    lo, hi = workloads.bisected_boxes(D, k)
+    lo, hi = workloads.bisected_boxes(D, min(k, D))
     sl = slice(rank * NSUB_PER_RANK, (rank + 1) * NSUB_PER_RANK)
     return workloads.Job(NX, NT, lo[sl], hi[sl], np.full(NSUB_PER_RANK, samples_per_sub, dtype=np.uint64),
                          seed=2, sub_id=np.arange(sl.start, sl.stop, dtype=np.uint32))
@@ -279,8 +287,10 @@ def run_bfi(args):
 
     samples_all = world * job.total_samples
     value = samples_all / (ms * 1e-3)
-    roof = roofline(job.total_samples, n_eval, kern_ms, "fp64")
-    roof["kernel"] = "hint_f32<10,2> + integrand_f64<10,2>"
+    roof = roofline(job.total_samples, n_eval, kern_ms, "fp64", NX, NT)
+    roof["kernel"] = f"hint + integrand FP64 <{NX},{NT}>"
+    if (NX, NT) == (10, 2) and args.samples_log2 == 20:
+        roof["traffic"] = TRAFFIC_FP64_10x2
 
     # ---- FP32 form of the same job with 2^24 points per subvolume ----
     fp32 = None
@@ -289,8 +299,8 @@ def run_bfi(args):
         plan32 = bfi.Plan(lat, job32.samples, bfi.FP32, device=local_rank)
         ms32, kern32, _, tot32, n_eval32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
                                                        max(1, args.warmup // 2), flush_buf, dist, stream)
-        roof32 = roofline(job32.total_samples, n_eval32, kern32, "fp32")
-        roof32["kernel"] = "hint_f32<10,2> + integrand_f32<10,2>"
+        roof32 = roofline(job32.total_samples, n_eval32, kern32, "fp32", NX, NT)
+        roof32["kernel"] = f"hint + integrand FP32 <{NX},{NT}>"
         plan32.close()
         # the same 2^34-point job in FP64 mode (its own FP64 points): the FP32
         # result's total difference, arithmetic plus point rounding
@@ -515,7 +525,10 @@ def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, f
 
 
 def main():
+    global NX, NT, D, R, K
     ap = argparse.ArgumentParser()
+    ap.add_argument("--lattice", default="10x2",
+                    help="NXxNT of the timed job (the workload is 10x2; others for profiling other kernels)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -530,6 +543,9 @@ def main():
     ap.add_argument("--samples-log2", type=int, default=20,
                     help="points per subvolume of the FP64 job (the workload is 2^20; smaller for profiling)")
     args = ap.parse_args()
+    NX, NT = (int(x) for x in args.lattice.lower().split("x"))
+    D, R = NX * NT, NX // 2 + 1
+    K = 2 + 3 * R
     if args.impl == "reference":
         run_reference(args)
     else:

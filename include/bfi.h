@@ -50,7 +50,8 @@
  *    smallest action of the subvolume.  BFI_FP32 evaluates the points, the
  *    action, the products and the weights in float, accumulates per thread in
  *    Kahan-compensated float, and merges in double.  Its shift m_s starts at
- *    the smallest FP32 action among the subvolume's first 4096 samples and
+ *    the smallest FP32 action among the subvolume's first n_s/32 samples
+ *    (256 to 4096) and
  *    moves down only when a sample beats it by more than 16.  Samples whose
  *    FP32 action lies within 28 of the smallest action seen get the action
  *    recomputed in compensated FP32 (pairs of floats carrying the rounding
@@ -64,10 +65,11 @@
  *    e^-W of the largest, and all such samples together move any sum by less
  *    than e^-c relative.  They are counted in n_s but left out of the sums.
  *    BFI_FP64 decides this from the FP32 action of the FP32 point with a
- *    margin of 1 + 1% of S (the FP32 error is ~1e-4).  The reference action
- *    starts at the smallest FP32 action among each subvolume's first 4096
- *    samples and follows the smallest evaluated action, shared within a CTA
- *    at fixed points of the sample loop, so the outcome is reproducible.
+ *    margin of 1 + 0.1% of S, far above the difference between the two.
+ *    The reference action starts at the smallest FP32 action among each
+ *    subvolume's first n_s/32 samples (256 to 4096) and follows the smallest evaluated
+ *    action, shared at fixed points of the sample loop, so the outcome is
+ *    reproducible.
  *  - Errors: every call returns a bfi_status; bfi_last_error() gives a
  *    message for the calling thread.  No call aborts the process.
  *  - Pointers: "host" pointers are ordinary CPU memory, "device" pointers

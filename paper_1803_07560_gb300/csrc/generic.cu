@@ -22,6 +22,7 @@ constexpr int kGWarps = kGBlock / 32;
 
 struct GenShape {
     int nx, nt, d, R, K, nq;
+    int dpad;  // per-warp stride of the point buffers: d rounded up to 4 (vector stores stay aligned)
 };
 
 GenShape gen_shape(int nx, int nt) {
@@ -32,6 +33,7 @@ GenShape gen_shape(int nx, int nt) {
     g.R = nx / 2 + 1;
     g.K = 2 + 3 * g.R;
     g.nq = (g.d + 3) / 4;
+    g.dpad = 4 * g.nq;
     return g;
 }
 
@@ -49,8 +51,8 @@ __host__ __device__ inline GenLayout gen_layout(const GenShape &g) {
     L.box_f = o; o = align16(o + 8 * g.d);                    // float2 (lo, width)
     L.lo_d = o;  o = align16(o + 8 * g.d);                    // double lo
     L.w_d = o;   o = align16(o + 8 * g.d);                    // double width
-    L.uf = o;    o = align16(o + 4 * g.d * kGWarps);          // float point per warp
-    L.ud = o;    o = align16(o + 8 * g.d * kGWarps);          // double point per warp
+    L.uf = o;    o = align16(o + 4 * g.dpad * kGWarps);       // float point per warp
+    L.ud = o;    o = align16(o + 8 * g.dpad * kGWarps);       // double point per warp
     L.sums = o;  o = align16(o + 8 * (g.K + g.R + 1) * kGWarps);  // per-warp sums (FP64, or FP32 sums + comps)
     L.mw = o;    o = align16(o + 8 * kGWarps + 8);             // per-warp shift, counter
     L.total = o;
@@ -74,6 +76,16 @@ __device__ __forceinline__ DF warp_sum_df(DF v) {
 }
 
 __device__ __forceinline__ int wrap(int j, int d) { return j >= d ? j - d : (j < 0 ? j + d : j); }
+
+// Four consecutive values at a 16-byte (float) or 32-byte (double) aligned
+// address: the warp's slices are 16-aligned and j is a multiple of 4.
+__device__ __forceinline__ void store4(float *p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double *p, double a, double b, double c, double d) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+}
 
 // S at the point u (shared memory), every lane gets the same value.
 template <typename Real>
@@ -121,37 +133,55 @@ __device__ DF warp_action_df(const float *u, const uint16_t *next, const GenShap
 }
 
 // Q_r = sum_j u_j u_{j + r Nt (mod d)} for the distances r this lane owns
-// (r = lane + 32 i), handed to f(r, Q_r).  FP32 sums are compensated.
+// (r = lane + 32 i), handed to f(r, Q_r).  Each lane starts its sweep at
+// j = lane, so at every step the lanes read consecutive words (no bank
+// conflicts); the order is fixed per lane, so the result is reproducible.
+// FP32 sums are compensated.
 template <typename F>
 __device__ __forceinline__ void lane_products(const double *u, const GenShape &g, F f) {
-    for (int r = threadIdx.x & 31; r < g.R; r += 32) {
+    const int lane = threadIdx.x & 31;
+    for (int r = lane; r < g.R; r += 32) {
         double q = 0.0;
-        for (int j = 0; j < g.d; ++j) q = fma(u[j], u[wrap(j + r * g.nt, g.d)], q);
+        int j = lane % g.d, jr = wrap(j + r * g.nt, g.d);
+        for (int t = 0; t < g.d; ++t) {
+            q = fma(u[j], u[jr], q);
+            j = (j + 1 == g.d) ? 0 : j + 1;
+            jr = (jr + 1 == g.d) ? 0 : jr + 1;
+        }
         f(r, q);
     }
 }
 
 template <typename F>
 __device__ __forceinline__ void lane_products(const float *u, const GenShape &g, F f) {
-    for (int r = threadIdx.x & 31; r < g.R; r += 32) {
+    const int lane = threadIdx.x & 31;
+    for (int r = lane; r < g.R; r += 32) {
         DF q{0.f, 0.f};
-        for (int j = 0; j < g.d; ++j) q = df_add(q, two_prod(u[j], u[wrap(j + r * g.nt, g.d)]));
+        int j = lane % g.d, jr = wrap(j + r * g.nt, g.d);
+        for (int t = 0; t < g.d; ++t) {
+            q = df_add(q, two_prod(u[j], u[jr]));
+            j = (j + 1 == g.d) ? 0 : j + 1;
+            jr = (jr + 1 == g.d) ? 0 : jr + 1;
+        }
         f(r, q.h + q.l);
     }
 }
 
-// Philox blocks q = lane, lane + 32, ... of sample i mapped into u.
+// Philox blocks q = lane, lane + 32, ... of sample i mapped into u; a full
+// block is written with one vector store (conflict-free), the ragged last one
+// word by word.
 template <typename Real, typename Box>
 __device__ __forceinline__ void warp_point(uint64_t i, uint32_t sid, const RoundKeys &rk, const GenShape &g, Box box,
                                            Real *u) {
     for (int q = threadIdx.x & 31; q < g.nq; q += 32) {
         const uint4 b = philox4x32_10(
             make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
-        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int j = 4 * q + t;
-            if (j < g.d) u[j] = box(j, w4[t]);
+        const int j = 4 * q;
+        if (j + 4 <= g.d) {
+            store4(u + j, box(j, b.x), box(j + 1, b.y), box(j + 2, b.z), box(j + 3, b.w));
+        } else {
+            const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+            for (int t = 0; t < 4 && j + t < g.d; ++t) u[j + t] = box(j + t, w4[t]);
         }
     }
     __syncwarp();
@@ -203,8 +233,8 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
     const float2 *bf = reinterpret_cast<const float2 *>(sm + L.box_f);
     const double *ld = reinterpret_cast<const double *>(sm + L.lo_d);
     const double *wd = reinterpret_cast<const double *>(sm + L.w_d);
-    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.d;
-    double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.d;
+    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.dpad;
+    double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.dpad;
     double *mw = reinterpret_cast<double *>(sm + L.mw);
     unsigned *cnt_all = reinterpret_cast<unsigned *>(mw + kGWarps);
     // per-warp sums: FP64 -> double[K]; FP32 -> float[K] then float comps[1 + R]
@@ -232,7 +262,7 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
             warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
             const float S_f = warp_action<float>(uf, next, g, ga.cf);
             if (FP64) {
-                if (!(S_f <= m_ref + args.skip_window + 1.0f + 0.01f * S_f)) continue;
+                if (!(S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f)) continue;
                 warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<double>::map(w, ld[j], wd[j]); }, ud);
                 const double S = warp_action<double>(ud, next, g, ga.cd);
                 m_ref = fminf(m_ref, __double2float_rn(S));
@@ -325,7 +355,7 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
 }
 
 // Per-subvolume reference action: the smallest FP32 action among the first
-// min(n_s, 4096) samples.  One CTA per subvolume, warp per sample.
+// hint_samples(n_s) samples.  One CTA per subvolume, warp per sample.
 __global__ void __launch_bounds__(kGBlock) generic_hint(const GenArgs ga) {
     extern __shared__ __align__(16) unsigned char sm[];
     const IntegrandArgs &args = ga.a;
@@ -340,9 +370,9 @@ __global__ void __launch_bounds__(kGBlock) generic_hint(const GenArgs ga) {
     __syncthreads();
     const uint16_t *next = reinterpret_cast<const uint16_t *>(sm + L.next);
     const float2 *bf = reinterpret_cast<const float2 *>(sm + L.box_f);
-    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.d;
+    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.dpad;
     const uint32_t sid = args.sub_id ? args.sub_id[s] : static_cast<uint32_t>(s);
-    const uint64_t n = min(args.samples[s], static_cast<uint64_t>(4096));
+    const uint64_t n = hint_samples(args.samples[s]);
     float mn = INFINITY;
     for (uint64_t k = warp; k < n; k += kGWarps) {
         warp_point<float>(k, sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
@@ -365,8 +395,8 @@ __global__ void __launch_bounds__(kGBlock) generic_eval(const EvalArgs a, const 
     const int64_t i = blockIdx.x * static_cast<int64_t>(kGWarps) + warp;
     if (i >= a.npts) return;  // warp-uniform
     const uint16_t *next = reinterpret_cast<const uint16_t *>(sm + L.next);
-    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.d;
-    double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.d;
+    float *uf = reinterpret_cast<float *>(sm + L.uf) + warp * g.dpad;
+    double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.dpad;
     for (int j = lane; j < g.d; j += 32) {
         ud[j] = a.y[i * g.d + j];
         uf[j] = static_cast<float>(a.y[i * g.d + j]);

@@ -358,9 +358,12 @@ __device__ __forceinline__ int dequeue32(uint32_t *q, int count) {
 // blockIdx.x + gridDim.x, ...; within a chunk thread t screens samples
 // first + t, first + t + B, ... with the FP32 action of the FP32 point (fast
 // pipes).  Samples that may carry weight (within skip_window of m_ref, plus
-// a margin of 1 + 1% of S, far above the ~1e-4 FP32 error) go to the warp's
+// a margin of 1 + 0.1% of S) go to the warp's
 // queue and are evaluated in FP64: Philox words drawn again, FP64 point,
-// action, products and weight.
+// action, products and weight.  The margin bounds |S_f32(y_f32) - S(y_f64)|:
+// the FP32 rounding of the action (~(d + 10) eps_32 S) plus the point
+// difference (|y_f32 - y_f64| <= ~1.1e-6, times sum_j |dS/dy_j| <=
+// ~52 sqrt(2 d S) for unit parameters: 0.004 at 10x2, 0.3 at 64x8).
 // ---------------------------------------------------------------------------
 template <int NX, int NT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(const IntegrandArgs args,
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
                 float uf[D];
                 make_point_smem<D>(v.first + k, v.sid, rk, s_box, uf);
                 const float S_f = action<NX, NT, float>(uf, lcf);
-                cand = S_f <= m_ref + args.skip_window + 1.0f + 0.01f * S_f;
+                cand = S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f;
             }
             count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
             if (count >= 32) {
@@ -525,9 +528,12 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
     }
 }
 
-// Per-subvolume hint: the smallest FP32 action among the first
-// min(n_s, kHintSamples) samples.  One CTA per subvolume.
-constexpr int kHintSamples = 4096;
+// Per-subvolume hint: the smallest FP32 action among the subvolume's first
+// hint_samples(n_s) samples (n_s/32, at least 256 and at most 4096: a few
+// percent of the work at most).  One CTA per subvolume.
+__host__ __device__ constexpr uint64_t hint_samples(uint64_t n) {
+    return n < 256 ? n : (n / 32 < 256 ? 256 : (n / 32 > 4096 ? 4096 : n / 32));
+}
 
 template <int NX, int NT>
 __global__ void __launch_bounds__(kBlock) hint_f32(const IntegrandArgs args, const LatticeConst<float> lc,
@@ -540,7 +546,7 @@ __global__ void __launch_bounds__(kBlock) hint_f32(const IntegrandArgs args, con
     if (threadIdx.x < D) BoxPair<float>::load(args.lo + s * D, args.hi + s * D, threadIdx.x, s_box[threadIdx.x].x,
                                               s_box[threadIdx.x].y);
     __syncthreads();
-    const uint64_t n = min(args.samples[s], static_cast<uint64_t>(kHintSamples));
+    const uint64_t n = hint_samples(args.samples[s]);
     const uint32_t sid = args.sub_id ? args.sub_id[s] : static_cast<uint32_t>(s);
     float mn = INFINITY;
     for (uint64_t k = threadIdx.x; k < n; k += blockDim.x) {
