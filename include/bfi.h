@@ -369,6 +369,24 @@ bfi_status bfi_integrate(bfi_ctx *ctx, const bfi_lattice *lattice, int64_t nsub,
                          double *slots, double *totals);
 
 /* ------------------------------------------------------------------------ */
+/* The N-sphere test integrand of Sec. 3 (Listings 1 and 2).                 */
+/* ------------------------------------------------------------------------ */
+
+/* Plain Monte Carlo of f(x) = sqrt(max(0, 1 - |x|^2)) over the box
+ * prod [lo_j, hi_j] (host arrays, 1 <= dims <= 32), n >= 2 samples with the
+ * lattice integrand's points (Philox counter (j/4, i mod 2^32, i / 2^32,
+ * sub_id), key (seed, job_id), FP64 points); over [-1,1]^k its integral is
+ * half the volume of the unit (k+1)-ball.  Outputs the line of the paper's
+ * integrand protocol: result = V mean f, abs_err = V sigma / sqrt(n) (unbiased
+ * sigma) and, if split_dim is not NULL, the coordinate j across which f is
+ * least even, the largest |sum_{x_j < mid} f - sum_{x_j >= mid} f| (the paper
+ * prints a suggestion without stating a rule; this is ours).  Synchronous on
+ * 'device'.  Errors: BFI_E_INVALID, BFI_E_CUDA. */
+bfi_status bfi_nsphere(int32_t dims, const double *lo, const double *hi, uint64_t n, uint32_t seed,
+                       uint32_t job_id, uint32_t sub_id, double *result, double *abs_err, int32_t *split_dim,
+                       int device);
+
+/* ------------------------------------------------------------------------ */
 /* FP64 merge of subvolume records on the host.                             */
 /* ------------------------------------------------------------------------ */
 

@@ -369,10 +369,11 @@ void oracle_points(int d, const double *lo, const double *hi, uint32_t sid, uint
 /* Its integral over [-1,1]^k is half the volume of the unit (k+1)-ball.     */
 /* ------------------------------------------------------------------------- */
 void oracle_nsphere(int dims, const double *lo, const double *hi, uint64_t n,
-                    uint32_t seed, uint32_t job_id, double *result, double *abs_err)
+                    uint32_t seed, uint32_t job_id, double *result, double *abs_err, int *split_dim)
 {
     uint32_t *words = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)dims);
     double *x = (double *)malloc(sizeof(double) * (size_t)dims);
+    nsum *below = (nsum *)calloc((size_t)dims, sizeof(nsum));
     double vol = 1.0;
     for (int j = 0; j < dims; ++j) vol *= hi[j] - lo[j];
     nsum sf = {0, 0}, sf2 = {0, 0};
@@ -384,11 +385,26 @@ void oracle_nsphere(int dims, const double *lo, const double *hi, uint64_t n,
         double f = r2 < 1.0 ? sqrt(1.0 - r2) : 0.0;
         nsum_add(&sf, f);
         nsum_add(&sf2, f * f);
+        /* how unevenly f falls on the two halves of each coordinate */
+        for (int j = 0; j < dims; ++j)
+            if (x[j] < 0.5 * (lo[j] + hi[j])) nsum_add(&below[j], f);
     }
     double nn = (double)n;
     double mean = nsum_value(&sf) / nn;
     double var = (nsum_value(&sf2) - nsum_value(&sf) * nsum_value(&sf) / nn) / (nn - 1.0);
     *result = vol * mean;
     *abs_err = vol * sqrt(var / nn);
-    free(words); free(x);
+    /* split suggestion (Sec. 3 prints one; the rule is our reading): the
+     * coordinate with the largest |sum below the midpoint - sum above it| */
+    if (split_dim) {
+        int best = 0;
+        double best_gap = -1.0;
+        for (int j = 0; j < dims; ++j) {
+            double b = nsum_value(&below[j]);
+            double gap = fabs(b - (nsum_value(&sf) - b));
+            if (gap > best_gap) { best_gap = gap; best = j; }
+        }
+        *split_dim = best;
+    }
+    free(words); free(x); free(below);
 }

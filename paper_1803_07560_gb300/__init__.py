@@ -114,6 +114,9 @@ _SIGNATURES = {
     "bfi_request_get_info": (ctypes.c_int, [_vp, _P(RequestInfo)]),
     "bfi_request_get_result": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "bfi_request_release": (ctypes.c_int, [_vp]),
+    "bfi_nsphere": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_uint32, _P(ctypes.c_double), _P(ctypes.c_double),
+                                   _P(ctypes.c_int32), ctypes.c_int]),
     "bfi_ctx_create": (ctypes.c_int, [_P(_vp), ctypes.c_int]),
     "bfi_ctx_destroy": (ctypes.c_int, [_vp]),
     "bfi_integrate": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, _vp,
@@ -141,6 +144,7 @@ def _load_library():
 
 _lib = _load_library()
 LIBRARY_PATH = _build.LIB
+CLI_PATH = _build.CLI  # the line-protocol integrand program (Sec. 3), built beside the library
 
 
 def _check(status: int):
@@ -472,6 +476,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def nsphere(dims: int, n: int, seed: int, job_id: int = 0, lo=-1.0, hi=1.0, sub_id: int = 0, device: int = 0):
+    """(result, abs_err, split_dim) of the N-sphere integrand of Sec. 3 on the GPU."""
+    lo_a, lo_p = _host(np.broadcast_to(np.asarray(lo, dtype=np.float64), (dims,)), np.float64)
+    hi_a, hi_p = _host(np.broadcast_to(np.asarray(hi, dtype=np.float64), (dims,)), np.float64)
+    res, err, sd = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(_lib.bfi_nsphere(dims, lo_p, hi_p, int(n), seed, job_id, sub_id, ctypes.byref(res), ctypes.byref(err),
+                            ctypes.byref(sd), device))
+    return res.value, err.value, sd.value
 
 
 def merge_host(nx: int, slots) -> np.ndarray:

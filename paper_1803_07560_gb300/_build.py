@@ -16,6 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build", platform.machine())  # per host architecture
 LIB = os.path.join(OUT_DIR, "libbfi.so")
+CLI_SRC = os.path.join(PKG, "cli", "bfi_cli.cpp")
+CLI = os.path.join(OUT_DIR, "bfi_cli")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,13 +37,13 @@ def _sources():
 
 
 def _deps():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "bfi.h"), __file__]
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "bfi.h"), CLI_SRC, __file__]
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(CLI):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(CLI))
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
@@ -78,9 +80,25 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    _build_cli()
     if verbose or ptxas_info:
         print("\n".join(logs))
     return LIB
+
+
+def _build_cli() -> None:
+    """The line-protocol integrand program, linked against libbfi.so (found
+    beside it at run time)."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        raise RuntimeError("no C++ compiler found for bfi_cli")
+    tmp = CLI + f".tmp{os.getpid()}"
+    cmd = [cxx, "-O2", "-std=c++17", "-Wall", f"-I{INCLUDE}", CLI_SRC, "-o", tmp, f"-L{OUT_DIR}", "-lbfi",
+           "-Wl,-rpath,$ORIGIN"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"bfi_cli build failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, CLI)
 
 
 if __name__ == "__main__":

@@ -216,3 +216,14 @@ def test_edge_cases_empty_and_single_sample():
     # one sample: a value but no variance estimate
     _, t1 = oracle.integrate(lat, lo[:1], hi[:1], [1], seed=1)
     assert np.isfinite(t1[0]) and np.isinf(t1[1])
+
+
+def test_nsphere_split_suggestion():
+    # The split suggestion is the coordinate across which the integrand is least
+    # even.  On [-1,1]^2 x [0,1] the ball's density falls along the third
+    # coordinate only; on a box symmetric in every coordinate no coordinate is
+    # preferred beyond noise, so a box lopsided in the first one picks it.
+    _, _, sd = oracle.nsphere(3, 200_000, 1, lo=[-1, -1, 0], hi=[1, 1, 1], split=True)
+    assert sd == 2
+    _, _, sd = oracle.nsphere(3, 200_000, 2, lo=[-0.2, -1, -1], hi=[1, 1, 1], split=True)
+    assert sd == 0
