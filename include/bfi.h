@@ -387,6 +387,72 @@ bfi_status bfi_nsphere(int32_t dims, const double *lo, const double *hi, uint64_
                        int device);
 
 /* ------------------------------------------------------------------------ */
+/* Adaptive subdivision with the convergence test of Sec. 3.                  */
+/* ------------------------------------------------------------------------ */
+
+/* Sec. 3: the volume is subdivided until each subvolume has converged.  A
+ * subvolume is evaluated twice, with n samples and with factor * n, and has
+ * converged when at least one of these holds for the two results r1, r2:
+ *   (1) |r1 - r2| <= rel_tol * max(|r1|, |r2|)
+ *   (2) |r1 - r2| <= abs_tol
+ *   (3) max(|r1|, |r2|) <= small
+ * (a criterion whose threshold is <= 0 is off).  A converged subvolume keeps
+ * its second evaluation; any other is halved along its split dimension and
+ * both halves are evaluated in the next round with n and factor * n samples.
+ * All subvolumes of a round go to the GPU in one launch.
+ *
+ * The tree is numbered like a heap: the whole volume is node 1, the halves of
+ * node h are 2h (lower) and 2h + 1 (upper); node h's evaluations draw points
+ * with sub_id 2h (n samples) and 2h + 1 (factor * n samples), so every result
+ * is reproducible from (seed, job_id) alone.  A subvolume at depth max_depth
+ * (the whole volume has depth 0; max_depth <= 30) is kept unconverged, and a
+ * round that would evaluate more than max_leaves subvolumes halves them in
+ * tree order while there is room and keeps the rest unconverged. */
+typedef struct {
+    double factor;       /* second evaluation: ceil(factor * n) samples, factor >= 1 (the paper doubles) */
+    double rel_tol;      /* criterion (1) */
+    double abs_tol;      /* criterion (2) */
+    double small;        /* criterion (3) */
+    int32_t max_depth;   /* 0..30 */
+    int64_t max_leaves;  /* >= 1 */
+} bfi_convergence;
+
+typedef struct {
+    int64_t rounds;            /* rounds of evaluation */
+    int64_t evaluated;         /* subvolumes evaluated (each twice) */
+    int64_t converged;         /* kept because a criterion held */
+    int64_t kept_depth;        /* kept unconverged at max_depth */
+    int64_t kept_budget;       /* kept unconverged for lack of room in max_leaves */
+    int64_t leaves;            /* subvolumes in the result = converged + kept_depth + kept_budget */
+    uint64_t samples;          /* samples drawn in all evaluations */
+} bfi_adaptive_stats;
+
+/* The N-sphere integrand over prod [lo_j, hi_j] (host arrays, dims <= 32):
+ * result = sum of the kept second evaluations, abs_err = the root of the sum
+ * of their squared errors.  The split dimension is the N-sphere
+ * integrand's suggestion.  Synchronous on 'device'; stats may be NULL.
+ * Errors: BFI_E_INVALID, BFI_E_CUDA. */
+bfi_status bfi_adaptive_nsphere(int32_t dims, const double *lo, const double *hi, uint64_t n, uint32_t seed,
+                                uint32_t job_id, const bfi_convergence *conv, double *result, double *abs_err,
+                                bfi_adaptive_stats *stats, int device);
+
+/* The lattice integral of Eq. (Gen2) over the box prod [lo_j, hi_j] (host
+ * arrays [d]) with the context's device: the test compares r = Z_s (done in
+ * logarithms, so Z_s may lie outside the double range), a subvolume is
+ * halved along its widest side (the first on ties), and totals (host
+ * [bfi_totals_len(nx)]) is the FP64 merge of the kept second evaluations.
+ * The kept subvolumes, in the order they are kept (by round, then by
+ * position in the round), go to leaf_lo / leaf_hi (host
+ * [leaf_capacity * d]) and leaf_slots (host [leaf_capacity *
+ * bfi_slot_len(nx)]) when those are not NULL, the first leaf_capacity of
+ * them; stats->leaves tells how many there are.  Errors: BFI_E_INVALID,
+ * BFI_E_UNSUPPORTED, BFI_E_NOMEM, BFI_E_CUDA. */
+bfi_status bfi_adaptive_integrate(bfi_ctx *ctx, const bfi_lattice *lattice, const double *lo, const double *hi,
+                                  uint64_t n, uint32_t seed, uint32_t job_id, bfi_precision precision,
+                                  const bfi_convergence *conv, double *totals, bfi_adaptive_stats *stats,
+                                  int64_t leaf_capacity, double *leaf_lo, double *leaf_hi, double *leaf_slots);
+
+/* ------------------------------------------------------------------------ */
 /* FP64 merge of subvolume records on the host.                             */
 /* ------------------------------------------------------------------------ */
 

@@ -78,7 +78,7 @@ def _load():
                                   ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                   ctypes.c_int, dp]
     lib.oracle_nsphere.argtypes = [ctypes.c_int, dp, dp, ctypes.c_uint64, ctypes.c_uint32,
-                                   ctypes.c_uint32, dp, dp, P(ctypes.c_int)]
+                                   ctypes.c_uint32, ctypes.c_uint32, dp, dp, P(ctypes.c_int)]
     _lib = lib
     return lib
 
@@ -185,7 +185,7 @@ def integrate(lat: Lattice, lo, hi, samples, seed: int, job_id: int = 0, sub_id=
     return slots, totals
 
 
-def nsphere(dims: int, n: int, seed: int, job_id: int = 0, lo=-1.0, hi=1.0, split: bool = False):
+def nsphere(dims: int, n: int, seed: int, job_id: int = 0, lo=-1.0, hi=1.0, split: bool = False, sub_id: int = 0):
     """Plain MC of sqrt(max(0, 1-|x|^2)) over a box (the integrand of Sec. 3):
     (result, abs_err), or (result, abs_err, split_dim) with split=True."""
     lib = _load()
@@ -193,5 +193,5 @@ def nsphere(dims: int, n: int, seed: int, job_id: int = 0, lo=-1.0, hi=1.0, spli
     hi_a = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, dtype=np.float64), (dims,)))
     res, err, sd = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     lib.oracle_nsphere(dims, _ptr(lo_a, ctypes.c_double), _ptr(hi_a, ctypes.c_double), n,
-                       seed, job_id, ctypes.byref(res), ctypes.byref(err), ctypes.byref(sd))
+                       seed, job_id, sub_id, ctypes.byref(res), ctypes.byref(err), ctypes.byref(sd))
     return (res.value, err.value, sd.value) if split else (res.value, err.value)

@@ -369,7 +369,8 @@ void oracle_points(int d, const double *lo, const double *hi, uint32_t sid, uint
 /* Its integral over [-1,1]^k is half the volume of the unit (k+1)-ball.     */
 /* ------------------------------------------------------------------------- */
 void oracle_nsphere(int dims, const double *lo, const double *hi, uint64_t n,
-                    uint32_t seed, uint32_t job_id, double *result, double *abs_err, int *split_dim)
+                    uint32_t seed, uint32_t job_id, uint32_t sub_id, double *result, double *abs_err,
+                    int *split_dim)
 {
     uint32_t *words = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)dims);
     double *x = (double *)malloc(sizeof(double) * (size_t)dims);
@@ -378,7 +379,7 @@ void oracle_nsphere(int dims, const double *lo, const double *hi, uint64_t n,
     for (int j = 0; j < dims; ++j) vol *= hi[j] - lo[j];
     nsum sf = {0, 0}, sf2 = {0, 0};
     for (uint64_t i = 0; i < n; ++i) {
-        oracle_sample_words(seed, job_id, 0u, i, dims, words);
+        oracle_sample_words(seed, job_id, sub_id, i, dims, words);
         oracle_words_to_point(dims, words, lo, hi, 0, x);
         double r2 = 0.0;
         for (int j = 0; j < dims; ++j) r2 += x[j] * x[j];

@@ -75,6 +75,26 @@ class Job(ctypes.Structure):
                 ("totals", ctypes.c_void_p)]
 
 
+class Convergence(ctypes.Structure):
+    """The convergence test of Sec. 3 (see bfi_convergence in bfi.h)."""
+
+    _fields_ = [("factor", ctypes.c_double), ("rel_tol", ctypes.c_double), ("abs_tol", ctypes.c_double),
+                ("small", ctypes.c_double), ("max_depth", ctypes.c_int32), ("max_leaves", ctypes.c_int64)]
+
+
+class AdaptiveStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("evaluated", ctypes.c_int64), ("converged", ctypes.c_int64),
+                ("kept_depth", ctypes.c_int64), ("kept_budget", ctypes.c_int64), ("leaves", ctypes.c_int64),
+                ("samples", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def convergence(factor=2.0, rel_tol=0.0, abs_tol=0.0, small=0.0, max_depth=12, max_leaves=1 << 16) -> Convergence:
+    return Convergence(factor, rel_tol, abs_tol, small, max_depth, max_leaves)
+
+
 def lattice(nx, nt, nu=1.0, D=1.0, a=1.0, tau=1.0, nonlinear=1.0, mass2=0.0) -> Lattice:
     return Lattice(nx, nt, nu, D, a, tau, nonlinear, mass2)
 
@@ -117,6 +137,12 @@ _SIGNATURES = {
     "bfi_nsphere": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, _P(ctypes.c_double), _P(ctypes.c_double),
                                    _P(ctypes.c_int32), ctypes.c_int]),
+    "bfi_adaptive_nsphere": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.c_uint32, _P(Convergence), _P(ctypes.c_double),
+                                            _P(ctypes.c_double), _P(AdaptiveStats), ctypes.c_int]),
+    "bfi_adaptive_integrate": (ctypes.c_int, [_vp, _P(Lattice), _vp, _vp, ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_int, _P(Convergence), _vp,
+                                              _P(AdaptiveStats), ctypes.c_int64, _vp, _vp, _vp]),
     "bfi_ctx_create": (ctypes.c_int, [_P(_vp), ctypes.c_int]),
     "bfi_ctx_destroy": (ctypes.c_int, [_vp]),
     "bfi_integrate": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, _vp,
@@ -279,6 +305,30 @@ class Context:
                                   None if slots is None else ctypes.c_void_p(slots.ctypes.data),
                                   ctypes.c_void_p(totals.ctypes.data)))
         return slots, totals
+
+    def adaptive_integrate(self, lat: Lattice, lo, hi, n: int, seed: int, conv: Convergence, job_id: int = 0,
+                           precision: int = FP64, leaf_capacity: int = 0):
+        """Adaptive subdivision of the box [lo, hi] (Sec. 3): (totals, stats)
+        or, with leaf_capacity > 0, (totals, stats, leaf_lo, leaf_hi,
+        leaf_slots) holding the first min(leaves, leaf_capacity) kept leaves."""
+        d = lat.nx * lat.nt
+        lo_a, lo_p = _host(np.broadcast_to(np.asarray(lo, dtype=np.float64), (d,)), np.float64)
+        hi_a, hi_p = _host(np.broadcast_to(np.asarray(hi, dtype=np.float64), (d,)), np.float64)
+        totals = np.empty(totals_len(lat.nx))
+        stats = AdaptiveStats()
+        cap = int(leaf_capacity)
+        llo = np.empty((cap, d)) if cap else None
+        lhi = np.empty((cap, d)) if cap else None
+        lsl = np.empty((cap, slot_len(lat.nx))) if cap else None
+        ptr = (lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data))
+        _check(_lib.bfi_adaptive_integrate(self._h, ctypes.byref(lat), lo_p, hi_p, int(n), seed & 0xFFFFFFFF,
+                                           job_id & 0xFFFFFFFF, precision, ctypes.byref(conv),
+                                           ctypes.c_void_p(totals.ctypes.data), ctypes.byref(stats), cap,
+                                           ptr(llo), ptr(lhi), ptr(lsl)))
+        if not cap:
+            return totals, stats
+        m = min(cap, stats.leaves)
+        return totals, stats, llo[:m], lhi[:m], lsl[:m]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -486,6 +536,17 @@ def nsphere(dims: int, n: int, seed: int, job_id: int = 0, lo=-1.0, hi=1.0, sub_
     _check(_lib.bfi_nsphere(dims, lo_p, hi_p, int(n), seed, job_id, sub_id, ctypes.byref(res), ctypes.byref(err),
                             ctypes.byref(sd), device))
     return res.value, err.value, sd.value
+
+
+def adaptive_nsphere(dims: int, n: int, seed: int, conv: Convergence, job_id: int = 0, lo=-1.0, hi=1.0,
+                     device: int = 0):
+    """(result, abs_err, stats) of the N-sphere integrand with adaptive subdivision (Sec. 3)."""
+    lo_a, lo_p = _host(np.broadcast_to(np.asarray(lo, dtype=np.float64), (dims,)), np.float64)
+    hi_a, hi_p = _host(np.broadcast_to(np.asarray(hi, dtype=np.float64), (dims,)), np.float64)
+    res, err, stats = ctypes.c_double(), ctypes.c_double(), AdaptiveStats()
+    _check(_lib.bfi_adaptive_nsphere(dims, lo_p, hi_p, int(n), seed, job_id, ctypes.byref(conv), ctypes.byref(res),
+                                     ctypes.byref(err), ctypes.byref(stats), device))
+    return res.value, err.value, stats
 
 
 def merge_host(nx: int, slots) -> np.ndarray:

@@ -21,6 +21,12 @@
 //
 // Line k (0-based) draws its points with Philox key (seed, k), so every line
 // is an independent estimate and a rerun repeats it exactly.
+//
+// --adaptive is the paper's wrapper (Listing 1) instead: no standard input;
+// the volume [min-extent, max-extent]^dimensions is subdivided until every
+// subvolume passes the convergence test of Sec. 3 (--samples n, --factor,
+// --rel-tol, --abs-tol, --small, --max-depth, --max-leaves) and one line
+// "result abs_error" is written.
 #include "bfi.h"
 
 #include <cmath>
@@ -37,8 +43,11 @@ void usage(const char *prog) {
                  "usage: %s [--integrand nsphere|burgers] [--seed S] [--device K]\n"
                  "          [--lattice NXxNT] [--nu X] [--D X] [--a X] [--tau X] [--nonlinear X] [--mass2 X]\n"
                  "          [--precision fp64|fp32] [--output z|logz|c<r>]\n"
+                 "          [--adaptive 1 --dimensions K --min-extent A --max-extent B --samples N\n"
+                 "           --factor F --rel-tol X --abs-tol X --small X --max-depth K --max-leaves K]\n"
                  "reads lines 'n lo_1 hi_1 ... lo_d hi_d' from standard input and writes\n"
-                 "'result abs_error split_dim' for each\n",
+                 "'result abs_error split_dim' for each; with --adaptive 1, integrates\n"
+                 "[A, B]^K adaptively and writes 'result abs_error'\n",
                  prog);
 }
 
@@ -49,6 +58,10 @@ struct Options {
     bfi_lattice lat{10, 2, 1.0, 1.0, 1.0, 1.0, 1.0, 0.0};
     bfi_precision precision = BFI_FP64;
     std::string output = "z";
+    bool adaptive = false;
+    int dims = 0;
+    double min_extent = -1.0, max_extent = 1.0, samples = 1e5;
+    bfi_convergence conv{2.0, 1e-2, 0.0, 0.0, 12, 1 << 16};
 };
 
 bool parse_double(const char *s, double *out) {
@@ -104,6 +117,28 @@ int parse_options(int argc, char **argv, Options *o) {
             o->precision = std::strcmp(v, "fp64") ? BFI_FP32 : BFI_FP64;
         } else if (k == "--output") {
             o->output = v;
+        } else if (k == "--adaptive" && parse_double(v, &x)) {
+            o->adaptive = x != 0.0;
+        } else if (k == "--dimensions" && parse_double(v, &x) && x >= 1 && x <= 32) {
+            o->dims = static_cast<int>(x);
+        } else if (k == "--min-extent" && parse_double(v, &x)) {
+            o->min_extent = x;
+        } else if (k == "--max-extent" && parse_double(v, &x)) {
+            o->max_extent = x;
+        } else if (k == "--samples" && parse_double(v, &x)) {
+            o->samples = x;
+        } else if (k == "--factor" && parse_double(v, &x)) {
+            o->conv.factor = x;
+        } else if (k == "--rel-tol" && parse_double(v, &x)) {
+            o->conv.rel_tol = x;
+        } else if (k == "--abs-tol" && parse_double(v, &x)) {
+            o->conv.abs_tol = x;
+        } else if (k == "--small" && parse_double(v, &x)) {
+            o->conv.small = x;
+        } else if (k == "--max-depth" && parse_double(v, &x) && x >= 0 && x <= 30) {
+            o->conv.max_depth = static_cast<int32_t>(x);
+        } else if (k == "--max-leaves" && parse_double(v, &x) && x >= 1) {
+            o->conv.max_leaves = static_cast<int64_t>(x);
         } else {
             std::fprintf(stderr, "bad option or value: %s %s\n", k.c_str(), v);
             usage(argv[0]);
@@ -147,11 +182,54 @@ int fail(const char *what) {
     return 3;
 }
 
+// The wrapper of Listing 1: adaptive subdivision of one cube.
+int run_adaptive(const Options &o) {
+    const bool burgers = o.integrand == "burgers";
+    const int d = burgers ? o.lat.nx * o.lat.nt : o.dims;
+    if (d < 1 || !(o.max_extent > o.min_extent) || !(o.samples >= 2.0) || o.samples != std::floor(o.samples) ||
+        o.samples >= 281474976710656.0) {
+        std::fprintf(stderr, "--adaptive needs --dimensions (nsphere), min-extent < max-extent and an integer "
+                             "--samples >= 2\n");
+        return 2;
+    }
+    const uint64_t n = static_cast<uint64_t>(o.samples);
+    std::vector<double> lo(d, o.min_extent), hi(d, o.max_extent);
+    double result = 0.0, err = 0.0;
+    if (!burgers) {
+        const bfi_status st = bfi_adaptive_nsphere(d, lo.data(), hi.data(), n, o.seed, 0u, &o.conv, &result, &err,
+                                                   nullptr, o.device);
+        if (st != BFI_OK) return st == BFI_E_INVALID ? (fail("bfi_adaptive_nsphere"), 2) : fail("bfi_adaptive_nsphere");
+    } else {
+        bfi_ctx *ctx = nullptr;
+        if (bfi_ctx_create(&ctx, o.device) != BFI_OK) return fail("bfi_ctx_create");
+        std::vector<double> totals(bfi_totals_len(o.lat.nx));
+        const bfi_status st = bfi_adaptive_integrate(ctx, &o.lat, lo.data(), hi.data(), n, o.seed, 0u, o.precision,
+                                                     &o.conv, totals.data(), nullptr, 0, nullptr, nullptr, nullptr);
+        bfi_ctx_destroy(ctx);
+        if (st != BFI_OK) return st == BFI_E_INVALID ? (fail("bfi_adaptive_integrate"), 2) : fail("bfi_adaptive_integrate");
+        const int R = bfi_num_r(o.lat.nx);
+        if (o.output == "z") {
+            result = std::exp(totals[0]);
+            err = result * totals[1];
+        } else if (o.output == "logz") {
+            result = totals[0];
+            err = totals[1];
+        } else {
+            const int r = std::atoi(o.output.c_str() + 1);
+            result = totals[4 + r];
+            err = totals[4 + R + r];
+        }
+    }
+    std::printf("%.15g %.15g\n", result, err);
+    return 0;
+}
+
 }  // namespace
 
 int main(int argc, char **argv) {
     Options o;
     if (const int rc = parse_options(argc, argv, &o)) return rc;
+    if (o.adaptive) return run_adaptive(o);
     const bool burgers = o.integrand == "burgers";
     const int d = o.lat.nx * o.lat.nt;
     bfi_ctx *ctx = nullptr;

@@ -17,4 +17,13 @@ int64_t plan_chunk_samples(uint64_t total);
 // Negligible-weight window for the largest per-subvolume budget n_max.
 float plan_negligible_window(bfi_precision precision, uint64_t n_max);
 
+// N-sphere integrand (nsphere.cu): nbox boxes (host arrays [nbox][dims],
+// n and sub_id [nbox]) in one launch on 'device'; sums [nbox][2 + dims] are
+// [sum f, sum f^2, sum_{x_j < mid_j} f for each j], written to host memory.
+bfi_status nsphere_batch(int dims, int64_t nbox, const double *lo, const double *hi, const uint64_t *n,
+                         const uint32_t *sub_id, uint32_t seed, uint32_t job_id, int device, double *sums);
+// Result, error and split suggestion of one box from its sums.
+void nsphere_finish(int dims, const double *lo, const double *hi, uint64_t n, const double *sums, double *result,
+                    double *abs_err, int32_t *split_dim);
+
 }  // namespace bfi

@@ -121,7 +121,43 @@ def test_cli_burgers_matches_oracle(bfi, output):
         assert int(out[k][2]) == int(np.argmax(h - l))
 
 
+@pytest.mark.gpu
+def test_listing1_through_the_wrapper_mode(bfi):
+    # Sec. 3, Listing 1: the wrapper integrates (half) the unit 4-ball's volume
+    # with the 3-dimensional integrand over [-1,1] and prints "result abs_error"
+    args = ["--adaptive", "1", "--integrand", "nsphere", "--dimensions", "3", "--min-extent", "-1",
+            "--max-extent", "1", "--samples", "1e5", "--rel-tol", "0.003", "--max-depth", "8"]
+    r = _run_cli(bfi, args, "")
+    assert r.returncode == 0, r.stderr
+    res, err = map(float, r.stdout.split())
+    assert err < 0.01 and abs(res - math.pi ** 2 / 4) < 4 * err
+    b = bfi.adaptive_nsphere(3, 100_000, 1, bfi.convergence(2.0, 0.003, 0.0, 0.0, 8, 1 << 16))
+    assert (res, err) == (float(f"{b[0]:.15g}"), float(f"{b[1]:.15g}"))
+
+
+@pytest.mark.gpu
+def test_wrapper_mode_lattice(bfi):
+    args = ["--adaptive", "1", "--integrand", "burgers", "--lattice", "4x2", "--min-extent", "-5",
+            "--max-extent", "5", "--samples", "20000", "--rel-tol", "0.05", "--max-depth", "4", "--output", "logz",
+            "--seed", "3"]
+    r = _run_cli(bfi, args, "")
+    assert r.returncode == 0, r.stderr
+    logz, rel = map(float, r.stdout.split())
+    ctx = bfi.Context(0)
+    try:
+        t, _ = ctx.adaptive_integrate(bfi.lattice(4, 2), -5.0, 5.0, 20_000, 3,
+                                      bfi.convergence(2.0, 0.05, 0.0, 0.0, 4, 1 << 16))
+    finally:
+        ctx.close()
+    assert (logz, rel) == (float(f"{t[0]:.15g}"), float(f"{t[1]:.15g}"))
+
+
 @pytest.mark.parametrize("args,stdin", [
+    (["--adaptive", "1"], ""),
+    (["--adaptive", "1", "--dimensions", "3", "--factor", "0.5"], ""),
+    (["--adaptive", "1", "--dimensions", "3", "--samples", "1"], ""),
+    (["--adaptive", "1", "--dimensions", "3", "--min-extent", "1", "--max-extent", "1"], ""),
+    (["--adaptive", "1", "--dimensions", "40"], ""),
     ([], "abc\n"),
     ([], "1e7 -1\n"),
     ([], "1.5 -1 1\n"),
