@@ -393,7 +393,8 @@ bfi_status bfi_nsphere(int32_t dims, const double *lo, const double *hi, uint64_
 /* Sec. 3: the volume is subdivided until each subvolume has converged.  A
  * subvolume is evaluated twice, with n samples and with factor * n, and has
  * converged when at least one of these holds for the two results r1, r2:
- *   (1) |r1 - r2| <= rel_tol * max(|r1|, |r2|)
+ *   (1) |r1 - r2| <= rel_tol * min(|r1|, |r2|)   (within a factor 1 + rel_tol;
+ *       Sec. 4 quotes this threshold as the ratio 1.025 .. 1.085)
  *   (2) |r1 - r2| <= abs_tol
  *   (3) max(|r1|, |r2|) <= small
  * (a criterion whose threshold is <= 0 is off).  A converged subvolume keeps

@@ -7,6 +7,9 @@ subvolume is evaluated twice, the second time with a user factor more samples,
 and has converged when one or more of three criteria holds for the two results:
 (1) their absolute relative difference is below a factor, (2) their absolute
 difference is below a value, (3) the larger absolute result is below a value.
+Sec. 4 quotes the factor of (1) as a ratio (1.025 to 1.085), so (1) reads
+|r1 - r2| <= rel_tol * min(|r1|, |r2|): the results lie within a factor
+1 + rel_tol of each other.
 A subvolume that has not converged is halved along the dimension its
 integrand suggests.
 
@@ -55,9 +58,10 @@ def _criteria_linear(r1, r2, c):
     """Values and thresholds of criteria (1)-(3) for two plain results."""
     diff = abs(r1 - r2)
     big = max(abs(r1), abs(r2))
+    little = min(abs(r1), abs(r2))
     out = []
     if c.rel_tol > 0:
-        out.append((diff, c.rel_tol * big))
+        out.append((diff, c.rel_tol * little))
     if c.abs_tol > 0:
         out.append((diff, c.abs_tol))
     if c.small > 0:
@@ -67,14 +71,15 @@ def _criteria_linear(r1, r2, c):
 
 def _criteria_log(l1, l2, c):
     """The same criteria for positive results given as logarithms:
-    |Z1 - Z2| / max(Z1, Z2) = 1 - exp(-|ln Z1 - ln Z2|)."""
+    |Z1 - Z2| / min(Z1, Z2) = exp(|ln Z1 - ln Z2|) - 1, and |Z1 - Z2| is
+    min(Z1, Z2) times that."""
     top = max(l1, l2)
-    rel = -math.expm1(-abs(l1 - l2))
+    rel = math.expm1(abs(l1 - l2))
     out = []
     if c.rel_tol > 0:
         out.append((rel, c.rel_tol))
     if c.abs_tol > 0:
-        out.append((math.exp(top) * rel, c.abs_tol))
+        out.append((math.exp(min(l1, l2)) * rel, c.abs_tol))
     if c.small > 0:
         out.append((top, math.log(c.small)))
     return out

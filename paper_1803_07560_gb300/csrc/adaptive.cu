@@ -54,18 +54,21 @@ bfi_status check_convergence(const bfi_convergence *c, uint64_t n, uint64_t *n2)
     return BFI_OK;
 }
 
-// The three criteria of Sec. 3 on two results.
+// The three criteria of Sec. 3 on two results; (1) is the ratio test of
+// Sec. 4 (results within a factor 1 + rel_tol of each other).
 bool converged_linear(double r1, double r2, const bfi_convergence &c) {
-    const double diff = std::fabs(r1 - r2), big = std::fmax(std::fabs(r1), std::fabs(r2));
-    return (c.rel_tol > 0.0 && diff <= c.rel_tol * big) || (c.abs_tol > 0.0 && diff <= c.abs_tol) ||
+    const double diff = std::fabs(r1 - r2), big = std::fmax(std::fabs(r1), std::fabs(r2)),
+                 little = std::fmin(std::fabs(r1), std::fabs(r2));
+    return (c.rel_tol > 0.0 && diff <= c.rel_tol * little) || (c.abs_tol > 0.0 && diff <= c.abs_tol) ||
            (c.small > 0.0 && big <= c.small);
 }
 
 // The same criteria for positive results given by their logarithms:
-// |Z1 - Z2| / max = 1 - exp(-|ln Z1 - ln Z2|).
+// |Z1 - Z2| / min(Z1, Z2) = exp(|ln Z1 - ln Z2|) - 1.
 bool converged_log(double l1, double l2, const bfi_convergence &c) {
-    const double top = std::fmax(l1, l2), rel = -std::expm1(-std::fabs(l1 - l2));
-    return (c.rel_tol > 0.0 && rel <= c.rel_tol) || (c.abs_tol > 0.0 && std::exp(top) * rel <= c.abs_tol) ||
+    const double top = std::fmax(l1, l2), rel = std::expm1(std::fabs(l1 - l2));
+    const double low = std::fmin(l1, l2);
+    return (c.rel_tol > 0.0 && rel <= c.rel_tol) || (c.abs_tol > 0.0 && std::exp(low) * rel <= c.abs_tol) ||
            (c.small > 0.0 && top <= std::log(c.small));
 }
 

@@ -119,3 +119,21 @@ def test_adaptive_lattice_agrees_with_quadrature():
     for r in range(R):
         assert abs(totals[4 + r] - Nq[r] / Zq) < 4 * totals[4 + R + r] + 1e-9
     _tiles(out, [-5] * 3, [5] * 3)
+
+
+def test_relative_criterion_is_a_ratio():
+    # Sec. 4 quotes criterion (1) as ratios (1.025 to 1.085): results 1.00 and
+    # 1.03 lie within a factor 1.0305 of each other but not within 1.0295, in
+    # plain values and in logarithms alike
+    from oracle.adaptive import _criteria_linear, _criteria_log
+    for tol, ok in [(0.0305, True), (0.0295, False)]:
+        c = Convergence(2.0, tol, 0.0, 0.0, 1, 1)
+        [(v, t)] = _criteria_linear(1.0, 1.03, c)
+        assert (v <= t) == ok
+        [(v, t)] = _criteria_linear(-1.03, -1.0, c)
+        assert (v <= t) == ok
+        [(v, t)] = _criteria_log(math.log(7.0), math.log(7.0 * 1.03), c)
+        assert (v <= t) == ok
+    # opposite signs are never within a ratio
+    [(v, t)] = _criteria_linear(1.0, -1.0, Convergence(2.0, 0.5, 0.0, 0.0, 1, 1))
+    assert v > t
