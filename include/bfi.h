@@ -191,6 +191,56 @@ bfi_status bfi_plan_set_grid(bfi_plan *plan, int32_t ctas_per_sm);
  * bfi_plan_get_timing waits for the last execution's events and writes
  * ms[0] = integrand kernel, ms[1] = merges (milliseconds).  Off by default.
  * Errors: BFI_E_INVALID (NULL, or no timed execution yet), BFI_E_CUDA. */
+/* Samplers: how the unit point u (from Philox, see Conventions) becomes the
+ * field v.  The box sampler (the default) takes v uniform in each box.  The
+ * other two run in FP64 only (the FP32 screen's error bound does not hold
+ * once a map stretches the coordinates, so every sample is evaluated in
+ * FP64), on the warp-per-sample kernel:
+ *
+ *   BFI_SAMPLE_TRANSFORM  the infinite range mapped onto (-1, 1) (Sec. 4; the
+ *       paper does not state its transform, this one is ours):
+ *       v_j = y_j / (1 - y_j^2) with y uniform in the box, which must lie in
+ *       [-1, 1]^d (outside it the numbers are undefined, never an
+ *       out-of-range access); the Jacobian prod (1 + y^2)/(1 - y^2)^2 is in
+ *       the weight, so a box of [-1, 1]^d integrates over all of R^d.
+ *   BFI_SAMPLE_GAUSSIAN   importance sampling (the better-concentrated
+ *       integrand Sec. 5 calls for): z_j = Phi^-1(u_j), v = mean + F z, so
+ *       v ~ N(mean, F F^T) with density q; the weight is exp(-S(v)) / q(v)
+ *       for v in the box [lo, hi) and 0 outside, so each box's Z_s is still
+ *       the integral over that box.  d <= 64.  The record's log V_s holds
+ *       (d/2) ln(2 pi) + ln |det F| instead of the box volume.
+ *
+ * Z_s, C(r) and the errors keep their meaning (estimates over the boxes);
+ * with GAUSSIAN, a box that no sample hits gives Z_s = 0 (m_s = +inf).
+ * mean (NULL = 0) and factor are host arrays, copied by the call. */
+typedef enum {
+    BFI_SAMPLE_BOX = 0,
+    BFI_SAMPLE_TRANSFORM = 1,
+    BFI_SAMPLE_GAUSSIAN = 2
+} bfi_sample_kind;
+
+typedef struct {
+    int32_t kind;          /* bfi_sample_kind */
+    const double *mean;    /* GAUSSIAN: host [d] or NULL */
+    const double *factor;  /* GAUSSIAN: host [d * d], row-major, non-singular */
+} bfi_sampler;
+
+/* Sets the plan's sampler for its next executions (re-sizes the grid for
+ * the sampler's kernel).  Errors: BFI_E_INVALID (unknown kind, missing,
+ * non-finite or singular factor), BFI_E_UNSUPPORTED (FP32 plan, d > 64 for
+ * GAUSSIAN), BFI_E_NOMEM, BFI_E_CUDA. */
+bfi_status bfi_plan_set_sampler(bfi_plan *plan, const bfi_sampler *sampler);
+
+/* A proposal for the Gaussian sampler: the factor F (host [d * d],
+ * row-major, upper triangular) with F F^T = (A + I / sigma0^2)^-1, where
+ * v^T A v / 2 is the action of Eq. (Gen2) without the advection term (the
+ * linear limit, mass2 included).  The linear limit has zero modes (the
+ * constant field among them) unless mass2 > 0; zero_mode_sigma = sigma0 > 0
+ * gives them a finite spread (INFINITY: no regulator).
+ * Errors: BFI_E_INVALID (a zero mode left unregulated), BFI_E_UNSUPPORTED
+ * (d > 64). */
+bfi_status bfi_gaussian_proposal(const bfi_lattice *lattice, double zero_mode_sigma, double *factor);
+
 bfi_status bfi_plan_set_timing(bfi_plan *plan, int enable);
 /* Samples fully evaluated (point, action, products, weight) by the last
  * execution, and the plan's negligible-weight window (see "Negligible
@@ -353,6 +403,12 @@ typedef struct bfi_ctx bfi_ctx;
 
 bfi_status bfi_ctx_create(bfi_ctx **out, int device);
 bfi_status bfi_ctx_destroy(bfi_ctx *ctx);
+
+/* The sampler of the context's next integrations (see bfi_plan_set_sampler);
+ * d is the dimension the Gaussian factor is for (ignored otherwise).
+ * Errors: BFI_E_INVALID, BFI_E_BUSY; the plan-level checks surface from
+ * bfi_integrate. */
+bfi_status bfi_ctx_set_sampler(bfi_ctx *ctx, const bfi_sampler *sampler, int32_t d);
 
 /* Integrate one job with host inputs and outputs: copies the bounds in, runs
  * the plan (re-planned only when the lattice, precision or budgets change),

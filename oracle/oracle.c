@@ -295,7 +295,7 @@ void oracle_merge(int nx, int64_t nsub, const double *slots, double *totals)
         double f = exp(q[2] - log(q[0]) - q[1] - L);
         varZ += f * f * (n * q[4] - q[3] * q[3]) / (n - 1.0);
     }
-    totals[1] = sqrt(varZ) / Z;
+    totals[1] = sqrt(varZ > 0.0 ? varZ : 0.0) / Z;
     for (int r = 0; r < R; ++r) {
         double C = N[r] / Z;
         double var = 0.0;

@@ -75,6 +75,34 @@ class Job(ctypes.Structure):
                 ("totals", ctypes.c_void_p)]
 
 
+SAMPLE_BOX, SAMPLE_TRANSFORM, SAMPLE_GAUSSIAN = 0, 1, 2
+
+
+class Sampler(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("mean", ctypes.c_void_p), ("factor", ctypes.c_void_p)]
+
+
+def _sampler(kind: int, d: int, mean=None, factor=None):
+    """A bfi_sampler and the host arrays it points to (kept alive by the caller)."""
+    keep = []
+    mp = fp = None
+    if kind == SAMPLE_GAUSSIAN:
+        f, fp = _host(np.reshape(factor, (d, d)), np.float64)
+        keep.append(f)
+        if mean is not None:
+            m, mp = _host(np.reshape(mean, (d,)), np.float64)
+            keep.append(m)
+    return Sampler(kind, mp, fp), keep
+
+
+def gaussian_proposal(lat: Lattice, zero_mode_sigma: float = float("inf")) -> np.ndarray:
+    """Factor F with F F^T = (A + I/sigma0^2)^-1 for the linear-limit action (see bfi.h)."""
+    d = lat.nx * lat.nt
+    out = np.empty((d, d))
+    _check(_lib.bfi_gaussian_proposal(ctypes.byref(lat), float(zero_mode_sigma), ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
 class Convergence(ctypes.Structure):
     """The convergence test of Sec. 3 (see bfi_convergence in bfi.h)."""
 
@@ -143,6 +171,9 @@ _SIGNATURES = {
     "bfi_adaptive_integrate": (ctypes.c_int, [_vp, _P(Lattice), _vp, _vp, ctypes.c_uint64, ctypes.c_uint32,
                                               ctypes.c_uint32, ctypes.c_int, _P(Convergence), _vp,
                                               _P(AdaptiveStats), ctypes.c_int64, _vp, _vp, _vp]),
+    "bfi_plan_set_sampler": (ctypes.c_int, [_vp, _P(Sampler)]),
+    "bfi_gaussian_proposal": (ctypes.c_int, [_P(Lattice), ctypes.c_double, _vp]),
+    "bfi_ctx_set_sampler": (ctypes.c_int, [_vp, _P(Sampler), ctypes.c_int32]),
     "bfi_ctx_create": (ctypes.c_int, [_P(_vp), ctypes.c_int]),
     "bfi_ctx_destroy": (ctypes.c_int, [_vp]),
     "bfi_integrate": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, _vp,
@@ -222,6 +253,7 @@ class Plan:
         self.precision = precision
         self.device = device
         self.nsub = int(smp.size)
+        self.d = lat.nx * lat.nt
         handle = ctypes.c_void_p()
         _check(_lib.bfi_plan_create(ctypes.byref(handle), ctypes.byref(lat), smp.size,
                                     smp.ctypes.data_as(_P(ctypes.c_uint64)), precision, device))
@@ -247,6 +279,10 @@ class Plan:
                                      _dev_ptr(slots, torch.float64), _dev_ptr(totals, torch.float64),
                                      _stream_ptr(stream)))
         return slots, totals
+
+    def set_sampler(self, kind: int, mean=None, factor=None):
+        smp, keep = _sampler(kind, self.d, mean, factor)
+        _check(_lib.bfi_plan_set_sampler(self._h, ctypes.byref(smp)))
 
     def set_grid(self, ctas_per_sm: int):
         """Persistent grid: CTAs per SM (0 = occupancy limit); never changes results."""
@@ -305,6 +341,13 @@ class Context:
                                   None if slots is None else ctypes.c_void_p(slots.ctypes.data),
                                   ctypes.c_void_p(totals.ctypes.data)))
         return slots, totals
+
+    def set_sampler(self, kind: int, d: int = 0, mean=None, factor=None):
+        """Sampler of the next integrations (d: the dimension of a Gaussian factor)."""
+        if kind == SAMPLE_GAUSSIAN and not d:
+            d = int(round(np.sqrt(np.size(factor))))
+        smp, keep = _sampler(kind, d, mean, factor)
+        _check(_lib.bfi_ctx_set_sampler(self._h, ctypes.byref(smp), d))
 
     def adaptive_integrate(self, lat: Lattice, lo, hi, n: int, seed: int, conv: Convergence, job_id: int = 0,
                            precision: int = FP64, leaf_capacity: int = 0):

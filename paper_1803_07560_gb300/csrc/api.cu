@@ -6,6 +6,7 @@
 #include "bfi_host.h"
 #include "bfi_kernels.h"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -120,6 +121,9 @@ struct bfi_plan {
     size_t scratch_bytes = 0;
     bool timing = false, timed = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    int32_t sampler = BFI_SAMPLE_BOX;
+    double *d_map = nullptr;  // Gaussian sampler: mean [d], then factor [d * d]
+    double log_norm = 0.0;    // Gaussian sampler: (d/2) ln 2 pi + ln |det F|
 };
 
 extern "C" {
@@ -139,6 +143,7 @@ bfi_status bfi_plan_destroy(bfi_plan *plan) {
         cudaFree(plan->d_hint);
         cudaFree(plan->d_stats);
         cudaFree(plan->d_fbuf);
+        cudaFree(plan->d_map);
         for (auto &e : plan->ev)
             if (e) cudaEventDestroy(e);
     }
@@ -258,10 +263,16 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
         bfi::IntegrandArgs a{lo,           hi,           sub_id,        plan->d_samples,     plan->d_chunk_off,
                              plan->d_partials, plan->d_hint, plan->d_stats, plan->nsub, plan->nchunks,
                              plan->chunk_samples, plan->skip_window};
-        BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
+        if (plan->sampler == BFI_SAMPLE_BOX) {
+            BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
+        } else {
+            const bfi::MapArgs mp{plan->sampler, plan->d_map, plan->d_map ? plan->d_map + plan->d : nullptr};
+            BFI_CUDA(bfi::launch_mapped(a, plan->lat, mp, seed, job_id, plan->grid, st));
+        }
     }
     if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[1], st));
-    bfi::MergeArgs m{lo, hi, plan->d_chunk_off, plan->d_partials, slots, plan->nsub, plan->R, plan->d};
+    bfi::MergeArgs m{lo, hi, plan->d_chunk_off, plan->d_partials, slots, plan->nsub, plan->R, plan->d,
+                     plan->sampler == BFI_SAMPLE_GAUSSIAN ? 1 : 0, plan->log_norm};
     bfi::TotalsArgs t{slots, totals, plan->d_fbuf, plan->nsub, plan->R};
     BFI_CUDA(bfi::launch_merges(m, t, st));
     if (plan->timing) {
@@ -279,6 +290,124 @@ bfi_status bfi_plan_set_grid(bfi_plan *plan, int32_t ctas_per_sm) {
     plan->per_sm = per_sm;
     const int64_t resident = static_cast<int64_t>(plan->sms) * per_sm;
     plan->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(plan->nchunks, resident)));
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_set_sampler(bfi_plan *plan, const bfi_sampler *sampler) {
+    if (!plan || !sampler) return fail(BFI_E_INVALID, "plan or sampler is NULL");
+    const int kind = sampler->kind;
+    if (kind != BFI_SAMPLE_BOX && kind != BFI_SAMPLE_TRANSFORM && kind != BFI_SAMPLE_GAUSSIAN)
+        return fail(BFI_E_INVALID, "unknown sampler kind %d", kind);
+    if (kind != BFI_SAMPLE_BOX && plan->precision != BFI_FP64)
+        return fail(BFI_E_UNSUPPORTED, "the transform and Gaussian samplers run in FP64 only");
+    const int d = plan->d;
+    double log_norm = 0.0;
+    if (kind == BFI_SAMPLE_GAUSSIAN) {
+        if (d > bfi::kMaxGaussD)
+            return fail(BFI_E_UNSUPPORTED, "the Gaussian sampler supports d <= %d (d = %d)", bfi::kMaxGaussD, d);
+        if (!sampler->factor) return fail(BFI_E_INVALID, "the Gaussian sampler needs a factor");
+        for (int k = 0; k < d * d; ++k)
+            if (!std::isfinite(sampler->factor[k])) return fail(BFI_E_INVALID, "the factor has a non-finite entry");
+        if (sampler->mean)
+            for (int k = 0; k < d; ++k)
+                if (!std::isfinite(sampler->mean[k])) return fail(BFI_E_INVALID, "the mean has a non-finite entry");
+        // ln |det F| by Gaussian elimination with partial pivoting
+        std::vector<double> a(sampler->factor, sampler->factor + d * d);
+        double log_det = 0.0;
+        for (int col = 0; col < d; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < d; ++r)
+                if (std::fabs(a[r * d + col]) > std::fabs(a[piv * d + col])) piv = r;
+            const double pv = a[piv * d + col];
+            if (pv == 0.0) return fail(BFI_E_INVALID, "the factor is singular");
+            if (piv != col)
+                for (int k = 0; k < d; ++k) std::swap(a[piv * d + k], a[col * d + k]);
+            log_det += std::log(std::fabs(pv));
+            for (int r = col + 1; r < d; ++r) {
+                const double f = a[r * d + col] / pv;
+                for (int k = col; k < d; ++k) a[r * d + k] -= f * a[col * d + k];
+            }
+        }
+        log_norm = 0.5 * d * std::log(2.0 * M_PI) + log_det;
+    }
+    DeviceGuard g(plan->device);
+    if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device: %s", cudaGetErrorString(g.err));
+    int per_sm = 0;
+    cudaError_t e = kind == BFI_SAMPLE_BOX
+                        ? plan->shape->occupancy[plan->precision](plan->lat.nx, plan->lat.nt, &per_sm)
+                        : bfi::occupancy_mapped(plan->lat.nx, plan->lat.nt, kind, &per_sm);
+    if (e != cudaSuccess) return fail(BFI_E_CUDA, "occupancy query failed: %s", cudaGetErrorString(e));
+    if (kind == BFI_SAMPLE_GAUSSIAN) {
+        if (!plan->d_map && cudaMalloc(&plan->d_map, sizeof(double) * (d + d * d)) != cudaSuccess) {
+            cudaGetLastError();
+            plan->d_map = nullptr;
+            return fail(BFI_E_NOMEM, "device allocation of the sampler failed");
+        }
+        std::vector<double> host(d + d * d, 0.0);
+        if (sampler->mean) std::copy(sampler->mean, sampler->mean + d, host.begin());
+        std::copy(sampler->factor, sampler->factor + d * d, host.begin() + d);
+        BFI_CUDA(cudaMemcpy(plan->d_map, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice));
+    }
+    plan->sampler = kind;
+    plan->log_norm = log_norm;
+    plan->per_sm_max = per_sm > 0 ? per_sm : 1;
+    plan->per_sm = plan->per_sm_max;
+    const int64_t resident = static_cast<int64_t>(plan->sms) * plan->per_sm_max;
+    plan->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(plan->nchunks, resident)));
+    return BFI_OK;
+}
+
+bfi_status bfi_gaussian_proposal(const bfi_lattice *lattice, double zero_mode_sigma, double *factor) {
+    bfi_status st = check_lattice(lattice);
+    if (st != BFI_OK) return st;
+    if (!factor) return fail(BFI_E_INVALID, "factor is NULL");
+    if (!(zero_mode_sigma > 0.0)) return fail(BFI_E_INVALID, "zero_mode_sigma must be > 0 (inf: no regulator)");
+    const int nx = lattice->nx, nt = lattice->nt, d = nx * nt;
+    if (d > bfi::kMaxGaussD) return fail(BFI_E_UNSUPPORTED, "the Gaussian sampler supports d <= %d", bfi::kMaxGaussD);
+    // B: the residual of Eq. (Gen2) without the advection term,
+    // (B v)_j = v_next(j) - v_j + c_dif (2 v_j - v_right(j) - v_left(j))
+    const double c_dif = lattice->nu * lattice->tau / (lattice->a * lattice->a);
+    std::vector<double> B(static_cast<size_t>(d) * d, 0.0), A(static_cast<size_t>(d) * d, 0.0);
+    for (int j = 0; j < d; ++j) {
+        const int l = j % nt;
+        const int nxt = l + 1 < nt ? j + 1 : j + 1 - nt;
+        const int right = (j + nt) % d, left = (j - nt + d) % d;
+        B[j * d + nxt] += 1.0;
+        B[j * d + j] += 2.0 * c_dif - 1.0;
+        B[j * d + right] -= c_dif;
+        B[j * d + left] -= c_dif;
+    }
+    // A = B^T B / (D tau) + (mass2 + 1/sigma0^2) I, the quadratic form of the
+    // linear-limit action S = v^T A v / 2 plus the regulator
+    const double diag = lattice->mass2 + (std::isinf(zero_mode_sigma) ? 0.0 : 1.0 / (zero_mode_sigma * zero_mode_sigma));
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c) {
+            double acc = 0.0;
+            for (int k = 0; k < d; ++k) acc += B[k * d + r] * B[k * d + c];
+            A[r * d + c] = acc / (lattice->D * lattice->tau) + (r == c ? diag : 0.0);
+        }
+    // Cholesky A = L L^T, then F = L^-T (upper triangular): F F^T = A^-1
+    std::vector<double> Lc(static_cast<size_t>(d) * d, 0.0);
+    for (int j = 0; j < d; ++j) {
+        double s2 = A[j * d + j];
+        for (int k = 0; k < j; ++k) s2 -= Lc[j * d + k] * Lc[j * d + k];
+        if (!(s2 > 0.0))
+            return fail(BFI_E_INVALID, "the linear-limit action has a zero mode: give a finite zero_mode_sigma");
+        const double ljj = std::sqrt(s2);
+        Lc[j * d + j] = ljj;
+        for (int i = j + 1; i < d; ++i) {
+            double t = A[i * d + j];
+            for (int k = 0; k < j; ++k) t -= Lc[i * d + k] * Lc[j * d + k];
+            Lc[i * d + j] = t / ljj;
+        }
+    }
+    // solve L^T F = I column by column (back substitution)
+    for (int c = 0; c < d; ++c)
+        for (int i = d - 1; i >= 0; --i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int k = i + 1; k < d; ++k) t -= Lc[k * d + i] * factor[k * d + c];
+            factor[i * d + c] = t / Lc[i * d + i];
+        }
     return BFI_OK;
 }
 
@@ -329,6 +458,8 @@ struct bfi_ctx {
     double *d_lo = nullptr, *d_hi = nullptr, *d_slots = nullptr, *d_totals = nullptr;
     uint32_t *d_sid = nullptr;
     size_t cap_lo = 0, cap_hi = 0, cap_sid = 0, cap_slots = 0, cap_totals = 0;
+    int32_t sampler = BFI_SAMPLE_BOX;         // applied to every plan the context makes
+    std::vector<double> map_mean, map_factor;
 };
 
 namespace {
@@ -399,6 +530,28 @@ bfi_status bfi_ctx_destroy(bfi_ctx *ctx) {
     return BFI_OK;
 }
 
+bfi_status bfi_ctx_set_sampler(bfi_ctx *ctx, const bfi_sampler *sampler, int32_t d) {
+    if (!ctx || !sampler) return fail(BFI_E_INVALID, "ctx or sampler is NULL");
+    BusyGuard busy(ctx->busy);
+    if (!busy.ok) return fail(BFI_E_BUSY, "context is in use by another thread");
+    const int kind = sampler->kind;
+    if (kind != BFI_SAMPLE_BOX && kind != BFI_SAMPLE_TRANSFORM && kind != BFI_SAMPLE_GAUSSIAN)
+        return fail(BFI_E_INVALID, "unknown sampler kind %d", kind);
+    ctx->map_mean.clear();
+    ctx->map_factor.clear();
+    if (kind == BFI_SAMPLE_GAUSSIAN) {
+        if (d < 1 || d > bfi::kMaxGaussD || !sampler->factor)
+            return fail(BFI_E_INVALID, "the Gaussian sampler needs 1 <= d <= %d and a factor", bfi::kMaxGaussD);
+        ctx->map_factor.assign(sampler->factor, sampler->factor + static_cast<size_t>(d) * d);
+        if (sampler->mean) ctx->map_mean.assign(sampler->mean, sampler->mean + d);
+    }
+    ctx->sampler = kind;
+    // the next integration re-plans with the sampler
+    bfi_plan_destroy(ctx->plan);
+    ctx->plan = nullptr;
+    return BFI_OK;
+}
+
 bfi_status bfi_integrate(bfi_ctx *ctx, const bfi_lattice *lattice, int64_t nsub, const double *lo, const double *hi,
                          const uint64_t *samples, const uint32_t *sub_id, uint32_t seed, uint32_t job_id,
                          bfi_precision precision, double *slots, double *totals) {
@@ -422,6 +575,22 @@ bfi_status bfi_integrate(bfi_ctx *ctx, const bfi_lattice *lattice, int64_t nsub,
         if (st != BFI_OK) return st;
         ctx->lat = *lattice;
         ctx->precision = precision;
+        if (ctx->sampler != BFI_SAMPLE_BOX) {
+            const bool gauss = ctx->sampler == BFI_SAMPLE_GAUSSIAN;
+            if (gauss && ctx->map_factor.size() != static_cast<size_t>(ctx->plan->d) * ctx->plan->d) {
+                bfi_plan_destroy(ctx->plan);
+                ctx->plan = nullptr;
+                return fail(BFI_E_INVALID, "the context's Gaussian sampler was set for another dimension");
+            }
+            const bfi_sampler smp{ctx->sampler, gauss && !ctx->map_mean.empty() ? ctx->map_mean.data() : nullptr,
+                                  gauss ? ctx->map_factor.data() : nullptr};
+            st = bfi_plan_set_sampler(ctx->plan, &smp);
+            if (st != BFI_OK) {
+                bfi_plan_destroy(ctx->plan);
+                ctx->plan = nullptr;
+                return st;
+            }
+        }
     }
     const int d = lattice->nx * lattice->nt;
     const size_t nbox = static_cast<size_t>(nsub) * d;
@@ -478,7 +647,7 @@ bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double 
         VZ += f[s] * f[s] * (n * q[4] - q[3] * q[3]) / (n - 1.0);
     }
     totals[0] = L + std::log(Z);
-    totals[1] = inf_err ? INFINITY : std::sqrt(VZ) / Z;
+    totals[1] = inf_err ? INFINITY : std::sqrt(VZ > 0.0 ? VZ : 0.0) / Z;
     totals[2] = n_tot;
     totals[3] = used;
     for (int r = 0; r < R; ++r) {

@@ -43,6 +43,8 @@ struct MergeArgs {
     double *slots;
     int64_t nsub;
     int32_t R, d;
+    int32_t log_norm_set;      // 1: every record's log-volume is log_norm (Gaussian sampler)
+    double log_norm;
 };
 
 struct TotalsArgs {
@@ -90,6 +92,18 @@ const ShapeKernels *shapes_config(int *n);
 const ShapeKernels *generic_shape(int nx, int nt);
 const ShapeKernels *find_shape(int nx, int nt);
 cudaError_t launch_merges(const MergeArgs &m, const TotalsArgs &t, cudaStream_t st);
+
+// Mapped samplers (generic.cu): kind 1 = the range map of Sec. 4, kind 2 =
+// Gaussian importance sampling with device mean [d] (or null) and factor [d*d].
+constexpr int kMaxGaussD = 64;
+struct MapArgs {
+    int kind;
+    const double *mean;
+    const double *factor;
+};
+cudaError_t launch_mapped(const IntegrandArgs &a, const LatticeParams &p, const MapArgs &m, uint32_t seed, uint32_t job,
+                          int grid, cudaStream_t st);
+cudaError_t occupancy_mapped(int nx, int nt, int kind, int *blocks_per_sm);
 cudaError_t launch_points(const PointsArgs &a, bool fp32, uint32_t seed, uint32_t job, cudaStream_t st);
 
 }  // namespace bfi

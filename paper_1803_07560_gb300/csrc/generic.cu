@@ -39,12 +39,13 @@ GenShape gen_shape(int nx, int nt) {
 
 // Dynamic shared memory layout of one CTA (byte offsets, 16-aligned).
 struct GenLayout {
-    int next, box_f, lo_d, w_d, uf, ud, sums, mw, total;
+    int next, box_f, lo_d, w_d, uf, ud, sums, mw, fac, mean, zb, total;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline GenLayout gen_layout(const GenShape &g) {
+// 'gauss' adds the Gaussian sampler's factor, mean and per-warp z vectors.
+__host__ __device__ inline GenLayout gen_layout(const GenShape &g, bool gauss = false) {
     GenLayout L;
     int o = 0;
     L.next = o;  o = align16(o + 2 * g.d);                    // uint16 next-time-slice index per site
@@ -55,6 +56,9 @@ __host__ __device__ inline GenLayout gen_layout(const GenShape &g) {
     L.ud = o;    o = align16(o + 8 * g.dpad * kGWarps);       // double point per warp
     L.sums = o;  o = align16(o + 8 * (g.K + g.R + 1) * kGWarps);  // per-warp sums (FP64, or FP32 sums + comps)
     L.mw = o;    o = align16(o + 8 * kGWarps + 8);             // per-warp shift, counter
+    L.fac = o;   if (gauss) o = align16(o + 8 * g.d * g.d);   // factor F, row-major
+    L.mean = o;  if (gauss) o = align16(o + 8 * g.d);         // mean
+    L.zb = o;    if (gauss) o = align16(o + 8 * g.dpad * kGWarps);  // z per warp
     L.total = o;
     return L;
 }
@@ -354,6 +358,134 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mapped samplers, FP64.  The unit point goes through a map to the field v
+// and the log-Jacobian joins the action, S_eff = S(v) - ln J:
+//   KIND 1 (the range map of Sec. 4): y uniform in the box (inside
+//          [-1,1]^d), v_j = y_j / (1 - y_j^2), ln J = sum_j ln(1 + y_j^2)
+//          - 2 ln(1 - y_j^2);
+//   KIND 2 (Gaussian importance sampling): z_j = Phi^-1(u_j), v = mean + F z,
+//          ln J = |z|^2 / 2 (the rest of 1/q goes into the record's
+//          log-volume on the host); samples outside the box [lo, hi) have
+//          weight 0.
+// Every sample is evaluated in FP64: a map stretches the coordinates, so the
+// FP32 screen's bound on |S_f32 - S| does not hold.  Each warp's shift starts
+// above every action (kNoShift) and drops to the first sample's S_eff.
+// ---------------------------------------------------------------------------
+constexpr double kNoShift = 1e300;
+
+template <int KIND>
+__global__ void __launch_bounds__(kGBlock) generic_mapped(const GenArgs ga, const MapArgs mp) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const IntegrandArgs &args = ga.a;
+    const GenShape &g = ga.g;
+    const GenLayout &L = ga.L;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint16_t *next = reinterpret_cast<const uint16_t *>(sm + L.next);
+    double *lo_s = reinterpret_cast<double *>(sm + L.lo_d);
+    double *b_s = reinterpret_cast<double *>(sm + L.w_d);  // KIND 1: width; KIND 2: upper bound
+    double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.dpad;
+    double *zb = reinterpret_cast<double *>(sm + L.zb) + warp * g.dpad;
+    double *fac = reinterpret_cast<double *>(sm + L.fac);
+    double *mean = reinterpret_cast<double *>(sm + L.mean);
+    double *mw = reinterpret_cast<double *>(sm + L.mw);
+    unsigned *cnt_all = reinterpret_cast<unsigned *>(mw + kGWarps);
+    double *sd = reinterpret_cast<double *>(sm + L.sums) + warp * (g.K + g.R + 1);
+    build_next(sm, L, g);
+    if (KIND == 2) {
+        for (int k = tid; k < g.d * g.d; k += kGBlock) fac[k] = mp.factor[k];
+        for (int k = tid; k < g.d; k += kGBlock) mean[k] = mp.mean ? mp.mean[k] : 0.0;
+    }
+
+    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+        const ChunkView v = chunk_view(args, c, g.d);
+        __syncthreads();  // the previous chunk's readers of box and sums are done
+        for (int j = tid; j < g.d; j += kGBlock) {
+            lo_s[j] = v.lo[j];
+            b_s[j] = KIND == 1 ? v.hi[j] - v.lo[j] : v.hi[j];
+        }
+        for (int k = lane; k < g.K; k += 32) sd[k] = 0.0;
+        if (tid == 0) *cnt_all = 0u;
+        __syncthreads();
+        double m_acc = kNoShift;
+        unsigned n_eval = 0;
+        for (uint64_t k = warp; k < v.cnt; k += kGWarps) {
+            const uint64_t i = v.first + k;
+            double part = 0.0;  // this lane's share of ln J
+            bool inside = true;
+            if (KIND == 1) {
+                warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) {
+                    const double y = Coord<double>::map(w, lo_s[j], b_s[j]);
+                    const double one_m = (1.0 - y) * (1.0 + y);
+                    part += log1p(y * y) - 2.0 * log(one_m);
+                    return y / one_m;
+                }, ud);
+            } else {
+                warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) {
+                    const double z = normcdfinv(unit_f64(w));
+                    part += z * z;
+                    return z;
+                }, zb);
+                for (int r = lane; r < g.d; r += 32) {  // v = mean + F z, one row per lane
+                    const double *row = fac + r * g.d;
+                    double acc = mean[r];
+                    for (int j = 0; j < g.d; ++j) acc = fma(row[j], zb[j], acc);
+                    ud[r] = acc;
+                    inside = inside && acc >= lo_s[r] && acc < b_s[r];
+                }
+                part *= 0.5;
+                __syncwarp();
+            }
+            const double ljac = warp_sum(part);
+            if (KIND == 2 && !__all_sync(0xffffffffu, inside)) continue;  // weight 0, counted in n
+            const double S = warp_action<double>(ud, next, g, ga.cd) - ljac;
+            if (S < m_acc - kRescaleMargin) {
+                const double f = exp(S - m_acc), f2 = f * f;
+                for (int kk = lane; kk < g.K; kk += 32) sd[kk] *= second_order(kk, g.R) ? f2 : f;
+                m_acc = S;
+                __syncwarp();  // another lane owns some of the sums it rescaled
+            }
+            const double w = exp(m_acc - S);
+            if (lane == 0) {
+                sd[0] += w;
+                sd[1] += w * w;
+            }
+            lane_products(ud, g, [&](int r, double q) {
+                const double wq = w * q;
+                sd[2 + r] += wq;
+                sd[2 + g.R + r] += w * wq;
+                sd[2 + 2 * g.R + r] += wq * wq;
+            });
+            ++n_eval;
+            __syncwarp();
+        }
+        if (lane == 0) {
+            mw[warp] = m_acc;
+            atomicAdd(cnt_all, n_eval);
+        }
+        __syncthreads();
+        // chunk record: warps merged in order at the smallest warp shift
+        double mb = mw[0];
+        for (int w = 1; w < kGWarps; ++w) mb = fmin(mb, mw[w]);
+        double *out = args.partials + c * (g.K + 2);
+        for (int k = tid; k < g.K; k += kGBlock) {
+            const bool sq = second_order(k, g.R);
+            double acc = 0.0;
+            for (int w = 0; w < kGWarps; ++w) {
+                const double f = mw[w] == mb ? 1.0 : exp(mb - mw[w]);
+                const double val = reinterpret_cast<const double *>(sm + L.sums)[w * (g.K + g.R + 1) + k];
+                acc = __dadd_rn(acc, __dmul_rn(val, sq ? f * f : f));
+            }
+            out[2 + k] = acc;
+        }
+        if (tid == 0) {
+            out[0] = static_cast<double>(v.cnt);
+            out[1] = mb == kNoShift ? INFINITY : mb;  // no sample with weight in the chunk
+            if (args.stats) atomicAdd(args.stats, static_cast<unsigned long long>(*cnt_all));
+        }
+    }
+}
+
 // Per-subvolume reference action: the smallest FP32 action among the first
 // hint_samples(n_s) samples.  One CTA per subvolume, warp per sample.
 __global__ void __launch_bounds__(kGBlock) generic_hint(const GenArgs ga) {
@@ -463,10 +595,42 @@ cudaError_t gen_eval(const EvalArgs &a, const LatticeParams &p, int mode, cudaSt
     return cudaGetLastError();
 }
 
+template <int KIND>
+cudaError_t mapped_launcher(const IntegrandArgs &args, const LatticeParams &p, const MapArgs &m, uint32_t seed,
+                            uint32_t job, int grid, cudaStream_t st) {
+    GenArgs ga = make_gen_args(args, p, seed, job);
+    ga.L = gen_layout(ga.g, KIND == 2);
+    cudaError_t e = cudaFuncSetAttribute(generic_mapped<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, ga.L.total);
+    if (e != cudaSuccess) return e;
+    generic_mapped<KIND><<<grid, kGBlock, ga.L.total, st>>>(ga, m);
+    return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t mapped_occupancy(int nx, int nt, int *blocks_per_sm) {
+    const GenLayout L = gen_layout(gen_shape(nx, nt), KIND == 2);
+    cudaError_t e = cudaFuncSetAttribute(generic_mapped<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, generic_mapped<KIND>, kGBlock, L.total);
+}
+
 const ShapeKernels kGeneric = {0, 0, 1, {gen_integrand_launcher<true>, gen_integrand_launcher<false>},
                                {gen_occupancy<true>, gen_occupancy<false>}, gen_eval};
 
 }  // namespace
+
+cudaError_t launch_mapped(const IntegrandArgs &a, const LatticeParams &p, const MapArgs &m, uint32_t seed, uint32_t job,
+                          int grid, cudaStream_t st) {
+    if (m.kind == 1) return mapped_launcher<1>(a, p, m, seed, job, grid, st);
+    if (m.kind == 2) return mapped_launcher<2>(a, p, m, seed, job, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t occupancy_mapped(int nx, int nt, int kind, int *blocks_per_sm) {
+    if (kind == 1) return mapped_occupancy<1>(nx, nt, blocks_per_sm);
+    if (kind == 2) return mapped_occupancy<2>(nx, nt, blocks_per_sm);
+    return cudaErrorInvalidValue;
+}
 
 const ShapeKernels *generic_shape(int nx, int nt) {
     if (nx < 2 || nt < 1 || nx * nt > kMaxD) return nullptr;

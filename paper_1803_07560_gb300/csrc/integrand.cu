@@ -59,7 +59,7 @@ __global__ void merge_subvolumes(const MergeArgs a) {
     for (int j = 0; j < a.d; ++j) log_vol += log(a.hi[s * a.d + j] - a.lo[s * a.d + j]);
     slot[0] = n;
     slot[1] = m;
-    slot[2] = log_vol;
+    slot[2] = a.log_norm_set ? a.log_norm : log_vol;
 }
 
 // ---------------------------------------------------------------------------
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kTotThreads) merge_totals(const TotalsArgs a) 
     const bool inf_err = block_max(bad, sh) > 0.0;
     if (t == 0) {
         a.totals[0] = L + log(Z);
-        a.totals[1] = inf_err ? INFINITY : sqrt(VZ) / Z;
+        a.totals[1] = inf_err ? INFINITY : sqrt(VZ > 0.0 ? VZ : 0.0) / Z;
         a.totals[2] = n_tot;
         a.totals[3] = used;
     }
