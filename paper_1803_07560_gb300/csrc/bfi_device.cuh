@@ -36,16 +36,69 @@ inline RoundKeys make_round_keys(uint32_t seed, uint32_t job_id) {
     return rk;
 }
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) {
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return static_cast<uint32_t>((static_cast<uint64_t>(a) * b) >> 32);
+#endif
+}
+
+// Rounds r0..9 of Philox4x32-10 on the state c.
+__host__ __device__ __forceinline__ uint4 philox_rounds(uint4 c, const RoundKeys &rk, int r0) {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
+    for (int r = r0; r < 10; ++r) {
         const uint32_t lo0 = kPhiloxM0 * c.x;
-        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t hi0 = mulhi32(kPhiloxM0, c.x);
         const uint32_t lo1 = kPhiloxM1 * c.z;
-        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+        const uint32_t hi1 = mulhi32(kPhiloxM1, c.z);
         c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
     }
     return c;
+}
+
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) { return philox_rounds(c, rk, 0); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 with a per-chunk prefix.  The counters of one chunk differ
+// only in the low index word x: (q, x, h, s) with the block q, the high index
+// word h (chunks are a power-of-two number of samples, aligned, so they never
+// cross a multiple of 2^32) and sub_id s fixed.  In round 1 both products
+// (of q and of h) are then fixed, in round 2 the product of word 2, in round
+// 3 the product of word 0; philox_prefix folds those, with the round keys
+// they meet, into five words, and philox_from_prefix finishes from x with
+// 16 of the 20 products.  The result equals philox4x32_10((q, x, h, s)).
+// ---------------------------------------------------------------------------
+struct __align__(16) PhiloxPrefix {
+    uint32_t a;    // round 1: word 0 = a ^ x
+    uint32_t g;    // round 2: word 2 = hi(M0 word0) ^ g
+    uint32_t fk;   // round 3: word 0 = hi(M1 word2) ^ fk
+    uint32_t h;    // round 3: word 2 = h ^ lo(M0 word0 of round 2)
+    uint32_t l3;   // round 3: word 3
+    uint32_t pad[3];
+};
+
+__host__ __device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t q, uint32_t h, uint32_t s,
+                                                               const RoundKeys &rk) {
+    // round 1 from (q, x, h, s): (hi(M1 h) ^ x ^ k0, lo(M1 h), hi(M0 q) ^ s ^ k1, lo(M0 q))
+    const uint32_t w1 = kPhiloxM1 * h, w2 = mulhi32(kPhiloxM0, q) ^ s ^ rk.k1[0], w3 = kPhiloxM0 * q;
+    // round 2: word 0 = hi(M1 w2) ^ w1 ^ k0 and word 1 = lo(M1 w2) are fixed
+    const uint32_t e = mulhi32(kPhiloxM1, w2) ^ w1 ^ rk.k0[1], f = kPhiloxM1 * w2;
+    PhiloxPrefix p;
+    p.a = mulhi32(kPhiloxM1, h) ^ rk.k0[0];
+    p.g = w3 ^ rk.k1[1];
+    // round 3: the product of word 0 (= e) is fixed
+    p.fk = f ^ rk.k0[2];
+    p.h = mulhi32(kPhiloxM0, e) ^ rk.k1[2];
+    p.l3 = kPhiloxM0 * e;
+    return p;
+}
+
+__host__ __device__ __forceinline__ uint4 philox_from_prefix(uint32_t x, const PhiloxPrefix &p, const RoundKeys &rk) {
+    const uint32_t c0 = p.a ^ x;                                   // round 1
+    const uint32_t c2 = mulhi32(kPhiloxM0, c0) ^ p.g, c3 = kPhiloxM0 * c0;   // round 2
+    const uint4 c = make_uint4(mulhi32(kPhiloxM1, c2) ^ p.fk, kPhiloxM1 * c2, p.h ^ c3, p.l3);  // round 3
+    return philox_rounds(c, rk, 3);
 }
 
 // ---------------------------------------------------------------------------

@@ -143,6 +143,73 @@ __device__ __forceinline__ void make_point_smem(uint64_t i, uint32_t sid, const 
     }
 }
 
+// The same two from the chunk's Philox prefixes (one per block q, in shared
+// memory): x is the low word of the sample index.
+template <int D>
+__device__ __forceinline__ void sample_words_pre(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
+                                                 uint32_t (&w)[D]) {
+    constexpr int NQ = (D + 3) / 4;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint4 b = philox_from_prefix(x, pre[q], rk);
+        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (4 * q + t < D) w[4 * q + t] = w4[t];
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void make_point_pre(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
+                                               const float2 *box, float (&u)[D]) {
+    constexpr int NQ = (D + 3) / 4;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint4 b = philox_from_prefix(x, pre[q], rk);
+        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = 4 * q + t;
+            if (j < D) {
+                const float2 bw = box[j];
+                u[j] = Coord<float>::map(w4[t], bw.x, bw.y);
+            }
+        }
+    }
+}
+
+// Screen point of the FP64 kernel: y = fmaf(1.m, w, lo') with 1.m the word's
+// top 23 bits as a float in [1,2) and lo' = lo - (1 - 2^-24) w folded per
+// chunk (box_scr), one operation fewer per coordinate than the FP32 point.
+// It differs from the FP32 point by the rounding of lo' (under 1e-6 here),
+// which the screen's margin covers.
+template <int D>
+__device__ __forceinline__ void make_screen_point_pre(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
+                                                      const float2 *box_scr, float (&u)[D]) {
+    constexpr int NQ = (D + 3) / 4;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint4 b = philox_from_prefix(x, pre[q], rk);
+        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = 4 * q + t;
+            if (j < D) {
+                const float2 bw = box_scr[j];
+                u[j] = __fmaf_rn(__uint_as_float(0x3f800000u | (w4[t] >> 9)), bw.y, bw.x);
+            }
+        }
+    }
+}
+
+// Prefixes of the chunk's blocks q = 0 .. NQ-1 (threads 0 .. NQ-1; the
+// caller synchronises before use).
+template <int D>
+__device__ __forceinline__ void chunk_prefixes(const ChunkView &v, const RoundKeys &rk, PhiloxPrefix *pre) {
+    constexpr int NQ = (D + 3) / 4;
+    if (threadIdx.x < NQ) pre[threadIdx.x] = philox_prefix(threadIdx.x, static_cast<uint32_t>(v.first >> 32), v.sid, rk);
+}
+
 // Running minimum shared across the CTA at fixed points of the sample loop:
 // every thread contributes, then every thread reads the same value, so the
 // decisions that depend on it do not depend on timing.  S >= 0, so the float
@@ -362,8 +429,8 @@ __device__ __forceinline__ int dequeue32(uint32_t *q, int count) {
 // queue and are evaluated in FP64: Philox words drawn again, FP64 point,
 // action, products and weight.  The margin bounds |S_f32(y_f32) - S(y_f64)|:
 // the FP32 rounding of the action (~(d + 10) eps_32 S) plus the point
-// difference (|y_f32 - y_f64| <= ~1.1e-6, times sum_j |dS/dy_j| <=
-// ~52 sqrt(2 d S) for unit parameters: 0.004 at 10x2, 0.3 at 64x8).
+// difference (|y_f32 - y_f64| <= ~1.8e-6 for the screen point, times
+// sum_j |dS/dy_j| <= ~52 sqrt(2 d S) for unit parameters: 0.007 at 10x2).
 // ---------------------------------------------------------------------------
 template <int NX, int NT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(const IntegrandArgs args,
@@ -376,7 +443,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
     constexpr int WARPS = BLOCK / 32;
     __shared__ ChunkShared<BLOCK> sh;
     __shared__ double s_lo[D], s_w[D];
-    __shared__ float2 s_box[D];  // the same bounds as floats, for the FP32 screen
+    __shared__ float2 s_box[D];  // (lo', width) as floats for the FP32 screen (make_screen_point_pre)
+    __shared__ PhiloxPrefix s_pre[(D + 3) / 4];
     __shared__ double s_sums[K * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -388,8 +456,11 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         if (tid < D) {
             s_lo[tid] = v.lo[tid];
             s_w[tid] = v.hi[tid] - v.lo[tid];
-            BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
+            float lo_f, w_f;
+            BoxPair<float>::load(v.lo, v.hi, tid, lo_f, w_f);
+            s_box[tid] = make_float2(__fmaf_rn(-0.99999994f, w_f, lo_f), w_f);
         }
+        chunk_prefixes<D>(v, rk, s_pre);
         const float hint = args.hint[v.s];
         float m_ref = hint;
         double m_acc = static_cast<double>(hint);
@@ -405,7 +476,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         // FP64 evaluation of queue entry 'lane' (a sample offset in the chunk)
         auto evaluate = [&](uint32_t k) {
             uint32_t w[D];
-            sample_words<D>(v.first + k, v.sid, rk, w);
+            sample_words_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, w);
             double u[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) u[j] = Coord<double>::map(w[j], s_lo[j], s_w[j]);
@@ -420,23 +491,30 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
             accumulate<double, K, R, BLOCK>(acc, exp(m_acc - S), Q);
             ++n_eval;
         };
+        // m_ref changes only where the queue is evaluated (then made uniform
+        // across the warp) and where the CTA shares it; thr follows it
+        float thr = m_ref + args.skip_window + 1.0f;
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
             bool cand = false;
             if (k < v.cnt) {
                 float uf[D];
-                make_point_smem<D>(v.first + k, v.sid, rk, s_box, uf);
+                make_screen_point_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, uf);
                 const float S_f = action<NX, NT, float>(uf, lcf);
-                cand = S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f;
+                cand = __fmaf_rn(-1e-3f, S_f, S_f) <= thr;  // S_f <= m_ref + window + 1 + 0.1% of S_f
             }
             count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
             if (count >= 32) {
                 evaluate(queue[lane]);
                 count = dequeue32(queue, count);
+                m_ref = warp_min(m_ref);
+                thr = m_ref + args.skip_window + 1.0f;
             }
-            m_ref = warp_min(m_ref);
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&sh.min_bits, m_ref);
+            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
+                share_min(&sh.min_bits, m_ref);
+                thr = m_ref + args.skip_window + 1.0f;
+            }
         }
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
@@ -466,6 +544,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
     using Sums = SmemSums<float, K, BLOCK>;
     __shared__ ChunkShared<BLOCK> sh;
     __shared__ float2 s_box[D];  // (lo, width) as floats; every thread reads the same word
+    __shared__ PhiloxPrefix s_pre[(D + 3) / 4];
     __shared__ float s_sums[Sums::WORDS * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -475,6 +554,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
         const ChunkView v = chunk_view(args, c, D);
         if (tid < D) BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
+        chunk_prefixes<D>(v, rk, s_pre);
         const float hint = args.hint[v.s];
         float m_acc = hint, m_ref = hint;
         if (tid == 0) {
@@ -488,7 +568,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         int count = 0;
         auto evaluate = [&](uint32_t k) {
             float u[D];
-            make_point_smem<D>(v.first + k, v.sid, rk, s_box, u);
+            make_point_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, u);
             const float S_f = action<NX, NT, float>(u, lc);
             DF S{S_f, 0.f};
             if (S_f < m_ref + kRefineWindow) {
@@ -504,22 +584,29 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
             accumulate<float, K, R, BLOCK>(acc, expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l)), Q);
             ++n_eval;
         };
+        // m_ref changes only where the queue is evaluated (then made uniform
+        // across the warp) and where the CTA shares it; thr follows it
+        float thr = m_ref + args.skip_window;
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
             bool cand = false;
             if (k < v.cnt) {
                 float u[D];
-                make_point_smem<D>(v.first + k, v.sid, rk, s_box, u);
-                cand = action<NX, NT, float>(u, lc) <= m_ref + args.skip_window;
+                make_point_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, u);
+                cand = action<NX, NT, float>(u, lc) <= thr;
             }
             count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
             if (count >= 32) {
                 evaluate(queue[lane]);
                 count = dequeue32(queue, count);
+                m_ref = warp_min(m_ref);
+                thr = m_ref + args.skip_window;
             }
-            m_ref = warp_min(m_ref);
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) share_min(&sh.min_bits, m_ref);
+            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
+                share_min(&sh.min_bits, m_ref);
+                thr = m_ref + args.skip_window;
+            }
         }
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
