@@ -328,6 +328,11 @@ def run_bfi(args):
     if not args.skip_tte and world == 1:
         tte = run_time_to_error(bfi, dev, stream)
 
+    # ---- the rows built on the hot path: line protocol, adaptive, samplers ----
+    next_rows = None
+    if not args.skip_next and world == 1:
+        next_rows = run_next_rows(bfi, dev, stream)
+
     # ---- the serving workload: jobs arriving while others run ----
     serving = None
     if args.serving_seconds > 0 and world == 1:
@@ -343,7 +348,8 @@ def run_bfi(args):
         samples, times, cores = time_oracle(1)
         cpu = {"value": samples / times[0], "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": "32 of the 1024 subvolumes (every 32nd) x 2^20 points of the same job, FP64 oracle"}
-    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch, serving, tte)
+    report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch, serving, tte,
+           next_rows)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -451,6 +457,105 @@ def run_time_to_error(bfi, dev, stream, log2_budgets=range(10, 25, 2), target=1e
     return out
 
 
+def _time_plan(plan, lo, hi, seed, stream, reps=2):
+    """CUDA-event time of one plan execution (after one untimed run), its totals
+    and evaluated-sample count."""
+    import torch
+    plan.execute(lo, hi, seed, stream=stream)
+    best, tot = None, None
+    for _ in range(reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, tot = plan.execute(lo, hi, seed, stream=stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        best = ms if best is None else min(best, ms)
+    n_eval, _ = plan.stats()
+    return best, tot.cpu().numpy(), n_eval
+
+
+FP64_FMA_PEAK = 2 * 152 * 2.07e9   # FP64 lanes per SM and clock x SMs x clock (DESIGN.md)
+
+
+def run_next_rows(bfi, dev, stream):
+    """The rows built on top of the hot path: the N-sphere integrand of the
+    line protocol, adaptive subdivision with the convergence test, and the
+    transform and Gaussian samplers, each timed on the GPU."""
+    import math
+    import time
+    import torch
+    import workloads
+    out = {}
+    # N-sphere integrand (Listing 2's integrand; 2^30 samples over [-1,1]^3)
+    bfi.nsphere(3, 1 << 20, 1)
+    t0 = time.perf_counter()
+    res, err, sd = bfi.nsphere(3, 1 << 30, 1)
+    wall = time.perf_counter() - t0
+    out["nsphere"] = {"workload": "f = sqrt(1-|x|^2) over [-1,1]^3, 2^30 samples (FP64 points), synchronous call",
+                      "samples_per_s_wall": (1 << 30) / wall, "ms_wall": wall * 1e3, "result": res, "abs_err": err,
+                      "exact": math.pi ** 2 / 4, "split_dim": sd}
+    # adaptive subdivision: Listing 1's run, and the 10x2 lattice over its box
+    conv = bfi.convergence(2.0, 0.003, 0.0, 0.0, 8, 1 << 16)
+    t0 = time.perf_counter()
+    res, err, st = bfi.adaptive_nsphere(3, 100_000, 1, conv)
+    wall = time.perf_counter() - t0
+    out["adaptive_nsphere"] = {"workload": "Listing 1: half the unit 4-ball over [-1,1]^3, n = 1e5, factor 2, "
+                                           "rel_tol 0.003, max_depth 8", "ms_wall": wall * 1e3, "result": res,
+                               "abs_err": err, "exact": math.pi ** 2 / 4, "stats": st.as_dict()}
+    ctx = bfi.Context(dev.index or 0)
+    conv = bfi.convergence(2.0, 0.2, 0.0, 0.0, 10, 1 << 12)
+    ctx.adaptive_integrate(bfi.lattice(10, 2), -5.0, 5.0, 1 << 16, 2, bfi.convergence(2.0, 0.2, 0.0, 0.0, 1, 4))
+    t0 = time.perf_counter()
+    tot, st = ctx.adaptive_integrate(bfi.lattice(10, 2), -5.0, 5.0, 1 << 16, 2, conv)
+    wall = time.perf_counter() - t0
+    ctx.close()
+    out["adaptive_lattice"] = {"workload": "10x2 over [-5,5]^20, n = 2^16, factor 2, rel_tol 0.2, max_depth 10, "
+                                           "at most 4096 subvolumes per round, FP64", "ms_wall": wall * 1e3,
+                               "samples_per_s_wall": st.samples / wall, "logZ": float(tot[0]),
+                               "Z_err_rel": float(tot[1]), "stats": st.as_dict()}
+    lat = bfi.lattice(10, 2)
+    d, nr = 20, 6
+    # transform sampler: [-1,1]^20 (all of R^20) bisected into 1024 subvolumes, 2^16 points each
+    lo_np, hi_np = workloads.bisected_boxes(d, 10, half=1.0)
+    lo, hi = torch.tensor(lo_np, device=dev), torch.tensor(hi_np, device=dev)
+    samples = np.full(1024, 1 << 16, dtype=np.uint64)
+    plan = bfi.Plan(lat, samples, bfi.FP64)
+    plan.set_sampler(bfi.SAMPLE_TRANSFORM)
+    ms, t, n_eval = _time_plan(plan, lo, hi, 2, stream)
+    plan.close()
+    n = int(samples.sum())
+    ops = (6 + 8 + nr) * d   # per sample: range map, action, products (logarithms not counted)
+    out["transform"] = {"workload": "10x2, v = y/(1-y^2) over [-1,1]^20 bisected into 1024 subvolumes x 2^16 "
+                                    "points, FP64, mass2 = 0", "ms": ms, "samples_per_s": n / (ms * 1e-3),
+                        "roofline": {"bound": "fp64", "fp64_ops_per_sample": ops,
+                                     "frac_of_fp64_fma_peak": n * ops / (ms * 1e-3) / FP64_FMA_PEAK,
+                                     "note": "algebraic FP64 operations only; log, log1p and exp not counted"},
+                        "logZ": float(t[0]), "Z_err_rel": float(t[1]),
+                        "C_err_over_C0_max": float(np.max(t[4 + nr:4 + 2 * nr]) / t[4])}
+    # Gaussian sampler on the paper's box: the regulated linear-limit proposal
+    box_lo = torch.full((1, d), -5.0, dtype=torch.float64, device=dev)
+    box_hi = torch.full((1, d), 5.0, dtype=torch.float64, device=dev)
+    gauss = []
+    for k in (20, 24):
+        plan = bfi.Plan(lat, [1 << k], bfi.FP64)
+        plan.set_sampler(bfi.SAMPLE_GAUSSIAN, factor=bfi.gaussian_proposal(lat, 6.0))
+        ms, t, n_eval = _time_plan(plan, box_lo, box_hi, 2, stream)
+        plan.close()
+        ops = (d + 1 + 8 + nr) * d   # per sample: F z, |z|^2, action, products (Phi^-1 and exp not counted)
+        gauss.append({"samples": 1 << k, "ms": ms, "samples_per_s": (1 << k) / (ms * 1e-3),
+                      "inside_box": n_eval / (1 << k),
+                      "frac_of_fp64_fma_peak": (1 << k) * ops / (ms * 1e-3) / FP64_FMA_PEAK,
+                      "logZ": float(t[0]), "Z_err_rel": float(t[1]),
+                      "C_err_over_C0_max": float(np.max(t[4 + nr:4 + 2 * nr]) / t[4])})
+    out["gaussian"] = {"workload": "10x2 over the box [-5,5]^20 as one volume, proposal N(0, (A + I/36)^-1) "
+                                   "(linear limit, zero modes at sigma0 = 6), FP64", "runs": gauss,
+                       "note": "the weights exp(-S)/q are heavy-tailed for the nonlinear action (ln Z grows "
+                               "with the budget): the linear-limit proposal does not cover the zero-action "
+                               "configurations away from the constant line"}
+    return out
+
+
 def run_serving(bfi, seconds, rate=200.0, seed=5):
     """The serving workload: Poisson arrivals at 'rate' jobs/s for 'seconds',
     sizes from the batching distribution plus 5% 64x8 lattices (numpy PCG64,
@@ -499,7 +604,7 @@ def run_serving(bfi, seconds, rate=200.0, seed=5):
 
 
 def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch=None,
-           serving=None, tte=None):
+           serving=None, tte=None, next_rows=None):
     if rank == 0:
         line = {
             "metric": "samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
@@ -520,6 +625,7 @@ def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, f
             "batch": batch,
             "serving": serving,
             "time_to_error": tte,
+            "next_rows": next_rows,
         }
         print(json.dumps(line), flush=True)
 
@@ -538,6 +644,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-tte", action="store_true")
+    ap.add_argument("--skip-next", action="store_true",
+                    help="skip the N-sphere, adaptive and sampler measurements")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="arrival window of the serving workload (the full workload is 60 s; 0 skips it)")
     ap.add_argument("--samples-log2", type=int, default=20,

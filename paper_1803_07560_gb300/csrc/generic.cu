@@ -44,7 +44,7 @@ struct GenLayout {
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-// 'gauss' adds the Gaussian sampler's factor, mean and per-warp z vectors.
+// 'gauss' adds the Gaussian sampler's factor and mean.
 __host__ __device__ inline GenLayout gen_layout(const GenShape &g, bool gauss = false) {
     GenLayout L;
     int o = 0;
@@ -58,7 +58,7 @@ __host__ __device__ inline GenLayout gen_layout(const GenShape &g, bool gauss = 
     L.mw = o;    o = align16(o + 8 * kGWarps + 8);             // per-warp shift, counter
     L.fac = o;   if (gauss) o = align16(o + 8 * g.d * g.d);   // factor F, row-major
     L.mean = o;  if (gauss) o = align16(o + 8 * g.d);         // mean
-    L.zb = o;    if (gauss) o = align16(o + 8 * g.dpad * kGWarps);  // z per warp
+    L.zb = o;    o = align16(o + 8 * g.dpad * kGWarps);             // per warp: y of the range map, or u then z
     L.total = o;
     return L;
 }
@@ -385,15 +385,15 @@ __global__ void __launch_bounds__(kGBlock) generic_mapped(const GenArgs ga, cons
     double *lo_s = reinterpret_cast<double *>(sm + L.lo_d);
     double *b_s = reinterpret_cast<double *>(sm + L.w_d);  // KIND 1: width; KIND 2: upper bound
     double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.dpad;
-    double *zb = reinterpret_cast<double *>(sm + L.zb) + warp * g.dpad;
+    double *zb = reinterpret_cast<double *>(sm + L.zb) + warp * g.dpad;  // y (KIND 1) or u, then z (KIND 2)
     double *fac = reinterpret_cast<double *>(sm + L.fac);
     double *mean = reinterpret_cast<double *>(sm + L.mean);
     double *mw = reinterpret_cast<double *>(sm + L.mw);
     unsigned *cnt_all = reinterpret_cast<unsigned *>(mw + kGWarps);
     double *sd = reinterpret_cast<double *>(sm + L.sums) + warp * (g.K + g.R + 1);
     build_next(sm, L, g);
-    if (KIND == 2) {
-        for (int k = tid; k < g.d * g.d; k += kGBlock) fac[k] = mp.factor[k];
+    if (KIND == 2) {  // the factor transposed (fac[j d + r] = F[r][j]): lane r reads consecutive words
+        for (int k = tid; k < g.d * g.d; k += kGBlock) fac[(k % g.d) * g.d + k / g.d] = mp.factor[k];
         for (int k = tid; k < g.d; k += kGBlock) mean[k] = mp.mean ? mp.mean[k] : 0.0;
     }
 
@@ -413,29 +413,35 @@ __global__ void __launch_bounds__(kGBlock) generic_mapped(const GenArgs ga, cons
             const uint64_t i = v.first + k;
             double part = 0.0;  // this lane's share of ln J
             bool inside = true;
+            // the Philox blocks are drawn by lanes q = lane (4 words each); the
+            // per-coordinate maps then run on lanes j = lane, lane + 32, ...
             if (KIND == 1) {
                 warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) {
-                    const double y = Coord<double>::map(w, lo_s[j], b_s[j]);
+                    return Coord<double>::map(w, lo_s[j], b_s[j]);
+                }, zb);
+                for (int j = lane; j < g.d; j += 32) {
+                    const double y = zb[j];
                     const double one_m = (1.0 - y) * (1.0 + y);
                     part += log1p(y * y) - 2.0 * log(one_m);
-                    return y / one_m;
-                }, ud);
+                    ud[j] = y / one_m;
+                }
             } else {
-                warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) {
-                    const double z = normcdfinv(unit_f64(w));
+                warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return unit_f64(w); }, zb);
+                for (int j = lane; j < g.d; j += 32) {
+                    const double z = normcdfinv(zb[j]);
                     part += z * z;
-                    return z;
-                }, zb);
-                for (int r = lane; r < g.d; r += 32) {  // v = mean + F z, one row per lane
-                    const double *row = fac + r * g.d;
-                    double acc = mean[r];
-                    for (int j = 0; j < g.d; ++j) acc = fma(row[j], zb[j], acc);
-                    ud[r] = acc;
-                    inside = inside && acc >= lo_s[r] && acc < b_s[r];
+                    zb[j] = z;
                 }
                 part *= 0.5;
                 __syncwarp();
+                for (int r = lane; r < g.d; r += 32) {  // v = mean + F z, one row per lane
+                    double acc = mean[r];
+                    for (int j = 0; j < g.d; ++j) acc = fma(fac[j * g.d + r], zb[j], acc);
+                    ud[r] = acc;
+                    inside = inside && acc >= lo_s[r] && acc < b_s[r];
+                }
             }
+            __syncwarp();
             const double ljac = warp_sum(part);
             if (KIND == 2 && !__all_sync(0xffffffffu, inside)) continue;  // weight 0, counted in n
             const double S = warp_action<double>(ud, next, g, ga.cd) - ljac;
