@@ -107,9 +107,13 @@ __host__ __device__ __forceinline__ uint4 philox_from_prefix(uint32_t x, const P
 //   float:  1 + (w>>9) 2^-23 in [1,2), minus (1 - 2^-24)  =  ((w>>9) + 0.5) 2^-23
 //   double: 1 + w 2^-32 in [1,2),      minus (1 - 2^-33)  =  (w + 0.5) 2^-32
 // Both subtractions are exact (the results have 24 and 33 significant bits).
+// In float the exponent and the top word bits are joined by one funnel shift:
+// shifting (0x7f : w) right by 9 gives 0x3f800000 | (w >> 9).  (In the FP64
+// kernel's screen the constant it holds costs a spill, so that kernel keeps
+// the shift-and-or form, with the same bits.)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float unit_f32(uint32_t w) {
-    return __uint_as_float(0x3f800000u | (w >> 9)) - 0.99999994f;
+    return __uint_as_float(__funnelshift_r(w, 0x7fu, 9)) - 0.99999994f;
 }
 
 __device__ __forceinline__ double unit_f64(uint32_t w) {

@@ -178,15 +178,60 @@ __device__ __forceinline__ void make_point_pre(uint32_t x, const PhiloxPrefix *p
     }
 }
 
-// Screen point of the FP64 kernel: y = fmaf(1.m, w, lo') with 1.m the word's
-// top 23 bits as a float in [1,2) and lo' = lo - (1 - 2^-24) w folded per
-// chunk (box_scr), one operation fewer per coordinate than the FP32 point.
-// It differs from the FP32 point by the rounding of lo' (under 1e-6 here),
-// which the screen's margin covers.
+// Prefixes of the chunk's blocks q = 0 .. NQ-1 (threads 0 .. NQ-1; the
+// caller synchronises before use).
 template <int D>
-__device__ __forceinline__ void make_screen_point_pre(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
-                                                      const float2 *box_scr, float (&u)[D]) {
+__device__ __forceinline__ void chunk_prefixes(const ChunkView &v, const RoundKeys &rk, PhiloxPrefix *pre) {
     constexpr int NQ = (D + 3) / 4;
+    if (threadIdx.x < NQ) pre[threadIdx.x] = philox_prefix(threadIdx.x, static_cast<uint32_t>(v.first >> 32), v.sid, rk);
+}
+
+// ---------------------------------------------------------------------------
+// Packed FP32 screen for even NX.  Site m is paired with site m + NX/2:
+// P[h NT + l] = (u[h NT + l], u[(h + NX/2) NT + l]), h < NX/2.  The next-slice,
+// right and left neighbours of a pair are pairs too, except across the seam
+// (right of h = NX/2 - 1, left of h = 0) where the partner's halves come
+// swapped; so the residuals of two sites go through one f32x2 instruction
+// each.  Every component is rounded as the scalar residual rounds it (right -
+// left as one FMA with -1); only the order of the final sum differs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 swap2(float2 a) { return make_float2(a.y, a.x); }
+
+template <int NX, int NT>
+__device__ __forceinline__ float action_pairs(const float2 (&P)[(NX / 2) * NT], const LatticeConst<float> &c) {
+    constexpr int H = NX / 2;
+    const float2 cadv = make_float2(c.c_adv, c.c_adv), k1 = make_float2(c.k1, c.k1);
+    const float2 ncd = make_float2(c.neg_c_dif, c.neg_c_dif), m1 = make_float2(-1.f, -1.f);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+#pragma unroll
+        for (int l = 0; l < NT; ++l) {
+            const float2 here = P[h * NT + l];
+            const float2 next = P[h * NT + (l + 1) % NT];
+            const float2 right = h + 1 < H ? P[(h + 1) * NT + l] : swap2(P[l]);
+            const float2 left = h > 0 ? P[(h - 1) * NT + l] : swap2(P[(H - 1) * NT + l]);
+            const float2 t = __ffma2_rn(cadv, __ffma2_rn(m1, left, right), k1);
+            float2 R = __ffma2_rn(here, t, next);
+            R = __ffma2_rn(ncd, __fadd2_rn(right, left), R);
+            acc = __ffma2_rn(R, R, acc);
+        }
+    }
+    float S = (acc.x + acc.y) * c.inv_2Dtau;
+    if (c.half_mass2 != 0.f) {
+        float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < H * NT; ++k) s2 = __ffma2_rn(P[k], P[k], s2);
+        S = fmaf(c.half_mass2, s2.x + s2.y, S);
+    }
+    return S;
+}
+
+// Points of sample x in that pair layout; Map(word, box[j]) -> coordinate.
+template <int NX, int NT, typename Map>
+__device__ __forceinline__ void make_pairs_pre(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
+                                               const float2 *box, Map map, float2 (&P)[(NX / 2) * NT]) {
+    constexpr int D = NX * NT, NQ = (D + 3) / 4, H = NX / 2;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         const uint4 b = philox_from_prefix(x, pre[q], rk);
@@ -195,19 +240,50 @@ __device__ __forceinline__ void make_screen_point_pre(uint32_t x, const PhiloxPr
         for (int t = 0; t < 4; ++t) {
             const int j = 4 * q + t;
             if (j < D) {
-                const float2 bw = box_scr[j];
-                u[j] = __fmaf_rn(__uint_as_float(0x3f800000u | (w4[t] >> 9)), bw.y, bw.x);
+                const int m = j / NT, l = j % NT;
+                const float val = map(w4[t], box[j]);
+                if (m < H) P[m * NT + l].x = val;
+                else P[(m - H) * NT + l].y = val;
             }
         }
     }
 }
 
-// Prefixes of the chunk's blocks q = 0 .. NQ-1 (threads 0 .. NQ-1; the
-// caller synchronises before use).
-template <int D>
-__device__ __forceinline__ void chunk_prefixes(const ChunkView &v, const RoundKeys &rk, PhiloxPrefix *pre) {
-    constexpr int NQ = (D + 3) / 4;
-    if (threadIdx.x < NQ) pre[threadIdx.x] = philox_prefix(threadIdx.x, static_cast<uint32_t>(v.first >> 32), v.sid, rk);
+// The FP32 point (Coord<float>::map), and the FP64 kernel's screen point
+// y = fmaf(1.m, w, lo') with 1.m the word's top 23 bits as a float in [1,2)
+// and lo' = lo - (1 - 2^-24) w folded per chunk into the box table, one
+// operation fewer per coordinate; it differs from the FP32 point by the
+// rounding of lo' (under 1e-6 here), which the screen's margin covers.
+struct MapF32 {
+    __device__ __forceinline__ float operator()(uint32_t w, float2 bw) const { return Coord<float>::map(w, bw.x, bw.y); }
+};
+struct MapScreen {
+    __device__ __forceinline__ float operator()(uint32_t w, float2 bw) const {
+        return __fmaf_rn(__uint_as_float(0x3f800000u | (w >> 9)), bw.y, bw.x);
+    }
+};
+
+// FP32 screen action of sample x: packed for even NX, scalar otherwise.
+template <int NX, int NT, typename Map>
+__device__ __forceinline__ float screen_action(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
+                                               const float2 *box, const LatticeConst<float> &c) {
+    if constexpr (NX % 2 == 0) {
+        float2 P[(NX / 2) * NT];
+        make_pairs_pre<NX, NT>(x, pre, rk, box, Map{}, P);
+        return action_pairs<NX, NT>(P, c);
+    } else {
+        constexpr int D = NX * NT, NQ = (D + 3) / 4;
+        float u[D];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const uint4 b = philox_from_prefix(x, pre[q], rk);
+            const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (4 * q + t < D) u[4 * q + t] = Map{}(w4[t], box[4 * q + t]);
+        }
+        return action<NX, NT, float>(u, c);
+    }
 }
 
 // Running minimum shared across the CTA at fixed points of the sample loop:
@@ -443,7 +519,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
     constexpr int WARPS = BLOCK / 32;
     __shared__ ChunkShared<BLOCK> sh;
     __shared__ double s_lo[D], s_w[D];
-    __shared__ float2 s_box[D];  // (lo', width) as floats for the FP32 screen (make_screen_point_pre)
+    __shared__ float2 s_box[D];  // (lo', width) as floats for the FP32 screen (MapScreen)
     __shared__ PhiloxPrefix s_pre[(D + 3) / 4];
     __shared__ double s_sums[K * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
@@ -499,9 +575,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
             const uint64_t k = row * BLOCK + tid;
             bool cand = false;
             if (k < v.cnt) {
-                float uf[D];
-                make_screen_point_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, uf);
-                const float S_f = action<NX, NT, float>(uf, lcf);
+                const float S_f = screen_action<NX, NT, MapScreen>(static_cast<uint32_t>(v.first + k), s_pre, rk,
+                                                                   s_box, lcf);
                 cand = __fmaf_rn(-1e-3f, S_f, S_f) <= thr;  // S_f <= m_ref + window + 1 + 0.1% of S_f
             }
             count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
@@ -591,11 +666,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
             bool cand = false;
-            if (k < v.cnt) {
-                float u[D];
-                make_point_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, u);
-                cand = action<NX, NT, float>(u, lc) <= thr;
-            }
+            if (k < v.cnt)
+                cand = screen_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, lc) <= thr;
             count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
             if (count >= 32) {
                 evaluate(queue[lane]);
