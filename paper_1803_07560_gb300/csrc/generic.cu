@@ -223,10 +223,97 @@ struct GenArgs {
 };
 
 // ---------------------------------------------------------------------------
-// The integrand.  FP64 = true: FP32 screen, FP64 evaluation; false: FP32
-// screen and evaluation with the compensated action near the minimum.
+// Register-resident FP32 screen for Nx = 32 SPL.  Lane t owns the spatial
+// sites [SPL t, SPL t + SPL) with all NT time slices: the coordinates
+// [C t, C t + C), C = SPL NT, which are whole Philox blocks (C is a multiple
+// of 4).  It draws its own blocks, keeps the field and the chunk's box in
+// registers, and takes the one site of each spatial neighbour from lanes
+// t - 1 and t + 1 (2 NT shuffles), so the screen touches no shared memory.
+// The per-lane residual sums meet in an XOR butterfly (bit-identical on all
+// lanes).  Points and residuals round as the shared-memory screen's do; only
+// the order of the sum differs.
 // ---------------------------------------------------------------------------
-template <bool FP64>
+template <int SPL, int NT>
+struct LaneScreen {
+    static constexpr int C = SPL * NT;
+    static_assert(C % 4 == 0, "a lane's coordinates must be whole Philox blocks");
+    float lo[C], w[C];
+
+    __device__ __forceinline__ void load(const float2 *bf) {
+        const int j0 = (threadIdx.x & 31) * C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            lo[c] = bf[j0 + c].x;
+            w[c] = bf[j0 + c].y;
+        }
+    }
+
+    __device__ __forceinline__ float action(uint64_t i, uint32_t sid, const RoundKeys &rk,
+                                            const LatticeConst<float> &cf) const {
+        const int lane = threadIdx.x & 31;
+        float X[C];  // X[s NT + l]
+#pragma unroll
+        for (int b = 0; b < C / 4; ++b) {
+            const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(lane * (C / 4) + b), static_cast<uint32_t>(i),
+                                                     static_cast<uint32_t>(i >> 32), sid),
+                                          rk);
+            X[4 * b + 0] = Coord<float>::map(r.x, lo[4 * b + 0], w[4 * b + 0]);
+            X[4 * b + 1] = Coord<float>::map(r.y, lo[4 * b + 1], w[4 * b + 1]);
+            X[4 * b + 2] = Coord<float>::map(r.z, lo[4 * b + 2], w[4 * b + 2]);
+            X[4 * b + 3] = Coord<float>::map(r.w, lo[4 * b + 3], w[4 * b + 3]);
+        }
+        float left[NT], right[NT];
+#pragma unroll
+        for (int l = 0; l < NT; ++l) {
+            left[l] = __shfl_sync(0xffffffffu, X[(SPL - 1) * NT + l], (lane + 31) & 31);
+            right[l] = __shfl_sync(0xffffffffu, X[l], (lane + 1) & 31);
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int sp = 0; sp < SPL; ++sp) {
+#pragma unroll
+            for (int l = 0; l < NT; ++l) {
+                const float here = X[sp * NT + l];
+                const float nxt = X[sp * NT + (l + 1) % NT];
+                const float r = sp + 1 < SPL ? X[(sp + 1) * NT + l] : right[l];
+                const float le = sp > 0 ? X[(sp - 1) * NT + l] : left[l];
+                const float t = fmaf(cf.c_adv, r - le, cf.k1);
+                float R = fmaf(here, t, nxt);
+                R = fmaf(cf.neg_c_dif, r + le, R);
+                acc = fmaf(R, R, acc);
+            }
+        }
+        float S = warp_sum(acc) * cf.inv_2Dtau;
+        if (cf.half_mass2 != 0.f) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) s2 = fmaf(X[c], X[c], s2);
+            S = fmaf(cf.half_mass2, warp_sum(s2), S);
+        }
+        return S;
+    }
+};
+
+// Placeholder screen of the shared-memory path (SPL = 0).
+struct NoLaneScreen {
+    __device__ __forceinline__ void load(const float2 *) {}
+};
+template <int SPL, int NT>
+struct ScreenOf {
+    using type = LaneScreen<SPL, NT>;
+};
+template <int NT>
+struct ScreenOf<0, NT> {
+    using type = NoLaneScreen;
+};
+
+// ---------------------------------------------------------------------------
+// The integrand.  FP64 = true: FP32 screen, FP64 evaluation; false: FP32
+// screen and evaluation with the compensated action near the minimum.  SPL > 0
+// takes the register-resident screen (Nx = 32 SPL, NT time slices); SPL = 0
+// the shared-memory one, for any shape.
+// ---------------------------------------------------------------------------
+template <bool FP64, int SPL, int NT>
 __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
     extern __shared__ __align__(16) unsigned char sm[];
     const IntegrandArgs &args = ga.a;
@@ -256,6 +343,8 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
         }
         if (tid == 0) *cnt_all = 0u;
         __syncthreads();
+        typename ScreenOf<SPL, NT>::type scr;
+        scr.load(bf);
         const float hint = args.hint[v.s];
         float m_ref = hint;
         double m_acc = static_cast<double>(hint);
@@ -263,8 +352,13 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
         unsigned n_eval = 0;
         for (uint64_t k = warp; k < v.cnt; k += kGWarps) {
             const uint64_t i = v.first + k;
-            warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
-            const float S_f = warp_action<float>(uf, next, g, ga.cf);
+            float S_f;
+            if constexpr (SPL > 0) {
+                S_f = scr.action(i, v.sid, ga.rk, ga.cf);
+            } else {
+                warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
+                S_f = warp_action<float>(uf, next, g, ga.cf);
+            }
             if (FP64) {
                 if (!(S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f)) continue;
                 warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<double>::map(w, ld[j], wd[j]); }, ud);
@@ -289,6 +383,8 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
                 });
             } else {
                 if (!(S_f <= m_ref + args.skip_window)) continue;
+                if constexpr (SPL > 0)  // the evaluation reads the point from shared memory
+                    warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
                 DF S{S_f, 0.f};
                 if (S_f < m_ref + kRefineWindow) {
                     S = warp_action_df(uf, next, g, ga.cdf);
@@ -568,26 +664,29 @@ GenArgs make_gen_args(const IntegrandArgs &a, const LatticeParams &p, uint32_t s
     return ga;
 }
 
-template <bool FP64>
+template <bool FP64, int SPL = 0, int NT = 0>
 cudaError_t gen_integrand_launcher(const IntegrandArgs &args, const LatticeParams &p, uint32_t seed, uint32_t job,
                                    int grid, cudaStream_t st) {
     const GenArgs ga = make_gen_args(args, p, seed, job);
     cudaError_t e = cudaFuncSetAttribute(generic_hint, cudaFuncAttributeMaxDynamicSharedMemorySize, ga.L.total);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(generic_integrand<FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, ga.L.total);
+        e = cudaFuncSetAttribute(generic_integrand<FP64, SPL, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 ga.L.total);
     if (e != cudaSuccess) return e;
     generic_hint<<<static_cast<unsigned>(args.nsub), kGBlock, ga.L.total, st>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    generic_integrand<FP64><<<grid, kGBlock, ga.L.total, st>>>(ga);
+    generic_integrand<FP64, SPL, NT><<<grid, kGBlock, ga.L.total, st>>>(ga);
     return cudaGetLastError();
 }
 
-template <bool FP64>
+template <bool FP64, int SPL = 0, int NT = 0>
 cudaError_t gen_occupancy(int nx, int nt, int *blocks_per_sm) {
     const GenLayout L = gen_layout(gen_shape(nx, nt));
-    cudaError_t e = cudaFuncSetAttribute(generic_integrand<FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    cudaError_t e = cudaFuncSetAttribute(generic_integrand<FP64, SPL, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         L.total);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, generic_integrand<FP64>, kGBlock, L.total);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, generic_integrand<FP64, SPL, NT>, kGBlock,
+                                                         L.total);
 }
 
 cudaError_t gen_eval(const EvalArgs &a, const LatticeParams &p, int mode, cudaStream_t st) {
@@ -623,6 +722,15 @@ cudaError_t mapped_occupancy(int nx, int nt, int *blocks_per_sm) {
 const ShapeKernels kGeneric = {0, 0, 1, {gen_integrand_launcher<true>, gen_integrand_launcher<false>},
                                {gen_occupancy<true>, gen_occupancy<false>}, gen_eval};
 
+// Shapes with Nx = 32 SPL and SPL NT in {4, 8, 16}: the register-resident screen.
+#define BFI_LANES(SPL, NT)                                                                                   \
+    {32 * SPL, NT, 1, {gen_integrand_launcher<true, SPL, NT>, gen_integrand_launcher<false, SPL, NT>},      \
+     {gen_occupancy<true, SPL, NT>, gen_occupancy<false, SPL, NT>}, gen_eval}
+const ShapeKernels kLanes[] = {BFI_LANES(1, 4),  BFI_LANES(1, 8), BFI_LANES(1, 16), BFI_LANES(2, 2),
+                               BFI_LANES(2, 4),  BFI_LANES(2, 8), BFI_LANES(4, 1),  BFI_LANES(4, 2),
+                               BFI_LANES(4, 4),  BFI_LANES(8, 1), BFI_LANES(8, 2),  BFI_LANES(16, 1)};
+#undef BFI_LANES
+
 }  // namespace
 
 cudaError_t launch_mapped(const IntegrandArgs &a, const LatticeParams &p, const MapArgs &m, uint32_t seed, uint32_t job,
@@ -640,6 +748,8 @@ cudaError_t occupancy_mapped(int nx, int nt, int kind, int *blocks_per_sm) {
 
 const ShapeKernels *generic_shape(int nx, int nt) {
     if (nx < 2 || nt < 1 || nx * nt > kMaxD) return nullptr;
+    for (const ShapeKernels &k : kLanes)
+        if (k.nx == nx && k.nt == nt) return &k;
     return &kGeneric;
 }
 
