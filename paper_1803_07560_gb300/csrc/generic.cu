@@ -44,8 +44,11 @@ struct GenLayout {
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-// 'gauss' adds the Gaussian sampler's factor and mean.
-__host__ __device__ inline GenLayout gen_layout(const GenShape &g, bool gauss = false) {
+// 'mapped' (the sampler kind of the mapped kernel, 0 for the plain integrand)
+// adds the per-warp y / z vectors, and for the Gaussian sampler (2) its
+// factor and mean.
+__host__ __device__ inline GenLayout gen_layout(const GenShape &g, int mapped = 0) {
+    const bool gauss = mapped == 2;
     GenLayout L;
     int o = 0;
     L.next = o;  o = align16(o + 2 * g.d);                    // uint16 next-time-slice index per site
@@ -58,7 +61,7 @@ __host__ __device__ inline GenLayout gen_layout(const GenShape &g, bool gauss = 
     L.mw = o;    o = align16(o + 8 * kGWarps + 8);             // per-warp shift, counter
     L.fac = o;   if (gauss) o = align16(o + 8 * g.d * g.d);   // factor F, row-major
     L.mean = o;  if (gauss) o = align16(o + 8 * g.d);         // mean
-    L.zb = o;    o = align16(o + 8 * g.dpad * kGWarps);             // per warp: y of the range map, or u then z
+    L.zb = o;    if (mapped) o = align16(o + 8 * g.dpad * kGWarps);  // per warp: y of the range map, or u then z
     L.total = o;
     return L;
 }
@@ -704,7 +707,7 @@ template <int KIND>
 cudaError_t mapped_launcher(const IntegrandArgs &args, const LatticeParams &p, const MapArgs &m, uint32_t seed,
                             uint32_t job, int grid, cudaStream_t st) {
     GenArgs ga = make_gen_args(args, p, seed, job);
-    ga.L = gen_layout(ga.g, KIND == 2);
+    ga.L = gen_layout(ga.g, KIND);
     cudaError_t e = cudaFuncSetAttribute(generic_mapped<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, ga.L.total);
     if (e != cudaSuccess) return e;
     generic_mapped<KIND><<<grid, kGBlock, ga.L.total, st>>>(ga, m);
@@ -713,7 +716,7 @@ cudaError_t mapped_launcher(const IntegrandArgs &args, const LatticeParams &p, c
 
 template <int KIND>
 cudaError_t mapped_occupancy(int nx, int nt, int *blocks_per_sm) {
-    const GenLayout L = gen_layout(gen_shape(nx, nt), KIND == 2);
+    const GenLayout L = gen_layout(gen_shape(nx, nt), KIND);
     cudaError_t e = cudaFuncSetAttribute(generic_mapped<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, generic_mapped<KIND>, kGBlock, L.total);
