@@ -232,6 +232,7 @@ struct GenArgs {
 // of 4).  It draws its own blocks, keeps the field and the chunk's box in
 // registers, and takes the one site of each spatial neighbour from lanes
 // t - 1 and t + 1 (2 NT shuffles), so the screen touches no shared memory.
+// For even NT the residuals of slices l and l + NT/2 run as one f32x2 pair.
 // The per-lane residual sums meet in an XOR butterfly (bit-identical on all
 // lanes).  Points and residuals round as the shared-memory screen's do; only
 // the order of the sum differs.
@@ -271,19 +272,47 @@ struct LaneScreen {
             left[l] = __shfl_sync(0xffffffffu, X[(SPL - 1) * NT + l], (lane + 31) & 31);
             right[l] = __shfl_sync(0xffffffffu, X[l], (lane + 1) & 31);
         }
-        float acc = 0.f;
+        float acc;
+        if constexpr (NT % 2 == 0) {
+            // slices l and l + NT/2 of a site as one f32x2 pair: the next
+            // slice of a pair is the following pair (swapped after the last)
+            constexpr int HN = NT / 2;
+            const float2 cadv = make_float2(cf.c_adv, cf.c_adv), k1 = make_float2(cf.k1, cf.k1);
+            const float2 ncd = make_float2(cf.neg_c_dif, cf.neg_c_dif), m1 = make_float2(-1.f, -1.f);
+            float2 a2 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int sp = 0; sp < SPL; ++sp) {
+            for (int sp = 0; sp < SPL; ++sp) {
 #pragma unroll
-            for (int l = 0; l < NT; ++l) {
-                const float here = X[sp * NT + l];
-                const float nxt = X[sp * NT + (l + 1) % NT];
-                const float r = sp + 1 < SPL ? X[(sp + 1) * NT + l] : right[l];
-                const float le = sp > 0 ? X[(sp - 1) * NT + l] : left[l];
-                const float t = fmaf(cf.c_adv, r - le, cf.k1);
-                float R = fmaf(here, t, nxt);
-                R = fmaf(cf.neg_c_dif, r + le, R);
-                acc = fmaf(R, R, acc);
+                for (int l = 0; l < HN; ++l) {
+                    const float2 here = make_float2(X[sp * NT + l], X[sp * NT + l + HN]);
+                    const float2 nxt = l + 1 < HN ? make_float2(X[sp * NT + l + 1], X[sp * NT + l + 1 + HN])
+                                                  : make_float2(X[sp * NT + HN], X[sp * NT]);
+                    const float2 r = sp + 1 < SPL ? make_float2(X[(sp + 1) * NT + l], X[(sp + 1) * NT + l + HN])
+                                                  : make_float2(right[l], right[l + HN]);
+                    const float2 le = sp > 0 ? make_float2(X[(sp - 1) * NT + l], X[(sp - 1) * NT + l + HN])
+                                             : make_float2(left[l], left[l + HN]);
+                    const float2 t = __ffma2_rn(cadv, __ffma2_rn(m1, le, r), k1);
+                    float2 R = __ffma2_rn(here, t, nxt);
+                    R = __ffma2_rn(ncd, __fadd2_rn(r, le), R);
+                    a2 = __ffma2_rn(R, R, a2);
+                }
+            }
+            acc = a2.x + a2.y;
+        } else {
+            acc = 0.f;
+#pragma unroll
+            for (int sp = 0; sp < SPL; ++sp) {
+#pragma unroll
+                for (int l = 0; l < NT; ++l) {
+                    const float here = X[sp * NT + l];
+                    const float nxt = X[sp * NT + (l + 1) % NT];
+                    const float r = sp + 1 < SPL ? X[(sp + 1) * NT + l] : right[l];
+                    const float le = sp > 0 ? X[(sp - 1) * NT + l] : left[l];
+                    const float t = fmaf(cf.c_adv, r - le, cf.k1);
+                    float R = fmaf(here, t, nxt);
+                    R = fmaf(cf.neg_c_dif, r + le, R);
+                    acc = fmaf(R, R, acc);
+                }
             }
         }
         float S = warp_sum(acc) * cf.inv_2Dtau;
