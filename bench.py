@@ -478,31 +478,52 @@ def _time_plan(plan, lo, hi, seed, stream, reps=2):
 FP64_FMA_PEAK = 2 * 152 * 2.07e9   # FP64 lanes per SM and clock x SMs x clock
 
 
+def _oracle_rate(fn, samples, cores, what):
+    """The oracle as it stands, timed once on the host: samples/s."""
+    t0 = time.perf_counter()
+    fn()
+    wall = time.perf_counter() - t0
+    return {"value": samples / wall, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": what}
+
+
 def run_next_rows(bfi, dev, stream):
     """The rows built on top of the hot path: the N-sphere integrand of the
     line protocol, adaptive subdivision with the convergence test, and the
     transform and Gaussian samplers, each timed on the GPU."""
     import math
-    import time
     import torch
+    import oracle
     import workloads
+    from oracle import maps
     out = {}
     # N-sphere integrand (Listing 2's integrand; 2^30 samples over [-1,1]^3)
     bfi.nsphere(3, 1 << 20, 1)
     t0 = time.perf_counter()
     res, err, sd = bfi.nsphere(3, 1 << 30, 1)
     wall = time.perf_counter() - t0
+    ops = 4 * 3 + 4   # per sample, FP64: point d, |x|^2 2d, half sums d, sqrt, f^2, two sums (Philox is INT)
     out["nsphere"] = {"workload": "f = sqrt(1-|x|^2) over [-1,1]^3, 2^30 samples (FP64 points), synchronous call",
                       "samples_per_s_wall": (1 << 30) / wall, "ms_wall": wall * 1e3, "result": res, "abs_err": err,
-                      "exact": math.pi ** 2 / 4, "split_dim": sd}
+                      "exact": math.pi ** 2 / 4, "split_dim": sd,
+                      "roofline": {"bound": "fp64", "fp64_ops_per_sample": ops,
+                                   "frac_of_fp64_fma_peak": (1 << 30) * ops / wall / FP64_FMA_PEAK,
+                                   "note": "wall time of the synchronous call, allocation and copies included"},
+                      "cpu_baseline": _oracle_rate(lambda: oracle.nsphere(3, 1 << 21, 1), 1 << 21, 1,
+                                                   "oracle.nsphere, 2^21 samples over [-1,1]^3")}
     # adaptive subdivision: Listing 1's run, and the 10x2 lattice over its box
     conv = bfi.convergence(2.0, 0.003, 0.0, 0.0, 8, 1 << 16)
     t0 = time.perf_counter()
     res, err, st = bfi.adaptive_nsphere(3, 100_000, 1, conv)
     wall = time.perf_counter() - t0
+    from oracle.adaptive import Convergence, adaptive_nsphere as oracle_adaptive_nsphere
+    t0 = time.perf_counter()
+    oracle_adaptive_nsphere(3, 100_000, 1, Convergence(2.0, 0.003, 0.0, 0.0, 8, 1 << 16))
+    owall = time.perf_counter() - t0
     out["adaptive_nsphere"] = {"workload": "Listing 1: half the unit 4-ball over [-1,1]^3, n = 1e5, factor 2, "
                                            "rel_tol 0.003, max_depth 8", "ms_wall": wall * 1e3, "result": res,
-                               "abs_err": err, "exact": math.pi ** 2 / 4, "stats": st.as_dict()}
+                               "abs_err": err, "exact": math.pi ** 2 / 4, "stats": st.as_dict(),
+                               "cpu_baseline": {"value": owall * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+                                                "sample": "the same run through oracle.adaptive"}}
     ctx = bfi.Context(dev.index or 0)
     conv = bfi.convergence(2.0, 0.2, 0.0, 0.0, 10, 1 << 12)
     ctx.adaptive_integrate(bfi.lattice(10, 2), -5.0, 5.0, 1 << 16, 2, bfi.convergence(2.0, 0.2, 0.0, 0.0, 1, 4))
@@ -510,10 +531,18 @@ def run_next_rows(bfi, dev, stream):
     tot, st = ctx.adaptive_integrate(bfi.lattice(10, 2), -5.0, 5.0, 1 << 16, 2, conv)
     wall = time.perf_counter() - t0
     ctx.close()
+    from oracle.adaptive import adaptive_integrate as oracle_adaptive_integrate
+    t0 = time.perf_counter()
+    _, oout = oracle_adaptive_integrate(oracle.lattice(10, 2), -5.0, 5.0, 1 << 12, 2,
+                                        Convergence(2.0, 0.2, 0.0, 0.0, 4, 1 << 12))
+    owall = time.perf_counter() - t0
     out["adaptive_lattice"] = {"workload": "10x2 over [-5,5]^20, n = 2^16, factor 2, rel_tol 0.2, max_depth 10, "
                                            "at most 4096 subvolumes per round, FP64", "ms_wall": wall * 1e3,
                                "samples_per_s_wall": st.samples / wall, "logZ": float(tot[0]),
-                               "Z_err_rel": float(tot[1]), "stats": st.as_dict()}
+                               "Z_err_rel": float(tot[1]), "stats": st.as_dict(),
+                               "cpu_baseline": {"value": oout.stats["samples"] / owall, "unit": "samples/s",
+                                                "cores": 1, "kind": "oracle",
+                                                "sample": "oracle.adaptive on the same box, n = 2^12, depth 4"}}
     lat = bfi.lattice(10, 2)
     d, nr = 20, 6
     # transform sampler: [-1,1]^20 (all of R^20) bisected into 1024 subvolumes, 2^16 points each
@@ -532,7 +561,11 @@ def run_next_rows(bfi, dev, stream):
                                      "frac_of_fp64_fma_peak": n * ops / (ms * 1e-3) / FP64_FMA_PEAK,
                                      "note": "algebraic FP64 operations only; log, log1p and exp not counted"},
                         "logZ": float(t[0]), "Z_err_rel": float(t[1]),
-                        "C_err_over_C0_max": float(np.max(t[4 + nr:4 + 2 * nr]) / t[4])}
+                        "C_err_over_C0_max": float(np.max(t[4 + nr:4 + 2 * nr]) / t[4]),
+                        "cpu_baseline": _oracle_rate(
+                            lambda: maps.integrate_mapped(oracle.lattice(10, 2), lo_np[:4], hi_np[:4], 1 << 14, 2,
+                                                          kind=maps.TRANSFORM), 4 << 14, 1,
+                            "oracle.maps (numpy over the C action), 4 subvolumes x 2^14 points")}
     # Gaussian sampler on the paper's box: the regulated linear-limit proposal
     box_lo = torch.full((1, d), -5.0, dtype=torch.float64, device=dev)
     box_hi = torch.full((1, d), 5.0, dtype=torch.float64, device=dev)
@@ -548,8 +581,13 @@ def run_next_rows(bfi, dev, stream):
                       "frac_of_fp64_fma_peak": (1 << k) * ops / (ms * 1e-3) / FP64_FMA_PEAK,
                       "logZ": float(t[0]), "Z_err_rel": float(t[1]),
                       "C_err_over_C0_max": float(np.max(t[4 + nr:4 + 2 * nr]) / t[4])})
+    F_o = np.linalg.cholesky(maps.proposal_covariance(oracle.lattice(10, 2), 6.0))
     out["gaussian"] = {"workload": "10x2 over the box [-5,5]^20 as one volume, proposal N(0, (A + I/36)^-1) "
                                    "(linear limit, zero modes at sigma0 = 6), FP64", "runs": gauss,
+                       "cpu_baseline": _oracle_rate(
+                           lambda: maps.integrate_mapped(oracle.lattice(10, 2), -5 * np.ones(20), 5 * np.ones(20),
+                                                         1 << 16, 2, kind=maps.GAUSSIAN, factor=F_o), 1 << 16, 1,
+                           "oracle.maps (numpy over the C action), 2^16 points"),
                        "note": "the weights exp(-S)/q are heavy-tailed for the nonlinear action (ln Z grows "
                                "with the budget): the linear-limit proposal does not cover the zero-action "
                                "configurations away from the constant line"}
