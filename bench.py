@@ -336,7 +336,7 @@ def run_bfi(args):
     # ---- the serving workload: jobs arriving while others run ----
     serving = None
     if args.serving_seconds > 0 and world == 1:
-        serving = run_serving(bfi, args.serving_seconds)
+        serving = run_serving(bfi, args.serving_seconds, rate=args.serving_rate)
 
     # ---- end to end through the host-buffer C-ABI call ----
     e2e = None
@@ -684,6 +684,8 @@ def main():
     ap.add_argument("--skip-tte", action="store_true")
     ap.add_argument("--skip-next", action="store_true",
                     help="skip the N-sphere, adaptive and sampler measurements")
+    ap.add_argument("--serving-rate", type=float, default=200.0,
+                    help="arrivals per second of the serving workload (the workload is 200)")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="arrival window of the serving workload (the full workload is 60 s; 0 skips it)")
     ap.add_argument("--samples-log2", type=int, default=20,
