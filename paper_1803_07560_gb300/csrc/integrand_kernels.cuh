@@ -481,6 +481,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // count.  Needs count < 32 on entry (then count < 64 = kQueueCap on exit).
 __device__ __forceinline__ int enqueue(uint32_t *q, int count, bool cand, uint32_t k) {
     const unsigned mask = __ballot_sync(0xffffffffu, cand);
+    if (mask == 0u) return count;  // the common case: no candidate in the row (warp-uniform)
     if (cand) q[count + __popc(mask & lanemask_lt())] = k;
     __syncwarp();
     return count + __popc(mask);
