@@ -21,45 +21,54 @@
 
 namespace bfi {
 // ---------------------------------------------------------------------------
-// Per-subvolume FP64 merge of chunk records, in chunk order.  Also scales the
-// unscaled products Q_r = d P_r back to P_r and records log V_s.
+// Per-subvolume FP64 merge of chunk records, in chunk order.  One warp per
+// subvolume: lane t merges sums t, t + 32, ... (each in chunk order, so every
+// sum is the same as a sequential merge gives), and the reads of a chunk
+// record are coalesced.  Also scales the unscaled products Q_r = d P_r back to
+// P_r and records log V_s (the per-lane sums of log widths combined in a fixed
+// butterfly).
 // ---------------------------------------------------------------------------
 __global__ void merge_subvolumes(const MergeArgs a) {
-    const int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (s >= a.nsub) return;
+    const int64_t s = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= a.nsub) return;  // warp-uniform
     const int R = a.R, K = 2 + 3 * R, SL = 5 + 3 * R;
     double *slot = a.slots + s * SL;
     double n = 0.0, m = INFINITY;
-    for (int k = 0; k < K; ++k) slot[3 + k] = 0.0;
+    for (int k = lane; k < K; k += 32) slot[3 + k] = 0.0;
     for (int64_t c = a.chunk_off[s]; c < a.chunk_off[s + 1]; ++c) {
         const double *p = a.partials + c * (K + 2);
         n += p[0];
         const double mb = p[1];
         if (mb == INFINITY) continue;  // no evaluated samples in the chunk
         if (mb == m) {
-            for (int k = 0; k < K; ++k) slot[3 + k] = __dadd_rn(slot[3 + k], p[2 + k]);
+            for (int k = lane; k < K; k += 32) slot[3 + k] = __dadd_rn(slot[3 + k], p[2 + k]);
             continue;
         }
         const double mn = fmin(m, mb);
         const double fa = (m == INFINITY) ? 0.0 : exp(mn - m);
         const double fb = exp(mn - mb);
-        for (int k = 0; k < K; ++k) {
+        for (int k = lane; k < K; k += 32) {
             const bool sq = (k == 1) || (k >= 2 + R);
             slot[3 + k] = __dadd_rn(__dmul_rn(slot[3 + k], sq ? fa * fa : fa), __dmul_rn(p[2 + k], sq ? fb * fb : fb));
         }
         m = mn;
     }
     const double inv_d = 1.0 / static_cast<double>(a.d);
-    for (int r = 0; r < R; ++r) {
+    for (int r = lane; r < R; r += 32) {
         slot[5 + r] *= inv_d;
         slot[5 + R + r] *= inv_d;
         slot[5 + 2 * R + r] *= inv_d * inv_d;
     }
     double log_vol = 0.0;
-    for (int j = 0; j < a.d; ++j) log_vol += log(a.hi[s * a.d + j] - a.lo[s * a.d + j]);
-    slot[0] = n;
-    slot[1] = m;
-    slot[2] = a.log_norm_set ? a.log_norm : log_vol;
+    for (int j = lane; j < a.d; j += 32) log_vol += log(a.hi[s * a.d + j] - a.lo[s * a.d + j]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) log_vol += __shfl_xor_sync(0xffffffffu, log_vol, off);
+    if (lane == 0) {
+        slot[0] = n;
+        slot[1] = m;
+        slot[2] = a.log_norm_set ? a.log_norm : log_vol;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -71,28 +80,30 @@ __global__ void merge_subvolumes(const MergeArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kTotThreads = 256;
 
+// Block-wide sum / max: an XOR butterfly in each warp, then every thread adds
+// the kTotThreads/32 warp results in warp order (fixed order: reproducible).
 __device__ double block_sum(double v, double *sh) {
     const int t = threadIdx.x;
-    sh[t] = v;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((t & 31) == 0) sh[t >> 5] = v;
     __syncthreads();
-    for (int off = kTotThreads / 2; off > 0; off >>= 1) {
-        if (t < off) sh[t] = sh[t] + sh[t + off];
-        __syncthreads();
-    }
-    const double r = sh[0];
+    double r = 0.0;
+#pragma unroll
+    for (int w = 0; w < kTotThreads / 32; ++w) r += sh[w];
     __syncthreads();
     return r;
 }
 
 __device__ double block_max(double v, double *sh) {
     const int t = threadIdx.x;
-    sh[t] = v;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((t & 31) == 0) sh[t >> 5] = v;
     __syncthreads();
-    for (int off = kTotThreads / 2; off > 0; off >>= 1) {
-        if (t < off) sh[t] = fmax(sh[t], sh[t + off]);
-        __syncthreads();
-    }
-    const double r = sh[0];
+    double r = sh[0];
+#pragma unroll
+    for (int w = 1; w < kTotThreads / 32; ++w) r = fmax(r, sh[w]);
     __syncthreads();
     return r;
 }
@@ -197,8 +208,8 @@ const ShapeKernels *find_shape(int nx, int nt) {
 }
 
 cudaError_t launch_merges(const MergeArgs &m, const TotalsArgs &t, cudaStream_t st) {
-    const int threads = 128;
-    const int64_t blocks = (m.nsub + threads - 1) / threads;
+    const int threads = 256;  // 8 subvolumes (one warp each) per block
+    const int64_t blocks = (m.nsub * 32 + threads - 1) / threads;
     merge_subvolumes<<<static_cast<unsigned>(blocks), threads, 0, st>>>(m);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
