@@ -214,11 +214,11 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
     const size_t smp_bytes = sizeof(uint64_t) * nsub;
     const size_t par_bytes = sizeof(double) * static_cast<size_t>(std::max<int64_t>(p->nchunks, 1)) * (p->K + 2);
     const size_t hint_bytes = sizeof(float) * nsub;
-    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + sizeof(unsigned long long) + sizeof(double) * nsub;
+    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + sizeof(unsigned long long) + sizeof(double) * 2 * nsub;
     if (cudaMalloc(&p->d_chunk_off, off_bytes) != cudaSuccess || cudaMalloc(&p->d_samples, smp_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_partials, par_bytes) != cudaSuccess || cudaMalloc(&p->d_hint, hint_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_stats, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&p->d_fbuf, sizeof(double) * nsub) != cudaSuccess) {
+        cudaMalloc(&p->d_fbuf, sizeof(double) * 2 * nsub) != cudaSuccess) {
         cudaGetLastError();
         bfi_plan_destroy(p);
         return fail(BFI_E_NOMEM, "device allocation of %zu bytes failed", p->scratch_bytes);
@@ -632,7 +632,9 @@ bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double 
         used += 1.0;
         if (q[3] > 0.0) L = std::fmax(L, q[2] - std::log(q[0]) - q[1]);
     }
-    std::vector<double> f(static_cast<size_t>(nsub), 0.0);
+    // f_s and g_s = f_s^2 / (n_s - 1), the factor of every variance term (the
+    // same arithmetic as the device merge)
+    std::vector<double> f(static_cast<size_t>(nsub), 0.0), g(static_cast<size_t>(nsub), 0.0);
     double Z = 0.0, VZ = 0.0;
     for (int64_t s = 0; s < nsub; ++s) {
         const double *q = slots + s * SL;
@@ -644,7 +646,8 @@ bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double 
             inf_err = true;
             continue;
         }
-        VZ += f[s] * f[s] * (n * q[4] - q[3] * q[3]) / (n - 1.0);
+        g[s] = f[s] * f[s] / (n - 1.0);
+        VZ += g[s] * (n * q[4] - q[3] * q[3]);
     }
     totals[0] = L + std::log(Z);
     totals[1] = inf_err ? INFINITY : std::sqrt(VZ > 0.0 ? VZ : 0.0) / Z;
@@ -657,13 +660,13 @@ bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double 
         const double C = N / Z;
         double V = 0.0;
         for (int64_t s = 0; s < nsub; ++s) {
+            if (g[s] == 0.0) continue;
             const double *q = slots + s * SL;
-            if (!usable(q) || q[0] < 2.0) continue;
             const double n = q[0];
-            const double vN = (n * q[5 + 2 * R + r] - q[5 + r] * q[5 + r]) / (n - 1.0);
-            const double cov = (n * q[5 + R + r] - q[3] * q[5 + r]) / (n - 1.0);
-            const double vZ = (n * q[4] - q[3] * q[3]) / (n - 1.0);
-            V += f[s] * f[s] * (vN - 2.0 * C * cov + C * C * vZ);
+            const double vN = n * q[5 + 2 * R + r] - q[5 + r] * q[5 + r];
+            const double cov = n * q[5 + R + r] - q[3] * q[5 + r];
+            const double vZ = n * q[4] - q[3] * q[3];
+            V += g[s] * (vN - 2.0 * C * cov + C * C * vZ);
         }
         totals[4 + r] = C;
         totals[4 + R + r] = inf_err ? INFINITY : std::sqrt(V > 0.0 ? V : 0.0) / Z;

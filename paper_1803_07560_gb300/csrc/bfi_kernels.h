@@ -50,7 +50,7 @@ struct MergeArgs {
 struct TotalsArgs {
     const double *slots;
     double *totals;
-    double *f_buf;             // [nsub] scratch: per-subvolume scale factors
+    double *f_buf;             // [2 nsub] scratch: per-subvolume scale factors f_s, then f_s^2 / (n_s - 1)
     int64_t nsub;
     int32_t R;
 };

@@ -126,21 +126,26 @@ __global__ void __launch_bounds__(kTotThreads) merge_totals(const TotalsArgs a) 
     n_tot = block_sum(n_tot, sh);
     used = block_sum(used, sh);
 
-    // f_s = exp(ls_s - L) once per subvolume (0 for subvolumes without weight)
+    // f_s = exp(ls_s - L) once per subvolume (0 for subvolumes without weight),
+    // and g_s = f_s^2 / (n_s - 1), the factor of every variance term (one
+    // division per subvolume instead of one per term)
     double z = 0.0, vz = 0.0, bad = 0.0;
     for (int64_t s = t; s < a.nsub; s += kTotThreads) {
         const double *q = a.slots + s * SL;
-        double f = 0.0;
+        double f = 0.0, gs = 0.0;
         if (q[0] > 0.0 && q[3] > 0.0) {
             const double n = q[0];
             f = exp(q[2] - log(n) - q[1] - L);
             z += f * q[3];
-            if (n < 2.0)
+            if (n < 2.0) {
                 bad = 1.0;
-            else
-                vz += f * f * (n * q[4] - q[3] * q[3]) / (n - 1.0);
+            } else {
+                gs = f * f / (n - 1.0);
+                vz += gs * (n * q[4] - q[3] * q[3]);
+            }
         }
         f_buf[s] = f;
+        f_buf[a.nsub + s] = gs;
     }
     const double Z = block_sum(z, sh);
     const double VZ = block_sum(vz, sh);
@@ -157,14 +162,14 @@ __global__ void __launch_bounds__(kTotThreads) merge_totals(const TotalsArgs a) 
         const double C = block_sum(nr, sh) / Z;
         double var = 0.0;
         for (int64_t s = t; s < a.nsub; s += kTotThreads) {
+            const double gs = f_buf[a.nsub + s];
+            if (gs == 0.0) continue;
             const double *q = a.slots + s * SL;
-            const double f = f_buf[s];
             const double n = q[0];
-            if (f == 0.0 || n < 2.0) continue;
-            const double vN = (n * q[5 + 2 * R + r] - q[5 + r] * q[5 + r]) / (n - 1.0);
-            const double cov = (n * q[5 + R + r] - q[3] * q[5 + r]) / (n - 1.0);
-            const double vZ = (n * q[4] - q[3] * q[3]) / (n - 1.0);
-            var += f * f * (vN - 2.0 * C * cov + C * C * vZ);
+            const double vN = n * q[5 + 2 * R + r] - q[5 + r] * q[5 + r];
+            const double cov = n * q[5 + R + r] - q[3] * q[5 + r];
+            const double vZ = n * q[4] - q[3] * q[3];
+            var += gs * (vN - 2.0 * C * cov + C * C * vZ);
         }
         const double V = block_sum(var, sh);
         if (t == 0) {

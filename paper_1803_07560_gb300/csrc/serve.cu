@@ -85,7 +85,7 @@ Layout layout_for(int64_t nsub, int64_t nchunks, int d, int K, int SL, int TL) {
     L.smp = o;   o += round_up(sizeof(uint64_t) * nsub);
     L.hint = o;  o += round_up(sizeof(float) * nsub);
     L.stats = o; o += round_up(sizeof(unsigned long long));
-    L.fbuf = o;  o += round_up(sizeof(double) * nsub);
+    L.fbuf = o;  o += round_up(sizeof(double) * 2 * nsub);
     L.part = o;  o += round_up(sizeof(double) * static_cast<size_t>(nchunks > 0 ? nchunks : 1) * (K + 2));
     L.lo = o;    o += round_up(sizeof(double) * nsub * d);
     L.hi = o;    o += round_up(sizeof(double) * nsub * d);

@@ -122,7 +122,7 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
     const size_t smp_bytes = round_up(sizeof(uint64_t) * nsub);
     const size_t hint_bytes = round_up(sizeof(float) * nsub);
     const size_t stat_bytes = round_up(sizeof(unsigned long long));
-    const size_t fbuf_bytes = round_up(sizeof(double) * nsub);
+    const size_t fbuf_bytes = round_up(sizeof(double) * 2 * nsub);
     const size_t par_bytes = round_up(sizeof(double) * static_cast<size_t>(nchunks > 0 ? nchunks : 1) * (K + 2));
     const size_t need = off_bytes + smp_bytes + hint_bytes + stat_bytes + fbuf_bytes + par_bytes;
     if (need > kStaticScratchBytes) {

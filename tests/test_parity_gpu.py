@@ -215,7 +215,9 @@ def test_device_merge_equals_host_merge_and_is_deterministic(bfi, dev):
     h_t = bfi.merge_host(10, g_s)
     R = 6
     np.testing.assert_allclose(h_t[:4 + R], g_t[:4 + R], rtol=1e-13, atol=1e-13 * abs(g_t[4]))
-    np.testing.assert_allclose(h_t[4 + R:], g_t[4 + R:], rtol=1e-9, atol=1e-9 * g_t[4])
+    # the stated C(r) errors are square roots of variances that cancel when one
+    # sample dominates: summed in different orders they agree to ~sqrt(eps) C(0)
+    np.testing.assert_allclose(h_t[4 + R:], g_t[4 + R:], rtol=1e-9, atol=FP64_ERR_ATOL * g_t[4])
 
 
 def test_host_buffer_path_equals_device_path(bfi, dev):
