@@ -46,7 +46,9 @@ __host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
 
 // Rounds r0..9 of Philox4x32-10 on the state c.
 __host__ __device__ __forceinline__ uint4 philox_rounds(uint4 c, const RoundKeys &rk, int r0) {
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
     for (int r = r0; r < 10; ++r) {
         const uint32_t lo0 = kPhiloxM0 * c.x;
         const uint32_t hi0 = mulhi32(kPhiloxM0, c.x);

@@ -233,7 +233,7 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
     }
     if (ok) {
         const bfi::MergeArgs mg{lo, hi, static_cast<const int64_t *>(at(p.L.off)), static_cast<const double *>(at(p.L.part)),
-                                slots, p.nsub, r.R, r.d};
+                                slots, p.nsub, r.R, r.d, 0, 0.0};
         const bfi::TotalsArgs tg{slots, totals, static_cast<double *>(at(p.L.fbuf)), p.nsub, r.R};
         ok = cuda(bfi::launch_merges(mg, tg, st), "merge launch") &&
              cuda(cudaMemcpyAsync(sl.stage, slots, sizeof(double) * p.nsub * r.SL, cudaMemcpyDeviceToHost, st), "copy") &&

@@ -170,7 +170,7 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
         if ((e = shape->integrand[precision](a, lp, seed, job_id, static_cast<int>(grid), cs)) != cudaSuccess)
             return cuda_fail("integrand launch", e);
     }
-    const bfi::MergeArgs m{lo, hi, d_off, d_partials, slots, nsub, R, d};
+    const bfi::MergeArgs m{lo, hi, d_off, d_partials, slots, nsub, R, d, 0, 0.0};
     const bfi::TotalsArgs t{slots, totals, d_fbuf, nsub, R};
     if ((e = bfi::launch_merges(m, t, cs)) != cudaSuccess) return cuda_fail("merge launch", e);
     return BFI_OK;
