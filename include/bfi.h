@@ -46,13 +46,16 @@
  *    subvolumes; the error of C(r) is the first-order (delta-method) error of
  *    a ratio of sums.  A subvolume with exactly one sample makes the errors
  *    +inf; subvolumes with no samples are skipped.
- *  - Precision: BFI_FP64 evaluates everything in double; m_s is then the
- *    smallest action of the subvolume.  BFI_FP32 evaluates the points, the
- *    action, the products and the weights in float, accumulates per thread in
- *    Kahan-compensated float, and merges in double.  Its shift m_s starts at
- *    the smallest FP32 action among the subvolume's first n_s/32 samples
- *    (256 to 4096) and
- *    moves down only when a sample beats it by more than 16.  Samples whose
+ *  - Precision: BFI_FP64 evaluates in double every sample that can carry
+ *    weight (the FP32 screen under Negligible weights decides which):
+ *    its FP64 point, action, products and weight, accumulated in double.
+ *    BFI_FP32 evaluates the points, the action, the products and the weights
+ *    in float, accumulates per thread in Kahan-compensated float, and merges
+ *    in double.  In both the shift m_s starts at the smallest FP32 action
+ *    among the subvolume's first n_s/32 samples (256 to 4096) and moves down
+ *    only when a sample beats it by more than 16, so it lies within
+ *    [min S - 1e-3, min S + 16] (the records do not depend on its exact
+ *    value beyond rounding).  In BFI_FP32, samples whose
  *    FP32 action lies within 28 of the smallest action seen get the action
  *    recomputed in compensated FP32 (pairs of floats carrying the rounding
  *    error, about 2^-44 relative); every other sample has a weight below
@@ -72,6 +75,14 @@
  *    reproducible.
  *  - Errors: every call returns a bfi_status; bfi_last_error() gives a
  *    message for the calling thread.  No call aborts the process.
+ *
+ * Entry points, in the order below: sizes and errors; plans (the
+ * device-resident path: create, execute on a stream, grid, timing, stats,
+ * samplers); the allocation-free one-call path; batches of jobs in one CUDA
+ * graph and the grid autotuner; the serving loop (submit, poll, wait,
+ * cancel); contexts and the host-buffer one-call path; the N-sphere test
+ * integrand and adaptive subdivision of Sec. 3; the host merge; single steps
+ * (points, action and products) for step-by-step checks.
  *  - Pointers: "host" pointers are ordinary CPU memory, "device" pointers
  *    are CUDA device memory of the plan's or context's device.  The caller
  *    owns every array it passes and may free it once the call returns (for
