@@ -95,7 +95,7 @@ def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2):
             "traffic": None, "kernel_ms": kern_ms, "samples": n, "evaluated": n_eval,
             "issue_frac": w_issue / t / ISSUE_PEAK_OPS, "fp64_frac": w_dp / t / FP64_PEAK_OPS,
             "screen_ops_per_sample": screen_ops(nx, nt),
-            "peak_source": "unit counts x 2070 MHz (DESIGN.md)"}
+            "peak_source": "unit counts x 2070 MHz: 128 FP32/INT and 2 FP64 lanes per SM, 152 SMs"}
 
 
 def rank_info():
@@ -331,7 +331,8 @@ def run_bfi(args):
     # ---- the rows built on the hot path: line protocol, adaptive, samplers ----
     next_rows = None
     if not args.skip_next and world == 1:
-        next_rows = run_next_rows(bfi, dev, stream)
+        next_rows = run_next_rows(bfi, dev, stream, rows=args.next_rows.split(","),
+                                  transform_log2=args.transform_log2)
 
     # ---- the serving workload: jobs arriving while others run ----
     serving = None
@@ -475,7 +476,11 @@ def _time_plan(plan, lo, hi, seed, stream, reps=2):
     return best, tot.cpu().numpy(), n_eval
 
 
-FP64_FMA_PEAK = 2 * 152 * 2.07e9   # FP64 lanes per SM and clock x SMs x clock (DESIGN.md)
+FP64_FMA_PEAK = 2 * 152 * 2.07e9   # FP64 lanes per SM and clock x SMs x clock
+# FP64 add, multiply and FMA per sample of the thread-per-sample range-map kernel at 10x2 (d = 20, R = 6):
+# 13 d for the map (point, 1 - y^2, two Newton steps, v, J and the running product), 6 d + 3 for S_eff,
+# 5 d + d/2 + 1 for the products Q_r, 3 + 6 R for the weight's sums
+TRANSFORM_FP64_OPS_10x2 = 13 * 20 + (6 * 20 + 3) + (5 * 20 + 10 + 1) + (3 + 6 * 6)
 
 
 def _oracle_rate(fn, samples, cores, what):
@@ -486,15 +491,30 @@ def _oracle_rate(fn, samples, cores, what):
     return {"value": samples / wall, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": what}
 
 
-def run_next_rows(bfi, dev, stream):
+NEXT_ROWS = ("nsphere", "adaptive", "transform", "gaussian")
+
+
+def run_next_rows(bfi, dev, stream, rows=NEXT_ROWS, transform_log2=18):
     """The rows built on top of the hot path: the N-sphere integrand of the
     line protocol, adaptive subdivision with the convergence test, and the
-    transform and Gaussian samplers, each timed on the GPU."""
+    transform and Gaussian samplers, each timed on the GPU ('rows' picks
+    some; 'transform_log2' sets the transform's points per subvolume)."""
+    out = {}
+    lat, d, nr = bfi.lattice(10, 2), 20, 6
+    if "nsphere" in rows:
+        out.update(_next_nsphere(bfi))
+    if "adaptive" in rows:
+        out.update(_next_adaptive(bfi, dev))
+    if "transform" in rows:
+        out.update(_next_transform(bfi, dev, stream, lat, d, nr, transform_log2))
+    if "gaussian" in rows:
+        out.update(_next_gaussian(bfi, dev, stream, lat, d, nr))
+    return out
+
+
+def _next_nsphere(bfi):
     import math
-    import torch
     import oracle
-    import workloads
-    from oracle import maps
     out = {}
     # N-sphere integrand (Listing 2's integrand; 2^30 samples over [-1,1]^3)
     bfi.nsphere(3, 1 << 20, 1)
@@ -510,6 +530,13 @@ def run_next_rows(bfi, dev, stream):
                                    "note": "wall time of the synchronous call, allocation and copies included"},
                       "cpu_baseline": _oracle_rate(lambda: oracle.nsphere(3, 1 << 21, 1), 1 << 21, 1,
                                                    "oracle.nsphere, 2^21 samples over [-1,1]^3")}
+    return out
+
+
+def _next_adaptive(bfi, dev):
+    import math
+    import oracle
+    out = {}
     # adaptive subdivision: Listing 1's run, and the 10x2 lattice over its box
     conv = bfi.convergence(2.0, 0.003, 0.0, 0.0, 8, 1 << 16)
     t0 = time.perf_counter()
@@ -543,29 +570,46 @@ def run_next_rows(bfi, dev, stream):
                                "cpu_baseline": {"value": oout.stats["samples"] / owall, "unit": "samples/s",
                                                 "cores": 1, "kind": "oracle",
                                                 "sample": "oracle.adaptive on the same box, n = 2^12, depth 4"}}
-    lat = bfi.lattice(10, 2)
-    d, nr = 20, 6
-    # transform sampler: [-1,1]^20 (all of R^20) bisected into 1024 subvolumes, 2^16 points each
+    return out
+
+
+def _next_transform(bfi, dev, stream, lat, d, nr, log2n):
+    import torch
+    import oracle
+    import workloads
+    from oracle import maps
+    out = {}
+    # transform sampler: [-1,1]^20 (all of R^20) bisected into 1024 subvolumes, 2^log2n points each
     lo_np, hi_np = workloads.bisected_boxes(d, 10, half=1.0)
     lo, hi = torch.tensor(lo_np, device=dev), torch.tensor(hi_np, device=dev)
-    samples = np.full(1024, 1 << 16, dtype=np.uint64)
+    samples = np.full(1024, 1 << log2n, dtype=np.uint64)
     plan = bfi.Plan(lat, samples, bfi.FP64)
     plan.set_sampler(bfi.SAMPLE_TRANSFORM)
     ms, t, n_eval = _time_plan(plan, lo, hi, 2, stream)
     plan.close()
     n = int(samples.sum())
-    ops = (6 + 8 + nr) * d   # per sample: range map, action, products (logarithms not counted)
-    out["transform"] = {"workload": "10x2, v = y/(1-y^2) over [-1,1]^20 bisected into 1024 subvolumes x 2^16 "
-                                    "points, FP64, mass2 = 0", "ms": ms, "samples_per_s": n / (ms * 1e-3),
+    ops = TRANSFORM_FP64_OPS_10x2
+    out["transform"] = {"workload": f"10x2, v = y/(1-y^2) over [-1,1]^20 bisected into 1024 subvolumes x "
+                                    f"2^{log2n} points, FP64, mass2 = 0", "ms": ms, "samples_per_s": n / (ms * 1e-3),
                         "roofline": {"bound": "fp64", "fp64_ops_per_sample": ops,
                                      "frac_of_fp64_fma_peak": n * ops / (ms * 1e-3) / FP64_FMA_PEAK,
-                                     "note": "algebraic FP64 operations only; log, log1p and exp not counted"},
+                                     "note": "FP64 add, multiply and FMA of the definition (13 per coordinate "
+                                             "for the map with its Newton reciprocal, 6 per residual, the "
+                                             "products and sums); the one log and exp per sample not counted"},
                         "logZ": float(t[0]), "Z_err_rel": float(t[1]),
                         "C_err_over_C0_max": float(np.max(t[4 + nr:4 + 2 * nr]) / t[4]),
                         "cpu_baseline": _oracle_rate(
                             lambda: maps.integrate_mapped(oracle.lattice(10, 2), lo_np[:4], hi_np[:4], 1 << 14, 2,
                                                           kind=maps.TRANSFORM), 4 << 14, 1,
                             "oracle.maps (numpy over the C action), 4 subvolumes x 2^14 points")}
+    return out
+
+
+def _next_gaussian(bfi, dev, stream, lat, d, nr):
+    import torch
+    import oracle
+    from oracle import maps
+    out = {}
     # Gaussian sampler on the paper's box: the regulated linear-limit proposal
     box_lo = torch.full((1, d), -5.0, dtype=torch.float64, device=dev)
     box_hi = torch.full((1, d), 5.0, dtype=torch.float64, device=dev)
@@ -684,6 +728,10 @@ def main():
     ap.add_argument("--skip-tte", action="store_true")
     ap.add_argument("--skip-next", action="store_true",
                     help="skip the N-sphere, adaptive and sampler measurements")
+    ap.add_argument("--next-rows", default=",".join(NEXT_ROWS),
+                    help="which of those rows to run (comma list of " + ", ".join(NEXT_ROWS) + ")")
+    ap.add_argument("--transform-log2", type=int, default=18,
+                    help="points per subvolume of the transform-sampler row (2^18; smaller for profiling)")
     ap.add_argument("--serving-rate", type=float, default=200.0,
                     help="arrivals per second of the serving workload (the workload is 200)")
     ap.add_argument("--serving-seconds", type=float, default=10.0,

@@ -265,6 +265,8 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
                              plan->chunk_samples, plan->skip_window};
         if (plan->sampler == BFI_SAMPLE_BOX) {
             BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
+        } else if (plan->sampler == BFI_SAMPLE_TRANSFORM && plan->shape->transform) {
+            BFI_CUDA(plan->shape->transform(a, plan->lat, seed, job_id, plan->grid, st));
         } else {
             const bfi::MapArgs mp{plan->sampler, plan->d_map, plan->d_map ? plan->d_map + plan->d : nullptr};
             BFI_CUDA(bfi::launch_mapped(a, plan->lat, mp, seed, job_id, plan->grid, st));
@@ -333,9 +335,13 @@ bfi_status bfi_plan_set_sampler(bfi_plan *plan, const bfi_sampler *sampler) {
     DeviceGuard g(plan->device);
     if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device: %s", cudaGetErrorString(g.err));
     int per_sm = 0;
-    cudaError_t e = kind == BFI_SAMPLE_BOX
-                        ? plan->shape->occupancy[plan->precision](plan->lat.nx, plan->lat.nt, &per_sm)
-                        : bfi::occupancy_mapped(plan->lat.nx, plan->lat.nt, kind, &per_sm);
+    cudaError_t e;
+    if (kind == BFI_SAMPLE_BOX)
+        e = plan->shape->occupancy[plan->precision](plan->lat.nx, plan->lat.nt, &per_sm);
+    else if (kind == BFI_SAMPLE_TRANSFORM && plan->shape->transform_occupancy)
+        e = plan->shape->transform_occupancy(plan->lat.nx, plan->lat.nt, &per_sm);
+    else
+        e = bfi::occupancy_mapped(plan->lat.nx, plan->lat.nt, kind, &per_sm);
     if (e != cudaSuccess) return fail(BFI_E_CUDA, "occupancy query failed: %s", cudaGetErrorString(e));
     if (kind == BFI_SAMPLE_GAUSSIAN) {
         if (!plan->d_map && cudaMalloc(&plan->d_map, sizeof(double) * (d + d * d)) != cudaSuccess) {

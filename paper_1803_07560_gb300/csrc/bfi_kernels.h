@@ -82,6 +82,8 @@ struct ShapeKernels {
     IntegrandLauncher integrand[2];
     OccupancyQuery occupancy[2];
     EvalLauncher eval;   // mode 0 = FP64, 1 = FP32, 2 = FP32 compensated action
+    IntegrandLauncher transform;      // the range map in FP64, thread per sample (null: generic_mapped)
+    OccupancyQuery transform_occupancy;
 };
 
 // Compiled shape tables (shapes_small.cu, shapes_config.cu) and the generic

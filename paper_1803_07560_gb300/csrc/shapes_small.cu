@@ -1,6 +1,7 @@
-// shapes_small.cu -- instantiates the thread-per-sample integrand kernels for the
+// shapes_small.cu -- instantiates the thread-per-sample integrand and range-map kernels for the
 // lattice shapes listed in BFI_SHAPES_SMALL (bfi_kernels.h).
 #include "integrand_kernels.cuh"
+#include "mapped_kernels.cuh"
 
 namespace bfi {
 
@@ -8,7 +9,7 @@ namespace bfi {
     {NX, NT, 0,                                                                   \
      {launch_integrand<NX, NT, double>, launch_integrand<NX, NT, float>},         \
      {occupancy_integrand<NX, NT, double>, occupancy_integrand<NX, NT, float>},   \
-     launch_eval<NX, NT>},
+     launch_eval<NX, NT>, launch_transform<NX, NT>, occupancy_transform<NX, NT>},
 
 static const ShapeKernels kTable[] = {BFI_SHAPES_SMALL(BFI_SHAPE_ENTRY)};
 

@@ -54,9 +54,12 @@ def _run_plan(bfi, lat, lo, hi, samples, seed, sub_id, kind, mean=None, factor=N
     return out
 
 
+# (5, 3) and (7, 2) run on the warp-per-sample kernel; the other shapes have a
+# compiled thread-per-sample kernel (both translation units of shapes)
 @pytest.mark.gpu
 @pytest.mark.parametrize("nx,nt,mass2,nonlinear", [(4, 2, 0.0, 1.0), (10, 2, 0.0, 1.0), (5, 3, 0.3, 1.0),
-                                                   (3, 1, 1.0, 0.0), (2, 2, 0.0, 1.0)])
+                                                   (3, 1, 1.0, 0.0), (2, 2, 0.0, 1.0), (7, 2, 0.0, 1.0),
+                                                   (6, 4, 0.0, 1.0), (16, 2, 0.2, 1.0), (16, 4, 0.0, 1.0)])
 def test_transform_matches_oracle(bfi, nx, nt, mass2, nonlinear):
     d = nx * nt
     lo, hi = _boxes_in_unit_cube(d, 3, seed=nx * 10 + nt)
@@ -69,6 +72,28 @@ def test_transform_matches_oracle(bfi, nx, nt, mass2, nonlinear):
     R = nx // 2 + 1
     assert_slots_close(g_s, o_s, R, FP64_RTOL, 1e-9)
     assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9, m=np.abs(o_s[:, 1]).max())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,nt", [(10, 2), (5, 3)])
+def test_transform_ragged_counts_and_edge_boxes(bfi, nx, nt):
+    """Sample counts of 0, 1, one short of a CTA row, a row and a few chunks,
+    and boxes near the ends of the range: a slab in every coordinate near
+    y = 1 (v between 128 and 256) and one near y = -1, the whole range, and a
+    box of width 2^-20 around 0.  (Slabs closer to +-1 put S far beyond 1e9,
+    where two FP64 evaluations of exp(-S) share no digits.)"""
+    d = nx * nt
+    lo = np.stack([np.full(d, -1.0), np.full(d, 1.0 - 2.0 ** -8), np.full(d, -1.0 + 2.0 ** -9), np.full(d, -1.0),
+                   np.full(d, -2.0 ** -21), np.full(d, -0.5), np.full(d, -1.0)])
+    hi = np.stack([np.full(d, 1.0), np.full(d, 1.0 - 2.0 ** -9), np.full(d, -1.0 + 2.0 ** -8), np.full(d, 1.0),
+                   np.full(d, 2.0 ** -21), np.full(d, 0.25), np.full(d, 1.0)])
+    samples = np.array([0, 4097, 3001, 1, 255, 256, 70_001], dtype=np.uint64)
+    g_s, g_t = _run_plan(bfi, bfi.lattice(nx, nt), lo, hi, samples, 11, None, bfi.SAMPLE_TRANSFORM)
+    o_s, o_t = integrate_mapped(oracle.lattice(nx, nt), lo, hi, samples, 11, kind=TRANSFORM)
+    R = nx // 2 + 1
+    assert g_s[0, 0] == 0 and g_s[0, 1] == math.inf and np.all(g_s[0, 3:] == 0.0)
+    assert_slots_close(g_s, o_s, R, FP64_RTOL, 1e-9)
+    assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9, m=np.abs(o_s[1:, 1]).max())
 
 
 @pytest.mark.gpu
