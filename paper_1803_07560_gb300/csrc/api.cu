@@ -124,6 +124,7 @@ struct bfi_plan {
     int32_t sampler = BFI_SAMPLE_BOX;
     double *d_map = nullptr;  // Gaussian sampler: mean [d], then factor [d * d]
     double log_norm = 0.0;    // Gaussian sampler: (d/2) ln 2 pi + ln |det F|
+    bool map_upper = false;   // Gaussian sampler: F is upper triangular
 };
 
 extern "C" {
@@ -269,7 +270,10 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
             BFI_CUDA(plan->shape->transform(a, plan->lat, seed, job_id, plan->grid, st));
         } else {
             const bfi::MapArgs mp{plan->sampler, plan->d_map, plan->d_map ? plan->d_map + plan->d : nullptr};
-            BFI_CUDA(bfi::launch_mapped(a, plan->lat, mp, seed, job_id, plan->grid, st));
+            if (plan->sampler == BFI_SAMPLE_GAUSSIAN && plan->shape->gaussian)
+                BFI_CUDA(plan->shape->gaussian(a, plan->lat, mp, plan->map_upper, seed, job_id, plan->grid, st));
+            else
+                BFI_CUDA(bfi::launch_mapped(a, plan->lat, mp, seed, job_id, plan->grid, st));
         }
     }
     if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[1], st));
@@ -340,6 +344,8 @@ bfi_status bfi_plan_set_sampler(bfi_plan *plan, const bfi_sampler *sampler) {
         e = plan->shape->occupancy[plan->precision](plan->lat.nx, plan->lat.nt, &per_sm);
     else if (kind == BFI_SAMPLE_TRANSFORM && plan->shape->transform_occupancy)
         e = plan->shape->transform_occupancy(plan->lat.nx, plan->lat.nt, &per_sm);
+    else if (kind == BFI_SAMPLE_GAUSSIAN && plan->shape->gaussian_occupancy)
+        e = plan->shape->gaussian_occupancy(plan->lat.nx, plan->lat.nt, &per_sm);
     else
         e = bfi::occupancy_mapped(plan->lat.nx, plan->lat.nt, kind, &per_sm);
     if (e != cudaSuccess) return fail(BFI_E_CUDA, "occupancy query failed: %s", cudaGetErrorString(e));
@@ -356,6 +362,17 @@ bfi_status bfi_plan_set_sampler(bfi_plan *plan, const bfi_sampler *sampler) {
     }
     plan->sampler = kind;
     plan->log_norm = log_norm;
+    plan->map_upper = false;
+    if (kind == BFI_SAMPLE_GAUSSIAN) {
+        bool upper = true;
+        for (int r = 1; r < d && upper; ++r)
+            for (int j = 0; j < r; ++j)
+                if (sampler->factor[r * d + j] != 0.0) {
+                    upper = false;
+                    break;
+                }
+        plan->map_upper = upper;
+    }
     plan->per_sm_max = per_sm > 0 ? per_sm : 1;
     plan->per_sm = plan->per_sm_max;
     const int64_t resident = static_cast<int64_t>(plan->sms) * plan->per_sm_max;

@@ -72,6 +72,10 @@ struct EvalArgs {
 
 using IntegrandLauncher = cudaError_t (*)(const IntegrandArgs &, const LatticeParams &, uint32_t, uint32_t, int,
                                           cudaStream_t);
+struct MapArgs;
+// Gaussian sampler: map arguments and whether the factor is upper triangular
+using GaussLauncher = cudaError_t (*)(const IntegrandArgs &, const LatticeParams &, const MapArgs &, bool, uint32_t,
+                                      uint32_t, int, cudaStream_t);
 using OccupancyQuery = cudaError_t (*)(int nx, int nt, int *blocks_per_sm);
 using EvalLauncher = cudaError_t (*)(const EvalArgs &, const LatticeParams &, int mode, cudaStream_t);
 
@@ -84,6 +88,8 @@ struct ShapeKernels {
     EvalLauncher eval;   // mode 0 = FP64, 1 = FP32, 2 = FP32 compensated action
     IntegrandLauncher transform;      // the range map in FP64, thread per sample (null: generic_mapped)
     OccupancyQuery transform_occupancy;
+    GaussLauncher gaussian;           // the Gaussian sampler in FP64, thread per sample (null: generic_mapped)
+    OccupancyQuery gaussian_occupancy;
 };
 
 // Compiled shape tables (shapes_small.cu, shapes_config.cu) and the generic

@@ -1,12 +1,15 @@
 // mapped_kernels.cuh -- the range map of Sec. 4 (the infinite range of every
-// coordinate taken to (-1, 1)) as a thread-per-sample FP64 kernel over the
-// compiled lattice shapes, with its launcher.  Included by the shapes_*.cu
-// files next to the box-sampler kernels.
+// coordinate taken to (-1, 1)) and Gaussian importance sampling as
+// thread-per-sample FP64 kernels over the compiled lattice shapes, with their
+// launchers.  Included by the shapes_*.cu files next to the box-sampler
+// kernels.
 //
 //   transform_f64  persistent, thread per sample: Philox point y in the box,
 //                  v_j = y_j / (1 - y_j^2), S_eff = S(v) - ln J with
 //                  ln J = sum_j ln[(1 + y_j^2) / (1 - y_j^2)^2], weight,
 //                  products and per-thread sums -> one FP64 record per chunk
+//   gaussian_f64   the same with v = mean + F Phi^-1(u), S_eff = S(v) -
+//                  |z|^2 / 2 and weight 0 outside the box (d <= 40)
 //
 // There is no FP32 screen: the map stretches the coordinates without bound
 // near y = +-1, so no fixed margin covers the FP32 action's error there, and
@@ -133,6 +136,126 @@ __global__ void __launch_bounds__(BLOCK, 1) transform_f64(const IntegrandArgs ar
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         chunk_record<double, K, R, BLOCK>(acc, m_acc, sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian importance sampling, thread per sample (d <= kGaussThreadMaxD):
+// z_j = Phi^-1(u_j) for the unit point u (the box plays no part in drawing),
+// v = mean + F z, S_eff = S(v) - |z|^2 / 2, and weight 0 outside the box
+// [lo, hi).  The rest of 1/q (the record's log-volume (d/2) ln 2 pi +
+// ln |det F|) is set by the merge.  F, held transposed in shared memory
+// (column j of F contiguous, every thread reading the same word), is applied
+// column by column as each z_j is drawn, so z is never stored; for an upper
+// triangular F (TRI, the proposal bfi_gaussian_proposal returns) column j
+// stops at row j.  Samples outside the box are counted in n and skip the
+// action; the kernel counts the evaluated (inside) samples in stats.
+// ---------------------------------------------------------------------------
+constexpr int kGaussThreadMaxD = 40;
+
+template <int NX, int NT, int BLOCK, bool TRI>
+__global__ void __launch_bounds__(BLOCK, 1) gaussian_f64(const IntegrandArgs args, const LatticeConst<double> lc,
+                                                         const RoundKeys rk, const double *mean,
+                                                         const double *factor) {
+    constexpr int D = NX * NT;
+    constexpr int R = NX / 2 + 1;
+    constexpr int K = sum_count(R);
+    constexpr int NQ = (D + 3) / 4;
+    static_assert(D <= kGaussThreadMaxD, "the thread-per-sample Gaussian kernel holds v in registers");
+    __shared__ ChunkShared<BLOCK> sh;
+    __shared__ double s_ft[D * D];  // s_ft[j D + r] = F[r][j]
+    __shared__ double s_mean[D], s_lo[D], s_hi[D];
+    __shared__ PhiloxPrefix s_pre[NQ];
+    __shared__ double s_sums[K * BLOCK];
+    const int tid = threadIdx.x;
+    SmemSums<double, K, BLOCK> acc{s_sums + tid};
+    for (int k = tid; k < D * D; k += BLOCK) s_ft[(k % D) * D + k / D] = factor[k];
+    for (int k = tid; k < D; k += BLOCK) s_mean[k] = mean ? mean[k] : 0.0;
+
+    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+        const ChunkView v = chunk_view(args, c, D);
+        if (tid < D) {
+            s_lo[tid] = v.lo[tid];
+            s_hi[tid] = v.hi[tid];
+        }
+        chunk_prefixes<D>(v, rk, s_pre);
+        if (tid == 0) sh.evaluated = 0u;
+        acc.zero();
+        __syncthreads();
+
+        double m_acc = INFINITY;
+        unsigned n_eval = 0;
+        for (uint64_t k = tid; k < v.cnt; k += BLOCK) {
+            const uint32_t x = static_cast<uint32_t>(v.first + k);
+            double u[D];
+#pragma unroll
+            for (int r = 0; r < D; ++r) u[r] = s_mean[r];
+            double zz = 0.0;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const uint4 b = philox_from_prefix(x, s_pre[q], rk);
+                const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int j = 4 * q + t;
+                    if (j < D) {
+                        const double z = normcdfinv(unit_f64(w4[t]));
+                        zz = fma(z, z, zz);
+#pragma unroll
+                        for (int r = 0; r < (TRI ? j + 1 : D); ++r) u[r] = fma(s_ft[j * D + r], z, u[r]);
+                    }
+                }
+            }
+            bool inside = true;
+#pragma unroll
+            for (int r = 0; r < D; ++r) inside = inside && u[r] >= s_lo[r] && u[r] < s_hi[r];
+            if (!inside) continue;  // weight 0
+            const double S = action<NX, NT, double>(u, lc) - 0.5 * zz;
+            double Q[R];
+            products<NX, NT, double>(u, Q);
+            if (S < m_acc - kRescaleMargin) {
+                rescale<double, K, R, BLOCK>(acc, exp(S - m_acc));
+                m_acc = S;
+            }
+            accumulate<double, K, R, BLOCK>(acc, exp(m_acc - S), Q);
+            ++n_eval;
+        }
+        add_evaluated(args.stats, n_eval, &sh.evaluated);
+        chunk_record<double, K, R, BLOCK>(acc, m_acc, sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
+    }
+}
+
+template <int NX, int NT>
+cudaError_t launch_gaussian(const IntegrandArgs &args, const LatticeParams &p, const MapArgs &m, bool upper,
+                            uint32_t seed, uint32_t job, int grid, cudaStream_t st) {
+    const RoundKeys rk = make_round_keys(seed, job);
+    if (upper)
+        gaussian_f64<NX, NT, kBlock, true><<<grid, kBlock, 0, st>>>(args, make_const<double>(p), rk, m.mean, m.factor);
+    else
+        gaussian_f64<NX, NT, kBlock, false><<<grid, kBlock, 0, st>>>(args, make_const<double>(p), rk, m.mean, m.factor);
+    return cudaGetLastError();
+}
+
+template <int NX, int NT>
+cudaError_t occupancy_gaussian(int, int, int *blocks_per_sm) {
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, gaussian_f64<NX, NT, kBlock, true>, kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gaussian_f64<NX, NT, kBlock, false>, kBlock, 0);
+    *blocks_per_sm = a < b ? a : b;
+    return e;
+}
+
+// The Gaussian entries of the shape table: null above kGaussThreadMaxD (those
+// shapes use generic_mapped<2>).
+template <int NX, int NT>
+constexpr GaussLauncher gaussian_entry() {
+    if constexpr (NX * NT <= kGaussThreadMaxD) return launch_gaussian<NX, NT>;
+    else return nullptr;
+}
+template <int NX, int NT>
+constexpr OccupancyQuery gaussian_occupancy_entry() {
+    if constexpr (NX * NT <= kGaussThreadMaxD) return occupancy_gaussian<NX, NT>;
+    else return nullptr;
 }
 
 template <int NX, int NT>

@@ -1,4 +1,4 @@
-// shapes_config.cu -- instantiates the thread-per-sample integrand and range-map kernels for the
+// shapes_config.cu -- instantiates the thread-per-sample integrand and sampler kernels for the
 // lattice shapes listed in BFI_SHAPES_CONFIG (bfi_kernels.h).
 #include "integrand_kernels.cuh"
 #include "mapped_kernels.cuh"
@@ -9,7 +9,8 @@ namespace bfi {
     {NX, NT, 0,                                                                   \
      {launch_integrand<NX, NT, double>, launch_integrand<NX, NT, float>},         \
      {occupancy_integrand<NX, NT, double>, occupancy_integrand<NX, NT, float>},   \
-     launch_eval<NX, NT>, launch_transform<NX, NT>, occupancy_transform<NX, NT>},
+     launch_eval<NX, NT>, launch_transform<NX, NT>, occupancy_transform<NX, NT>,     \
+     gaussian_entry<NX, NT>(), gaussian_occupancy_entry<NX, NT>()},
 
 static const ShapeKernels kTable[] = {BFI_SHAPES_CONFIG(BFI_SHAPE_ENTRY)};
 

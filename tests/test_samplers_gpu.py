@@ -96,18 +96,32 @@ def test_transform_ragged_counts_and_edge_boxes(bfi, nx, nt):
     assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9, m=np.abs(o_s[1:, 1]).max())
 
 
+# factor: "lower" (Cholesky factor of the covariance), "upper" (the inverse
+# transpose of the precision's Cholesky factor, the form of
+# bfi_gaussian_proposal) or "dense" (lower times an orthogonal matrix).
+# Shapes with d <= 40 in the compiled tables run on the thread-per-sample
+# kernel (upper: its triangular form); (5, 3), (8, 8) and (32, 2) on the
+# warp-per-sample kernel.
 @pytest.mark.gpu
-@pytest.mark.parametrize("nx,nt,sigma,with_mean,dense", [(4, 2, 4.0, False, False), (10, 2, 5.0, False, False),
-                                                         (3, 1, 2.0, True, False), (5, 3, 3.0, True, True),
-                                                         (8, 8, 3.0, False, False)])
-def test_gaussian_matches_oracle(bfi, nx, nt, sigma, with_mean, dense):
+@pytest.mark.parametrize("nx,nt,sigma,with_mean,factor", [(4, 2, 4.0, False, "lower"), (10, 2, 5.0, False, "lower"),
+                                                          (3, 1, 2.0, True, "lower"), (5, 3, 3.0, True, "dense"),
+                                                          (8, 8, 3.0, False, "lower"), (10, 2, 5.0, True, "upper"),
+                                                          (6, 4, 3.0, False, "upper"), (8, 4, 3.0, True, "dense"),
+                                                          (10, 4, 4.0, False, "upper"), (2, 1, 2.0, False, "upper"),
+                                                          (32, 2, 3.0, False, "upper")])
+def test_gaussian_matches_oracle(bfi, nx, nt, sigma, with_mean, factor):
     d = nx * nt
     lat_o = oracle.lattice(nx, nt)
-    F = np.linalg.cholesky(proposal_covariance(lat_o, sigma))
+    cov = proposal_covariance(lat_o, sigma)
+    F = np.linalg.cholesky(cov)
     rng = np.random.default_rng(d)
-    if dense:  # any non-singular factor, not only a triangular one
+    if factor == "dense":  # any non-singular factor, not only a triangular one
         Q, _ = np.linalg.qr(rng.normal(size=(d, d)))
         F = F @ Q
+    elif factor == "upper":
+        F = np.linalg.inv(np.linalg.cholesky(np.linalg.inv(cov))).T
+        assert np.allclose(np.tril(F, -1), 0.0) and np.allclose(F @ F.T, cov)
+        F = np.triu(F)
     mean = rng.normal(scale=0.3, size=d) if with_mean else None
     lo = np.stack([np.full(d, -5.0), np.full(d, -2.0), np.full(d, 0.0)])
     hi = np.stack([np.full(d, 5.0), np.full(d, 3.0), np.full(d, 5.0)])
