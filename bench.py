@@ -104,11 +104,15 @@ def rank_info():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    """nvidia-smi clock / throttle sampling while the timed region runs; the
+    raw samples go to $BFI_CLOCKS_DIR (default: the system temporary
+    directory) as clocks_<pid>.csv."""
 
     def __init__(self, gpu_index: int):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(os.environ.get("BFI_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 f"clocks_{os.getpid()}.csv")
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
