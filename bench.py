@@ -52,13 +52,22 @@ FP64_PEAK_OPS = 2 * SM_COUNT * SM_MAX_MHZ * 1e6      # FP64 operations/s
 # kernel, from ncu's dram__bytes_read.sum + dram__bytes_write.sum (a 1-pass
 # capture; profiles/integrand_f64_10x2.md).  Must be reset to None whenever
 # that kernel changes.
-TRAFFIC_FP64_10x2 = 757248
+TRAFFIC_FP64_10x2 = None
 
 
 def screen_ops(nx, nt):
-    """Per sample, every sample: Philox words, FP32 point, FP32 action."""
+    """Per sample the full FP32 screen examines: Philox words, FP32 point, FP32 action."""
     d = nx * nt
     return ((d + 3) // 4) * 10 * 4 + 2 * d + 8 * d
+
+
+def partial_ops(nx, nt):
+    """Per sample, stage 1 of the two-stage screen: the first BP of the ceil(d/4) Philox blocks (BP about 0.6
+    of them), the FP32 points of the MC sites they complete, the residuals of sites 1 .. MC-2."""
+    d = nx * nt
+    bp = (3 * ((d + 3) // 4) + 4) // 5
+    mc = min((4 * bp) // nt, nx)
+    return bp * 10 * 4 + 2 * mc * nt + 8 * (mc - 2) * nt
 
 
 def eval_ops_fp64(nx, nt):
@@ -75,15 +84,17 @@ def eval_ops_fp32(nx, nt):
     return d * r + 2 + 4 * k
 
 
-def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2):
-    """Algorithmic work of one launch against the binding resource."""
+def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2, screened=None):
+    """Algorithmic work of one launch against the binding resource.  'screened' (two-stage screen only): the
+    samples the full screen examined; every sample then costs partial_ops and those add screen_ops."""
     t = kern_ms * 1e-3
+    w_screen = n * screen_ops(nx, nt) if screened is None else n * partial_ops(nx, nt) + screened * screen_ops(nx, nt)
     if precision == "fp64":
         dp, integer = eval_ops_fp64(nx, nt)
-        w_issue = n * screen_ops(nx, nt) + n_eval * integer
+        w_issue = w_screen + n_eval * integer
         w_dp = n_eval * dp
     else:
-        w_issue = n * screen_ops(nx, nt) + n_eval * eval_ops_fp32(nx, nt)
+        w_issue = w_screen + n_eval * eval_ops_fp32(nx, nt)
         w_dp = 0
     t_issue, t_dp = w_issue / ISSUE_PEAK_OPS, w_dp / FP64_PEAK_OPS
     if t_issue >= t_dp:
@@ -95,6 +106,8 @@ def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2):
             "traffic": None, "kernel_ms": kern_ms, "samples": n, "evaluated": n_eval,
             "issue_frac": w_issue / t / ISSUE_PEAK_OPS, "fp64_frac": w_dp / t / FP64_PEAK_OPS,
             "screen_ops_per_sample": screen_ops(nx, nt),
+            "partial_ops_per_sample": None if screened is None else partial_ops(nx, nt),
+            "full_screened": n if screened is None else screened,
             "peak_source": "unit counts x 2070 MHz: 128 FP32/INT and 2 FP64 lanes per SM, 152 SMs"}
 
 
@@ -246,7 +259,8 @@ def timed_steps(plan, lo, hi, sid, job, steps, warmup, flush_buf, dist, stream):
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    return total_ms / steps, kern_ms / steps, slots, totals, plan.stats()[0]
+    full, two_stage = plan.screen_stats()
+    return total_ms / steps, kern_ms / steps, slots, totals, plan.stats()[0], (full if two_stage else None)
 
 
 def run_bfi(args):
@@ -275,7 +289,7 @@ def run_bfi(args):
     plan = bfi.Plan(lat, job.samples, bfi.FP64, device=local_rank)
     info = plan.info()
     sampler = ClockSampler(local_rank) if rank == 0 else None
-    ms, kern_ms, slots, totals, n_eval = timed_steps(plan, lo, hi, sid, job, args.steps, args.warmup,
+    ms, kern_ms, slots, totals, n_eval, n_full = timed_steps(plan, lo, hi, sid, job, args.steps, args.warmup,
                                                      flush_buf, dist, stream)
     clocks = sampler.stop() if sampler else None
 
@@ -291,7 +305,7 @@ def run_bfi(args):
 
     samples_all = world * job.total_samples
     value = samples_all / (ms * 1e-3)
-    roof = roofline(job.total_samples, n_eval, kern_ms, "fp64", NX, NT)
+    roof = roofline(job.total_samples, n_eval, kern_ms, "fp64", NX, NT, screened=n_full)
     roof["kernel"] = f"hint + integrand FP64 <{NX},{NT}>"
     if (NX, NT) == (10, 2) and args.samples_log2 == 20:
         roof["traffic"] = TRAFFIC_FP64_10x2
@@ -301,9 +315,9 @@ def run_bfi(args):
     if not args.skip_fp32:
         job32 = make_job(rank, world, 1 << (args.samples_log2 + 4))
         plan32 = bfi.Plan(lat, job32.samples, bfi.FP32, device=local_rank)
-        ms32, kern32, _, tot32, n_eval32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
+        ms32, kern32, _, tot32, n_eval32, n_full32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
                                                        max(1, args.warmup // 2), flush_buf, dist, stream)
-        roof32 = roofline(job32.total_samples, n_eval32, kern32, "fp32", NX, NT)
+        roof32 = roofline(job32.total_samples, n_eval32, kern32, "fp32", NX, NT, screened=n_full32)
         roof32["kernel"] = f"hint + integrand FP32 <{NX},{NT}>"
         plan32.close()
         # the same 2^34-point job in FP64 mode (its own FP64 points): the FP32

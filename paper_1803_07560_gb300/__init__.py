@@ -148,6 +148,7 @@ _SIGNATURES = {
     "bfi_autotune_grid": (ctypes.c_int, [_P(Lattice), ctypes.c_int, ctypes.c_int, _P(ctypes.c_int32)]),
     "bfi_plan_get_timing": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "bfi_plan_get_stats": (ctypes.c_int, [_vp, _P(ctypes.c_uint64), _P(ctypes.c_float)]),
+    "bfi_plan_get_screen_stats": (ctypes.c_int, [_vp, _P(ctypes.c_uint64), _P(ctypes.c_int32)]),
     "bfi_integrate_static_scratch": (ctypes.c_int, [_P(Lattice), ctypes.c_int64, _P(ctypes.c_uint64), _vp,
                                                     _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
                                                     _vp, _vp, _vp]),
@@ -303,6 +304,14 @@ class Plan:
         w = ctypes.c_float()
         _check(_lib.bfi_plan_get_stats(self._h, ctypes.byref(n), ctypes.byref(w)))
         return int(n.value), float(w.value)
+
+    def screen_stats(self):
+        """(samples the full FP32 screen examined in the last execution,
+        whether the two-stage screen ran); see bfi_plan_get_screen_stats."""
+        n = ctypes.c_uint64()
+        two = ctypes.c_int32()
+        _check(_lib.bfi_plan_get_screen_stats(self._h, ctypes.byref(n), ctypes.byref(two)))
+        return int(n.value), bool(two.value)
 
     def close(self):
         if getattr(self, "_h", None):

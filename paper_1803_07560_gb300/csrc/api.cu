@@ -215,10 +215,10 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
     const size_t smp_bytes = sizeof(uint64_t) * nsub;
     const size_t par_bytes = sizeof(double) * static_cast<size_t>(std::max<int64_t>(p->nchunks, 1)) * (p->K + 2);
     const size_t hint_bytes = sizeof(float) * nsub;
-    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + sizeof(unsigned long long) + sizeof(double) * 2 * nsub;
+    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + 2 * sizeof(unsigned long long) + sizeof(double) * 2 * nsub;
     if (cudaMalloc(&p->d_chunk_off, off_bytes) != cudaSuccess || cudaMalloc(&p->d_samples, smp_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_partials, par_bytes) != cudaSuccess || cudaMalloc(&p->d_hint, hint_bytes) != cudaSuccess ||
-        cudaMalloc(&p->d_stats, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&p->d_stats, 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&p->d_fbuf, sizeof(double) * 2 * nsub) != cudaSuccess) {
         cudaGetLastError();
         bfi_plan_destroy(p);
@@ -259,11 +259,11 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
     if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device: %s", cudaGetErrorString(g.err));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[0], st));
-    BFI_CUDA(cudaMemsetAsync(plan->d_stats, 0, sizeof(unsigned long long), st));
+    BFI_CUDA(cudaMemsetAsync(plan->d_stats, 0, 2 * sizeof(unsigned long long), st));
     if (plan->nchunks > 0) {
         bfi::IntegrandArgs a{lo,           hi,           sub_id,        plan->d_samples,     plan->d_chunk_off,
                              plan->d_partials, plan->d_hint, plan->d_stats, plan->nsub, plan->nchunks,
-                             plan->chunk_samples, plan->skip_window};
+                             plan->chunk_samples, plan->skip_window, plan->d_stats + 1};
         if (plan->sampler == BFI_SAMPLE_BOX) {
             BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
         } else if (plan->sampler == BFI_SAMPLE_TRANSFORM && plan->shape->transform) {
@@ -453,6 +453,23 @@ bfi_status bfi_plan_get_stats(bfi_plan *plan, uint64_t *evaluated, float *skip_w
         *evaluated = v;
     }
     if (skip_window) *skip_window = plan->skip_window;
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_get_screen_stats(bfi_plan *plan, uint64_t *screened, int32_t *two_stage) {
+    if (!plan) return fail(BFI_E_INVALID, "plan is NULL");
+    const bool two = plan->sampler == BFI_SAMPLE_BOX && plan->shape->two_stage != 0;
+    if (two_stage) *two_stage = two ? 1 : 0;
+    if (screened) {
+        if (two) {
+            DeviceGuard g(plan->device);
+            unsigned long long v = 0;
+            BFI_CUDA(cudaMemcpy(&v, plan->d_stats + 1, sizeof v, cudaMemcpyDeviceToHost));
+            *screened = v;
+        } else {
+            *screened = static_cast<uint64_t>(plan->total);
+        }
+    }
     return BFI_OK;
 }
 

@@ -34,6 +34,7 @@ struct IntegrandArgs {
     int64_t nchunks;
     int64_t chunk_samples;
     float skip_window;         // samples above (reference + skip_window) have negligible weight
+    unsigned long long *screened;  // [1] samples the full FP32 screen examined after the partial one, or null
 };
 
 struct MergeArgs {
@@ -90,6 +91,7 @@ struct ShapeKernels {
     OccupancyQuery transform_occupancy;
     GaussLauncher gaussian;           // the Gaussian sampler in FP64, thread per sample (null: generic_mapped)
     OccupancyQuery gaussian_occupancy;
+    int two_stage;                    // 1: the box-sampler kernels screen with the partial action first
 };
 
 // Compiled shape tables (shapes_small.cu, shapes_config.cu) and the generic

@@ -752,12 +752,12 @@ cudaError_t mapped_occupancy(int nx, int nt, int *blocks_per_sm) {
 }
 
 const ShapeKernels kGeneric = {0, 0, 1, {gen_integrand_launcher<true>, gen_integrand_launcher<false>},
-                               {gen_occupancy<true>, gen_occupancy<false>}, gen_eval, nullptr, nullptr, nullptr, nullptr};
+                               {gen_occupancy<true>, gen_occupancy<false>}, gen_eval, nullptr, nullptr, nullptr, nullptr, 0};
 
 // Shapes with Nx = 32 SPL and SPL NT in {4, 8, 16}: the register-resident screen.
 #define BFI_LANES(SPL, NT)                                                                                   \
     {32 * SPL, NT, 1, {gen_integrand_launcher<true, SPL, NT>, gen_integrand_launcher<false, SPL, NT>},      \
-     {gen_occupancy<true, SPL, NT>, gen_occupancy<false, SPL, NT>}, gen_eval, nullptr, nullptr, nullptr, nullptr}
+     {gen_occupancy<true, SPL, NT>, gen_occupancy<false, SPL, NT>}, gen_eval, nullptr, nullptr, nullptr, nullptr, 0}
 const ShapeKernels kLanes[] = {BFI_LANES(1, 4),  BFI_LANES(1, 8), BFI_LANES(1, 16), BFI_LANES(2, 2),
                                BFI_LANES(2, 4),  BFI_LANES(2, 8), BFI_LANES(4, 1),  BFI_LANES(4, 2),
                                BFI_LANES(4, 4),  BFI_LANES(8, 1), BFI_LANES(8, 2),  BFI_LANES(16, 1)};

@@ -286,6 +286,78 @@ __device__ __forceinline__ float screen_action(uint32_t x, const PhiloxPrefix *p
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two-stage screen.  Stage 1 draws only the first BP Philox blocks, which
+// hold the coordinates of the complete sites 0 .. MC-1, and sums the squared
+// residuals of sites 1 .. MC-2 (every slice): a partial action P <= S,
+// computed like the full FP32 action on a subset of its non-negative terms,
+// so the screen's bound |S_f32 - S| <= 1 + 0.1% S holds for it too.  A sample
+// whose P already exceeds the threshold is rejected; the few that survive
+// (about a tenth at 10x2 over the box) are queued and screened in full, 32 at
+// a time, by stage 2.  BP is about 0.6 of the blocks; the split is used where
+// it leaves at least one residual site out and the lattice has 3 or more
+// blocks.
+// ---------------------------------------------------------------------------
+template <int NX, int NT>
+struct PartialScreen {
+    static constexpr int D = NX * NT;
+    static constexpr int NQ = (D + 3) / 4;
+    static constexpr int BP = (3 * NQ + 4) / 5;
+    static constexpr int MC = (4 * BP) / NT < NX ? (4 * BP) / NT : NX;
+    static constexpr int DW = MC * NT;  // coordinates stage 1 maps
+#ifdef BFI_NO_PARTIAL_SCREEN
+    static constexpr bool enabled = false;
+#else
+    static constexpr bool enabled = NQ >= 3 && MC >= 3 && MC < NX;
+#endif
+};
+
+// Stage 1 on packed f32x2 pairs of time slices (h, h + NT/2) of one site:
+// the next slice of pair h is pair h + 1, and the swapped pair 0 for the last
+// one (NT is even wherever the split is used).  Each component rounds as the
+// scalar residual does.
+template <int NX, int NT, typename Map>
+__device__ __forceinline__ float partial_action(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
+                                                const float2 *box, const LatticeConst<float> &c) {
+    using PS = PartialScreen<NX, NT>;
+    static_assert(NT % 2 == 0, "the partial screen pairs time slices");
+    constexpr int H = NT / 2;
+    float2 P[PS::MC * H];
+#pragma unroll
+    for (int q = 0; q < PS::BP; ++q) {
+        const uint4 b = philox_from_prefix(x, pre[q], rk);
+        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = 4 * q + t;
+            if (j < PS::DW) {
+                const int m = j / NT, l = j % NT;
+                const float val = Map{}(w4[t], box[j]);
+                if (l < H) P[m * H + l].x = val;
+                else P[m * H + l - H].y = val;
+            }
+        }
+    }
+    const float2 cadv = make_float2(c.c_adv, c.c_adv), k1 = make_float2(c.k1, c.k1);
+    const float2 ncd = make_float2(c.neg_c_dif, c.neg_c_dif), m1 = make_float2(-1.f, -1.f);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 1; m + 1 < PS::MC; ++m) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const float2 here = P[m * H + h];
+            const float2 next = h + 1 < H ? P[m * H + h + 1] : swap2(P[m * H]);
+            const float2 right = P[(m + 1) * H + h];
+            const float2 left = P[(m - 1) * H + h];
+            const float2 t = __ffma2_rn(cadv, __ffma2_rn(m1, left, right), k1);
+            float2 R = __ffma2_rn(here, t, next);
+            R = __ffma2_rn(ncd, __fadd2_rn(right, left), R);
+            acc = __ffma2_rn(R, R, acc);
+        }
+    }
+    return (acc.x + acc.y) * c.inv_2Dtau;
+}
+
 // Running minimum shared across the CTA at fixed points of the sample loop:
 // every thread contributes, then every thread reads the same value, so the
 // decisions that depend on it do not depend on timing.  S >= 0, so the float
@@ -303,6 +375,14 @@ __device__ __forceinline__ void add_evaluated(unsigned long long *stats, unsigne
     atomicAdd(s_cnt, n_eval);
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(stats, static_cast<unsigned long long>(*s_cnt));
+}
+
+// The same for the samples the full screen examined (two-stage screens).
+__device__ __forceinline__ void add_screened(unsigned long long *screened, unsigned n_full, unsigned *s_cnt) {
+    if (!screened) return;
+    atomicAdd(s_cnt, n_full);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(screened, static_cast<unsigned long long>(*s_cnt));
 }
 
 // ---------------------------------------------------------------------------
@@ -457,6 +537,7 @@ struct ChunkShared {
     double mb;
     int min_bits;
     unsigned evaluated;
+    unsigned screened;
 };
 
 // ---------------------------------------------------------------------------
@@ -524,8 +605,10 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
     __shared__ PhiloxPrefix s_pre[(D + 3) / 4];
     __shared__ double s_sums[K * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
+    __shared__ uint32_t s_squeue[PartialScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];
     const int tid = threadIdx.x, lane = tid & 31;
     uint32_t *queue = s_queue[tid >> 5];
+    uint32_t *squeue = s_squeue[PartialScreen<NX, NT>::enabled ? tid >> 5 : 0];
     SmemSums<double, K, BLOCK> acc{s_sums + tid};
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
@@ -544,6 +627,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         if (tid == 0) {
             sh.min_bits = __float_as_int(hint);
             sh.evaluated = 0u;
+            sh.screened = 0u;
         }
         acc.zero();
         __syncthreads();
@@ -571,29 +655,52 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         // m_ref changes only where the queue is evaluated (then made uniform
         // across the warp) and where the CTA shares it; thr follows it
         float thr = m_ref + args.skip_window + 1.0f;
-        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
-        for (uint64_t row = 0; row < nrows; ++row) {
-            const uint64_t k = row * BLOCK + tid;
+        // full screen of sample offset k (valid lanes) and the candidate queue
+        unsigned n_full = 0;
+        auto screen = [&](uint32_t k, bool valid) {
             bool cand = false;
-            if (k < v.cnt) {
+            if (valid) {
+                ++n_full;
                 const float S_f = screen_action<NX, NT, MapScreen>(static_cast<uint32_t>(v.first + k), s_pre, rk,
                                                                    s_box, lcf);
                 cand = __fmaf_rn(-1e-3f, S_f, S_f) <= thr;  // S_f <= m_ref + window + 1 + 0.1% of S_f
             }
-            count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
+            count = enqueue(queue, count, cand, k);
             if (count >= 32) {
                 evaluate(queue[lane]);
                 count = dequeue32(queue, count);
                 m_ref = warp_min(m_ref);
                 thr = m_ref + args.skip_window + 1.0f;
             }
+        };
+        int scount = 0;  // stage-1 survivors waiting for the full screen
+        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
+        for (uint64_t row = 0; row < nrows; ++row) {
+            const uint64_t k = row * BLOCK + tid;
+            if constexpr (PartialScreen<NX, NT>::enabled) {
+                bool surv = false;
+                if (k < v.cnt) {
+                    const float P_f = partial_action<NX, NT, MapScreen>(static_cast<uint32_t>(v.first + k), s_pre,
+                                                                        rk, s_box, lcf);
+                    surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
+                }
+                scount = enqueue(squeue, scount, surv, static_cast<uint32_t>(k));
+                if (scount >= 32) {
+                    screen(squeue[lane], true);
+                    scount = dequeue32(squeue, scount);
+                }
+            } else {
+                screen(static_cast<uint32_t>(k), k < v.cnt);
+            }
             if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
                 share_min(&sh.min_bits, m_ref);
                 thr = m_ref + args.skip_window + 1.0f;
             }
         }
+        if (PartialScreen<NX, NT>::enabled && scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
+        if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
         chunk_record<double, K, R, BLOCK>(acc, m_acc, sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
     }
 }
@@ -623,8 +730,10 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
     __shared__ PhiloxPrefix s_pre[(D + 3) / 4];
     __shared__ float s_sums[Sums::WORDS * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
+    __shared__ uint32_t s_squeue[PartialScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];
     const int tid = threadIdx.x, lane = tid & 31;
     uint32_t *queue = s_queue[tid >> 5];
+    uint32_t *squeue = s_squeue[PartialScreen<NX, NT>::enabled ? tid >> 5 : 0];
     Sums acc{s_sums + tid};
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
@@ -636,6 +745,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         if (tid == 0) {
             sh.min_bits = __float_as_int(hint);
             sh.evaluated = 0u;
+            sh.screened = 0u;
         }
         acc.zero();
         __syncthreads();
@@ -663,26 +773,47 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         // m_ref changes only where the queue is evaluated (then made uniform
         // across the warp) and where the CTA shares it; thr follows it
         float thr = m_ref + args.skip_window;
-        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
-        for (uint64_t row = 0; row < nrows; ++row) {
-            const uint64_t k = row * BLOCK + tid;
-            bool cand = false;
-            if (k < v.cnt)
-                cand = screen_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, lc) <= thr;
-            count = enqueue(queue, count, cand, static_cast<uint32_t>(k));
+        unsigned n_full = 0;
+        auto screen = [&](uint32_t k, bool valid) {
+            n_full += valid ? 1u : 0u;
+            const bool cand =
+                valid && screen_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, lc) <= thr;
+            count = enqueue(queue, count, cand, k);
             if (count >= 32) {
                 evaluate(queue[lane]);
                 count = dequeue32(queue, count);
                 m_ref = warp_min(m_ref);
                 thr = m_ref + args.skip_window;
             }
+        };
+        int scount = 0;  // stage-1 survivors waiting for the full screen
+        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
+        for (uint64_t row = 0; row < nrows; ++row) {
+            const uint64_t k = row * BLOCK + tid;
+            if constexpr (PartialScreen<NX, NT>::enabled) {
+                bool surv = false;
+                if (k < v.cnt) {  // 0.1% slack: the partial and full sums add in different orders
+                    const float P_f = partial_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk,
+                                                                     s_box, lc);
+                    surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
+                }
+                scount = enqueue(squeue, scount, surv, static_cast<uint32_t>(k));
+                if (scount >= 32) {
+                    screen(squeue[lane], true);
+                    scount = dequeue32(squeue, scount);
+                }
+            } else {
+                screen(static_cast<uint32_t>(k), k < v.cnt);
+            }
             if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
                 share_min(&sh.min_bits, m_ref);
                 thr = m_ref + args.skip_window;
             }
         }
+        if (PartialScreen<NX, NT>::enabled && scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
+        if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
         chunk_record<float, K, R, BLOCK>(acc, static_cast<double>(m_acc), sh.f, &sh.mb, args.partials + c * (K + 2),
                                          v.cnt);
     }

@@ -228,7 +228,8 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
                              p.nsub,
                              p.nchunks,
                              p.chunk_samples,
-                             p.window};
+                             p.window,
+                             nullptr};
         ok = cuda(shape->integrand[prec](a, lp, r.seed, r.job_id, static_cast<int>(grid), st), "integrand launch");
     }
     if (ok) {

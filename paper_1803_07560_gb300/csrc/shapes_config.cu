@@ -10,7 +10,8 @@ namespace bfi {
      {launch_integrand<NX, NT, double>, launch_integrand<NX, NT, float>},         \
      {occupancy_integrand<NX, NT, double>, occupancy_integrand<NX, NT, float>},   \
      launch_eval<NX, NT>, launch_transform<NX, NT>, occupancy_transform<NX, NT>,     \
-     gaussian_entry<NX, NT>(), gaussian_occupancy_entry<NX, NT>()},
+     gaussian_entry<NX, NT>(), gaussian_occupancy_entry<NX, NT>(),                  \
+     PartialScreen<NX, NT>::enabled ? 1 : 0},
 
 static const ShapeKernels kTable[] = {BFI_SHAPES_CONFIG(BFI_SHAPE_ENTRY)};
 

@@ -166,7 +166,8 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
                                 lattice->a,  lattice->tau, lattice->nonlinear, lattice->mass2};
     if (nchunks > 0) {
         bfi::IntegrandArgs a{lo,         hi,     sub_id, d_samples, d_off,         d_partials,
-                             d_hint,     d_stats, nsub,  nchunks,   chunk_samples, bfi::plan_negligible_window(precision, n_max)};
+                             d_hint,     d_stats, nsub,  nchunks,   chunk_samples, bfi::plan_negligible_window(precision, n_max),
+                             nullptr};
         if ((e = shape->integrand[precision](a, lp, seed, job_id, static_cast<int>(grid), cs)) != cudaSuccess)
             return cuda_fail("integrand launch", e);
     }
