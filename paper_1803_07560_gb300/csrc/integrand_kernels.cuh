@@ -293,11 +293,18 @@ __device__ __forceinline__ float screen_action(uint32_t x, const PhiloxPrefix *p
 // computed like the full FP32 action on a subset of its non-negative terms,
 // so the screen's bound |S_f32 - S| <= 1 + 0.1% S holds for it too.  A sample
 // whose P already exceeds the threshold is rejected; the few that survive
-// (about a tenth at 10x2 over the box) are queued and screened in full, 32 at
-// a time, by stage 2.  BP is about 0.6 of the blocks; the split is used where
-// it leaves at least one residual site out and the lattice has 3 or more
-// blocks.
+// (about a fifth at 10x2 over the box) are queued and screened in full, 32 at
+// a time, by stage 2.  BP is about 0.6 of the blocks.  The split is used where
+// the lattice has 3 or more blocks and stage 1 covers at least 35% of the
+// residual sites, but not all: measured on GB300, 4x4 (25%) and 6x2 (33%)
+// ran 5-16% slower with it and 6x4 (33%) no faster, while 8x4 (37.5%) and
+// 10x2 (40%) ran 5-15% faster.
 // ---------------------------------------------------------------------------
+// Chunks with fewer rows per thread screen in one stage: the survivor queue's
+// final drain costs about one full-screen row per warp, which a short chunk
+// does not earn back.
+constexpr uint64_t kTwoStageMinRows = 16;
+
 template <int NX, int NT>
 struct PartialScreen {
     static constexpr int D = NX * NT;
@@ -308,7 +315,7 @@ struct PartialScreen {
 #ifdef BFI_NO_PARTIAL_SCREEN
     static constexpr bool enabled = false;
 #else
-    static constexpr bool enabled = NQ >= 3 && MC >= 3 && MC < NX;
+    static constexpr bool enabled = NQ >= 3 && MC < NX && 20 * (MC - 2) >= 7 * NX;
 #endif
 };
 
@@ -320,42 +327,46 @@ template <int NX, int NT, typename Map>
 __device__ __forceinline__ float partial_action(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
                                                 const float2 *box, const LatticeConst<float> &c) {
     using PS = PartialScreen<NX, NT>;
-    static_assert(NT % 2 == 0, "the partial screen pairs time slices");
-    constexpr int H = NT / 2;
-    float2 P[PS::MC * H];
+    static_assert(!PS::enabled || NT % 2 == 0, "the partial screen pairs time slices");
+    if constexpr (!PS::enabled) {
+        return 0.f;  // never called: the kernels take the one-stage path
+    } else {
+        constexpr int H = NT / 2;
+        float2 P[PS::MC * H];
 #pragma unroll
-    for (int q = 0; q < PS::BP; ++q) {
-        const uint4 b = philox_from_prefix(x, pre[q], rk);
-        const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
+        for (int q = 0; q < PS::BP; ++q) {
+            const uint4 b = philox_from_prefix(x, pre[q], rk);
+            const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int j = 4 * q + t;
-            if (j < PS::DW) {
-                const int m = j / NT, l = j % NT;
-                const float val = Map{}(w4[t], box[j]);
-                if (l < H) P[m * H + l].x = val;
-                else P[m * H + l - H].y = val;
+            for (int t = 0; t < 4; ++t) {
+                const int j = 4 * q + t;
+                if (j < PS::DW) {
+                    const int m = j / NT, l = j % NT;
+                    const float val = Map{}(w4[t], box[j]);
+                    if (l < H) P[m * H + l].x = val;
+                    else P[m * H + l - H].y = val;
+                }
             }
         }
-    }
-    const float2 cadv = make_float2(c.c_adv, c.c_adv), k1 = make_float2(c.k1, c.k1);
-    const float2 ncd = make_float2(c.neg_c_dif, c.neg_c_dif), m1 = make_float2(-1.f, -1.f);
-    float2 acc = make_float2(0.f, 0.f);
+        const float2 cadv = make_float2(c.c_adv, c.c_adv), k1 = make_float2(c.k1, c.k1);
+        const float2 ncd = make_float2(c.neg_c_dif, c.neg_c_dif), m1 = make_float2(-1.f, -1.f);
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int m = 1; m + 1 < PS::MC; ++m) {
+        for (int m = 1; m + 1 < PS::MC; ++m) {
 #pragma unroll
-        for (int h = 0; h < H; ++h) {
-            const float2 here = P[m * H + h];
-            const float2 next = h + 1 < H ? P[m * H + h + 1] : swap2(P[m * H]);
-            const float2 right = P[(m + 1) * H + h];
-            const float2 left = P[(m - 1) * H + h];
-            const float2 t = __ffma2_rn(cadv, __ffma2_rn(m1, left, right), k1);
-            float2 R = __ffma2_rn(here, t, next);
-            R = __ffma2_rn(ncd, __fadd2_rn(right, left), R);
-            acc = __ffma2_rn(R, R, acc);
+            for (int h = 0; h < H; ++h) {
+                const float2 here = P[m * H + h];
+                const float2 next = h + 1 < H ? P[m * H + h + 1] : swap2(P[m * H]);
+                const float2 right = P[(m + 1) * H + h];
+                const float2 left = P[(m - 1) * H + h];
+                const float2 t = __ffma2_rn(cadv, __ffma2_rn(m1, left, right), k1);
+                float2 R = __ffma2_rn(here, t, next);
+                R = __ffma2_rn(ncd, __fadd2_rn(right, left), R);
+                acc = __ffma2_rn(R, R, acc);
+            }
         }
+        return (acc.x + acc.y) * c.inv_2Dtau;
     }
-    return (acc.x + acc.y) * c.inv_2Dtau;
 }
 
 // Running minimum shared across the CTA at fixed points of the sample loop:
@@ -675,9 +686,10 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         };
         int scount = 0;  // stage-1 survivors waiting for the full screen
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
+        const bool two_stage = PartialScreen<NX, NT>::enabled && nrows >= kTwoStageMinRows;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
-            if constexpr (PartialScreen<NX, NT>::enabled) {
+            if (two_stage) {
                 bool surv = false;
                 if (k < v.cnt) {
                     const float P_f = partial_action<NX, NT, MapScreen>(static_cast<uint32_t>(v.first + k), s_pre,
@@ -697,7 +709,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
                 thr = m_ref + args.skip_window + 1.0f;
             }
         }
-        if (PartialScreen<NX, NT>::enabled && scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);
+        if (two_stage && scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
@@ -788,9 +800,10 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         };
         int scount = 0;  // stage-1 survivors waiting for the full screen
         const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
+        const bool two_stage = PartialScreen<NX, NT>::enabled && nrows >= kTwoStageMinRows;
         for (uint64_t row = 0; row < nrows; ++row) {
             const uint64_t k = row * BLOCK + tid;
-            if constexpr (PartialScreen<NX, NT>::enabled) {
+            if (two_stage) {
                 bool surv = false;
                 if (k < v.cnt) {  // 0.1% slack: the partial and full sums add in different orders
                     const float P_f = partial_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk,
@@ -810,7 +823,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
                 thr = m_ref + args.skip_window;
             }
         }
-        if (PartialScreen<NX, NT>::enabled && scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);
+        if (two_stage && scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
