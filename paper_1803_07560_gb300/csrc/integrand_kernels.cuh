@@ -302,7 +302,9 @@ __device__ __forceinline__ float screen_action(uint32_t x, const PhiloxPrefix *p
 // ---------------------------------------------------------------------------
 // Chunks with fewer rows per thread screen in one stage: the survivor queue's
 // final drain costs about one full-screen row per warp, which a short chunk
-// does not earn back.
+// does not earn back.  (A per-warp switch back to one stage when too many
+// samples survive was measured and rejected: early in a chunk the reference
+// action is still high, and the switch fired on the 10x2 workload too.)
 constexpr uint64_t kTwoStageMinRows = 16;
 
 template <int NX, int NT>
@@ -709,7 +711,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
                 thr = m_ref + args.skip_window + 1.0f;
             }
         }
-        if (two_stage && scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);
+        if (scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);  // survivors still queued
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
@@ -823,7 +825,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
                 thr = m_ref + args.skip_window;
             }
         }
-        if (two_stage && scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);
+        if (scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);  // survivors still queued
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
