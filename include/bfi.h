@@ -264,8 +264,8 @@ bfi_status bfi_plan_get_stats(bfi_plan *plan, uint64_t *evaluated, float *skip_w
  * the squared residuals of the sites whose neighbours they cover: a partial
  * action P <= S of Eq. (Gen2).  A sample with P above the negligible-weight
  * threshold (with the screen's margin) cannot carry weight and is dropped;
- * the rest are screened with the full FP32 action.  Chunks of fewer than 16
- * samples per thread skip stage 1.  *two_stage is 1 when the last execution
+ * the rest are screened with the full FP32 action.  Chunks of fewer than 256
+ * samples per thread (jobs below about 2^27 samples) skip stage 1.  *two_stage is 1 when the last execution
  * used the kernel with the split, and *screened is then the number of samples
  * the full screen examined; otherwise *screened is the plan's total sample
  * count (every sample fully screened or evaluated).  Waits for the device.  Either pointer

@@ -301,11 +301,16 @@ __device__ __forceinline__ float screen_action(uint32_t x, const PhiloxPrefix *p
 // 10x2 (40%) ran 5-15% faster.
 // ---------------------------------------------------------------------------
 // Chunks with fewer rows per thread screen in one stage: the survivor queue's
-// final drain costs about one full-screen row per warp, which a short chunk
-// does not earn back.  (A per-warp switch back to one stage when too many
+// final drain costs about one full-screen row per warp, and the smaller jobs
+// that get short chunks have less selective references.  Measured on the
+// batching workload (256 jobs, 2^20-2^28 samples each): 16 rows cost 4%
+// against one stage, 64 rows 2%, 256 rows nothing.  (A per-warp switch back to one stage when too many
 // samples survive was measured and rejected: early in a chunk the reference
 // action is still high, and the switch fired on the 10x2 workload too.)
-constexpr uint64_t kTwoStageMinRows = 16;
+#ifndef BFI_TWO_STAGE_MIN_ROWS
+#define BFI_TWO_STAGE_MIN_ROWS 256
+#endif
+constexpr uint64_t kTwoStageMinRows = BFI_TWO_STAGE_MIN_ROWS;
 
 template <int NX, int NT>
 struct PartialScreen {
