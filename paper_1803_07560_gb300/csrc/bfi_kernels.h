@@ -10,11 +10,15 @@ namespace bfi {
 constexpr int kBlock = 256;   // threads per CTA of the integrand kernels
 constexpr int kMaxD = 512;    // largest lattice (d = nx * nt) the library accepts
 
-// Lattice shapes with a compiled thread-per-sample kernel (NX, NT), in two
-// translation units that compile in parallel; every other shape with
-// d = NX NT <= kMaxD runs on the generic warp-per-sample kernel.
+// Lattice shapes with compiled thread-per-sample kernels (NX, NT), in five
+// translation units of about equal compile time that compile in parallel
+// (shapes_*.cu, each instantiating shapes_table.cuh); every other shape with
+// d = NX NT <= kMaxD runs on the generic warp-per-sample kernels.
 #define BFI_SHAPES_SMALL(X) X(2, 1) X(3, 1) X(4, 1) X(2, 2) X(3, 2) X(4, 2) X(6, 2) X(8, 2) X(10, 2)
-#define BFI_SHAPES_CONFIG(X) X(16, 2) X(32, 2) X(4, 4) X(6, 4) X(8, 4) X(10, 4) X(16, 4)
+#define BFI_SHAPES_CONFIG_A(X) X(10, 4)
+#define BFI_SHAPES_CONFIG_B(X) X(16, 2) X(4, 4)
+#define BFI_SHAPES_CONFIG_C(X) X(32, 2) X(6, 4)
+#define BFI_SHAPES_CONFIG_D(X) X(8, 4) X(16, 4)
 
 struct LatticeParams {
     int32_t nx, nt;
@@ -94,11 +98,14 @@ struct ShapeKernels {
     int two_stage;                    // 1: the box-sampler kernels screen with the partial action first
 };
 
-// Compiled shape tables (shapes_small.cu, shapes_config.cu) and the generic
-// kernels (generic.cu); find_shape looks in the tables, then falls back to
-// the generic kernels (null if d > kMaxD).
+// Compiled shape tables (shapes_*.cu) and the generic kernels (generic.cu);
+// find_shape looks in the tables, then falls back to the generic kernels
+// (null if d > kMaxD).
 const ShapeKernels *shapes_small(int *n);
-const ShapeKernels *shapes_config(int *n);
+const ShapeKernels *shapes_config_a(int *n);
+const ShapeKernels *shapes_config_b(int *n);
+const ShapeKernels *shapes_config_c(int *n);
+const ShapeKernels *shapes_config_d(int *n);
 const ShapeKernels *generic_shape(int nx, int nt);
 const ShapeKernels *find_shape(int nx, int nt);
 cudaError_t launch_merges(const MergeArgs &m, const TotalsArgs &t, cudaStream_t st);

@@ -203,7 +203,7 @@ __global__ void points_kernel(const PointsArgs a, const RoundKeys rk) {
 }
 
 const ShapeKernels *find_shape(int nx, int nt) {
-    for (auto table : {shapes_small, shapes_config}) {
+    for (auto table : {shapes_small, shapes_config_a, shapes_config_b, shapes_config_c, shapes_config_d}) {
         int n = 0;
         const ShapeKernels *t = table(&n);
         for (int i = 0; i < n; ++i)
