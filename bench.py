@@ -84,11 +84,24 @@ def eval_ops_fp32(nx, nt):
     return d * r + 2 + 4 * k
 
 
+def rest_ops(nx, nt):
+    """Per survivor of stage 1 with Nt = 2: the rest of the action without the sites stage 1 summed (blocks 0
+    and BP-1 .. again, their points, the residuals of sites 0 and MC-1 .. Nx-1); other shapes screen in full."""
+    d = nx * nt
+    nq = (d + 3) // 4
+    bp = (3 * nq + 4) // 5
+    mc = min((4 * bp) // nt, nx)
+    if nt != 2 or bp < 2:
+        return screen_ops(nx, nt)
+    blocks = 2 + (nq - bp)
+    return blocks * 10 * 4 + 2 * 4 * blocks + 8 * (nx - mc + 2) * nt
+
+
 def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2, screened=None):
     """Algorithmic work of one launch against the binding resource.  'screened' (two-stage screen only): the
-    samples the full screen examined; every sample then costs partial_ops and those add screen_ops."""
+    samples that survived stage 1; every sample then costs partial_ops and those add rest_ops."""
     t = kern_ms * 1e-3
-    w_screen = n * screen_ops(nx, nt) if screened is None else n * partial_ops(nx, nt) + screened * screen_ops(nx, nt)
+    w_screen = n * screen_ops(nx, nt) if screened is None else n * partial_ops(nx, nt) + screened * rest_ops(nx, nt)
     if precision == "fp64":
         dp, integer = eval_ops_fp64(nx, nt)
         w_issue = w_screen + n_eval * integer
@@ -107,6 +120,7 @@ def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2, screened=None):
             "issue_frac": w_issue / t / ISSUE_PEAK_OPS, "fp64_frac": w_dp / t / FP64_PEAK_OPS,
             "screen_ops_per_sample": screen_ops(nx, nt),
             "partial_ops_per_sample": None if screened is None else partial_ops(nx, nt),
+            "survivor_ops": None if screened is None else rest_ops(nx, nt),
             "full_screened": n if screened is None else screened,
             "peak_source": "unit counts x 2070 MHz: 128 FP32/INT and 2 FP64 lanes per SM, 152 SMs"}
 

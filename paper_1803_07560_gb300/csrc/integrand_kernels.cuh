@@ -376,6 +376,54 @@ __device__ __forceinline__ float partial_action(uint32_t x, const PhiloxPrefix *
     }
 }
 
+// Stage 2 for NT = 2 without redrawing what stage 1 summed: a survivor's
+// partial action P comes with it through the queue, and the rest of S is the
+// residuals of sites 0 and MC-1 .. NX-1.  They need sites 0, 1 (block 0),
+// MC-2, MC-1 (block BP-1) and MC .. NX-1 (blocks BP ..), so the blocks
+// 1 .. BP-2 are not drawn again.  Slices 0 and 1 of a site form one f32x2
+// pair (the next slice is the swapped pair).  The mass term needs every
+// coordinate, so with mass2 != 0 the kernels screen survivors in full.
+template <int NX, int NT>
+struct RestScreen {
+    using PS = PartialScreen<NX, NT>;
+    static constexpr bool enabled = PS::enabled && NT == 2 && PS::BP >= 2;
+};
+
+template <int NX, int NT, typename Map>
+__device__ __forceinline__ float rest_action(uint32_t x, const PhiloxPrefix *pre, const RoundKeys &rk,
+                                             const float2 *box, const LatticeConst<float> &c) {
+    using PS = PartialScreen<NX, NT>;
+    if constexpr (!RestScreen<NX, NT>::enabled) {
+        return 0.f;  // never called: the kernels screen survivors in full
+    } else {
+        float2 P[NX];  // P[m] = (u[m, 0], u[m, 1]); only the sites drawn here are read
+#pragma unroll
+        for (int q = 0; q < PS::NQ; ++q) {
+            if (q == 0 || q >= PS::BP - 1) {
+                const uint4 b = philox_from_prefix(x, pre[q], rk);
+                P[2 * q] = make_float2(Map{}(b.x, box[4 * q]), Map{}(b.y, box[4 * q + 1]));
+                P[2 * q + 1] = make_float2(Map{}(b.z, box[4 * q + 2]), Map{}(b.w, box[4 * q + 3]));
+            }
+        }
+        const float2 cadv = make_float2(c.c_adv, c.c_adv), k1 = make_float2(c.k1, c.k1);
+        const float2 ncd = make_float2(c.neg_c_dif, c.neg_c_dif), m1 = make_float2(-1.f, -1.f);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < NX; ++m) {
+            if (m == 0 || m >= PS::MC - 1) {
+                const float2 here = P[m];
+                const float2 right = P[(m + 1) % NX];
+                const float2 left = P[(m + NX - 1) % NX];
+                const float2 t = __ffma2_rn(cadv, __ffma2_rn(m1, left, right), k1);
+                float2 R = __ffma2_rn(here, t, swap2(here));
+                R = __ffma2_rn(ncd, __fadd2_rn(right, left), R);
+                acc = __ffma2_rn(R, R, acc);
+            }
+        }
+        return (acc.x + acc.y) * c.inv_2Dtau;
+    }
+}
+
 // Running minimum shared across the CTA at fixed points of the sample loop:
 // every thread contributes, then every thread reads the same value, so the
 // decisions that depend on it do not depend on timing.  S >= 0, so the float
@@ -596,6 +644,34 @@ __device__ __forceinline__ int dequeue32(uint32_t *q, int count) {
     return count - 32;
 }
 
+// The same for a queue that carries a float beside each entry (a survivor
+// and its partial action).
+__device__ __forceinline__ int enqueue_pair(uint32_t *q, float *pq, int count, bool cand, uint32_t k, float p) {
+    const unsigned mask = __ballot_sync(0xffffffffu, cand);
+    if (mask == 0u) return count;
+    if (cand) {
+        const int at = count + __popc(mask & lanemask_lt());
+        q[at] = k;
+        pq[at] = p;
+    }
+    __syncwarp();
+    return count + __popc(mask);
+}
+
+__device__ __forceinline__ int dequeue32_pair(uint32_t *q, float *pq, int count) {
+    const int lane = threadIdx.x & 31;
+    const bool mv = lane + 32 < count;
+    const uint32_t moved = mv ? q[lane + 32] : 0u;
+    const float pmoved = mv ? pq[lane + 32] : 0.f;
+    __syncwarp();
+    if (mv) {
+        q[lane] = moved;
+        pq[lane] = pmoved;
+    }
+    __syncwarp();
+    return count - 32;
+}
+
 // ---------------------------------------------------------------------------
 // FP64 integrand, thread per sample.  One CTA processes chunks blockIdx.x,
 // blockIdx.x + gridDim.x, ...; within a chunk thread t screens samples
@@ -624,9 +700,11 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
     __shared__ double s_sums[K * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
     __shared__ uint32_t s_squeue[PartialScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];
+    __shared__ float s_pqueue[RestScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];  // survivors' partial actions
     const int tid = threadIdx.x, lane = tid & 31;
     uint32_t *queue = s_queue[tid >> 5];
     uint32_t *squeue = s_squeue[PartialScreen<NX, NT>::enabled ? tid >> 5 : 0];
+    float *pqueue = s_pqueue[RestScreen<NX, NT>::enabled ? tid >> 5 : 0];
     SmemSums<double, K, BLOCK> acc{s_sums + tid};
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
@@ -675,12 +753,16 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         float thr = m_ref + args.skip_window + 1.0f;
         // full screen of sample offset k (valid lanes) and the candidate queue
         unsigned n_full = 0;
-        auto screen = [&](uint32_t k, bool valid) {
+        // full screen of sample offset k (valid lanes), or with rest (warp-uniform) the survivor's partial
+        // action P_f plus the rest of S, then the candidate queue
+        const bool rest_ok = RestScreen<NX, NT>::enabled && lcf.half_mass2 == 0.f;
+        auto screen = [&](uint32_t k, bool valid, bool rest, float P_f) {
             bool cand = false;
             if (valid) {
                 ++n_full;
-                const float S_f = screen_action<NX, NT, MapScreen>(static_cast<uint32_t>(v.first + k), s_pre, rk,
-                                                                   s_box, lcf);
+                const uint32_t x = static_cast<uint32_t>(v.first + k);
+                const float S_f = rest ? P_f + rest_action<NX, NT, MapScreen>(x, s_pre, rk, s_box, lcf)
+                                       : screen_action<NX, NT, MapScreen>(x, s_pre, rk, s_box, lcf);
                 cand = __fmaf_rn(-1e-3f, S_f, S_f) <= thr;  // S_f <= m_ref + window + 1 + 0.1% of S_f
             }
             count = enqueue(queue, count, cand, k);
@@ -698,25 +780,36 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
             const uint64_t k = row * BLOCK + tid;
             if (two_stage) {
                 bool surv = false;
+                float P_f = 0.f;
                 if (k < v.cnt) {
-                    const float P_f = partial_action<NX, NT, MapScreen>(static_cast<uint32_t>(v.first + k), s_pre,
-                                                                        rk, s_box, lcf);
+                    P_f = partial_action<NX, NT, MapScreen>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box,
+                                                            lcf);
                     surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
                 }
-                scount = enqueue(squeue, scount, surv, static_cast<uint32_t>(k));
-                if (scount >= 32) {
-                    screen(squeue[lane], true);
-                    scount = dequeue32(squeue, scount);
+                if constexpr (RestScreen<NX, NT>::enabled) {
+                    scount = enqueue_pair(squeue, pqueue, scount, surv, static_cast<uint32_t>(k), P_f);
+                    if (scount >= 32) {
+                        screen(squeue[lane], true, rest_ok, pqueue[lane]);
+                        scount = dequeue32_pair(squeue, pqueue, scount);
+                    }
+                } else {
+                    scount = enqueue(squeue, scount, surv, static_cast<uint32_t>(k));
+                    if (scount >= 32) {
+                        screen(squeue[lane], true, false, 0.f);
+                        scount = dequeue32(squeue, scount);
+                    }
                 }
             } else {
-                screen(static_cast<uint32_t>(k), k < v.cnt);
+                screen(static_cast<uint32_t>(k), k < v.cnt, false, 0.f);
             }
             if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
                 share_min(&sh.min_bits, m_ref);
                 thr = m_ref + args.skip_window + 1.0f;
             }
         }
-        if (scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);  // survivors still queued
+        if (scount > 0)  // survivors still queued
+            screen(lane < scount ? squeue[lane] : 0u, lane < scount, rest_ok,
+                   RestScreen<NX, NT>::enabled && lane < scount ? pqueue[lane] : 0.f);
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
@@ -750,9 +843,11 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
     __shared__ float s_sums[Sums::WORDS * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
     __shared__ uint32_t s_squeue[PartialScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];
+    __shared__ float s_pqueue[RestScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];  // survivors' partial actions
     const int tid = threadIdx.x, lane = tid & 31;
     uint32_t *queue = s_queue[tid >> 5];
     uint32_t *squeue = s_squeue[PartialScreen<NX, NT>::enabled ? tid >> 5 : 0];
+    float *pqueue = s_pqueue[RestScreen<NX, NT>::enabled ? tid >> 5 : 0];
     Sums acc{s_sums + tid};
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
@@ -793,10 +888,15 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         // across the warp) and where the CTA shares it; thr follows it
         float thr = m_ref + args.skip_window;
         unsigned n_full = 0;
-        auto screen = [&](uint32_t k, bool valid) {
+        const bool rest_ok = RestScreen<NX, NT>::enabled && lc.half_mass2 == 0.f;
+        auto screen = [&](uint32_t k, bool valid, bool rest, float P_f) {
             n_full += valid ? 1u : 0u;
-            const bool cand =
-                valid && screen_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, lc) <= thr;
+            bool cand = false;
+            if (valid) {
+                const uint32_t x = static_cast<uint32_t>(v.first + k);
+                cand = (rest ? P_f + rest_action<NX, NT, MapF32>(x, s_pre, rk, s_box, lc)
+                             : screen_action<NX, NT, MapF32>(x, s_pre, rk, s_box, lc)) <= thr;
+            }
             count = enqueue(queue, count, cand, k);
             if (count >= 32) {
                 evaluate(queue[lane]);
@@ -812,25 +912,35 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
             const uint64_t k = row * BLOCK + tid;
             if (two_stage) {
                 bool surv = false;
+                float P_f = 0.f;
                 if (k < v.cnt) {  // 0.1% slack: the partial and full sums add in different orders
-                    const float P_f = partial_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk,
-                                                                     s_box, lc);
+                    P_f = partial_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, lc);
                     surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
                 }
-                scount = enqueue(squeue, scount, surv, static_cast<uint32_t>(k));
-                if (scount >= 32) {
-                    screen(squeue[lane], true);
-                    scount = dequeue32(squeue, scount);
+                if constexpr (RestScreen<NX, NT>::enabled) {
+                    scount = enqueue_pair(squeue, pqueue, scount, surv, static_cast<uint32_t>(k), P_f);
+                    if (scount >= 32) {
+                        screen(squeue[lane], true, rest_ok, pqueue[lane]);
+                        scount = dequeue32_pair(squeue, pqueue, scount);
+                    }
+                } else {
+                    scount = enqueue(squeue, scount, surv, static_cast<uint32_t>(k));
+                    if (scount >= 32) {
+                        screen(squeue[lane], true, false, 0.f);
+                        scount = dequeue32(squeue, scount);
+                    }
                 }
             } else {
-                screen(static_cast<uint32_t>(k), k < v.cnt);
+                screen(static_cast<uint32_t>(k), k < v.cnt, false, 0.f);
             }
             if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
                 share_min(&sh.min_bits, m_ref);
                 thr = m_ref + args.skip_window;
             }
         }
-        if (scount > 0) screen(lane < scount ? squeue[lane] : 0u, lane < scount);  // survivors still queued
+        if (scount > 0)  // survivors still queued
+            screen(lane < scount ? squeue[lane] : 0u, lane < scount, rest_ok,
+                   RestScreen<NX, NT>::enabled && lane < scount ? pqueue[lane] : 0.f);
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
