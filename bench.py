@@ -52,7 +52,7 @@ FP64_PEAK_OPS = 2 * SM_COUNT * SM_MAX_MHZ * 1e6      # FP64 operations/s
 # kernel, from ncu's dram__bytes_read.sum + dram__bytes_write.sum (a 1-pass
 # capture; profiles/integrand_f64_10x2.md).  Must be reset to None whenever
 # that kernel changes.
-TRAFFIC_FP64_10x2 = 510976
+TRAFFIC_FP64_10x2 = 525824
 
 
 def screen_ops(nx, nt):
