@@ -260,16 +260,19 @@ bfi_status bfi_plan_set_timing(bfi_plan *plan, int enable);
 bfi_status bfi_plan_get_stats(bfi_plan *plan, uint64_t *evaluated, float *skip_window);
 /* The two-stage screen of the box sampler's thread-per-sample kernels
  * (compiled shapes with at least 3 Philox blocks per sample whose first ~60%
- * cover at least 35% of the sites: 8x2, 10x2, 16x2, 32x2, 8x4, 10x4, 16x4).  Stage 1 draws the first ~60% of a sample's Philox blocks and sums
- * the squared residuals of the sites whose neighbours they cover: a partial
+ * cover at least 35% of the sites: 8x2, 10x2, 16x2, 32x2, 8x4, 10x4, 16x4).
+ * Stage 1 draws the first ~60% of a sample's Philox blocks and sums the
+ * squared residuals of the sites whose neighbours they cover: a partial
  * action P <= S of Eq. (Gen2).  A sample with P above the negligible-weight
- * threshold (with the screen's margin) cannot carry weight and is dropped;
- * the rest are screened with the full FP32 action.  Chunks of fewer than 256
- * samples per thread (jobs below about 2^27 samples) skip stage 1.  *two_stage is 1 when the last execution
- * used the kernel with the split, and *screened is then the number of samples
- * the full screen examined; otherwise *screened is the plan's total sample
- * count (every sample fully screened or evaluated).  Waits for the device.  Either pointer
- * may be NULL.  Errors: BFI_E_INVALID, BFI_E_CUDA. */
+ * threshold (with the screen's margin) cannot carry weight and is dropped.
+ * Stage 2 screens the rest with the full FP32 action (for Nt = 2 and
+ * mass2 = 0: P plus the residuals stage 1 left out).  Chunks of fewer than
+ * 256 samples per thread (jobs below about 2^27 samples) skip stage 1.
+ * *two_stage is 1 when the last execution used the kernel with the split, and
+ * *screened is then the number of samples stage 2 examined; otherwise
+ * *screened is the plan's total sample count (every sample fully screened or
+ * evaluated).  Waits for the device.  Either pointer may be NULL.
+ * Errors: BFI_E_INVALID, BFI_E_CUDA. */
 bfi_status bfi_plan_get_screen_stats(bfi_plan *plan, uint64_t *screened, int32_t *two_stage);
 bfi_status bfi_plan_get_timing(bfi_plan *plan, float *ms);
 

@@ -293,8 +293,9 @@ __device__ __forceinline__ float screen_action(uint32_t x, const PhiloxPrefix *p
 // computed like the full FP32 action on a subset of its non-negative terms,
 // so the screen's bound |S_f32 - S| <= 1 + 0.1% S holds for it too.  A sample
 // whose P already exceeds the threshold is rejected; the few that survive
-// (about a fifth at 10x2 over the box) are queued and screened in full, 32 at
-// a time, by stage 2.  BP is about 0.6 of the blocks.  The split is used where
+// (about a fifth at 10x2 over the box) are queued and screened 32 at a time
+// by stage 2: for NT = 2 the rest of the action added to P (rest_action),
+// otherwise the full screen.  BP is about 0.6 of the blocks.  The split is used where
 // the lattice has 3 or more blocks and stage 1 covers at least 35% of the
 // residual sites, but not all: measured on GB300, 4x4 (25%) and 6x2 (33%)
 // ran 5-16% slower with it and 6x4 (33%) no faster, while 8x4 (37.5%) and
