@@ -387,7 +387,7 @@ __device__ __forceinline__ float partial_action(uint32_t x, const PhiloxPrefix *
 template <int NX, int NT>
 struct RestScreen {
     using PS = PartialScreen<NX, NT>;
-    static constexpr bool enabled = PS::enabled && NT == 2 && PS::BP >= 2;
+    static constexpr bool enabled = PS::enabled && NT == 2 && NX % 2 == 0 && PS::BP >= 2;  // whole blocks of sites
 };
 
 template <int NX, int NT, typename Map>

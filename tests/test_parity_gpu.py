@@ -279,28 +279,30 @@ def test_paper_10x2_full_size_sampled(bfi, dev, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("D", [20.0, 1.0])
-def test_two_stage_screen_and_a_flat_action(bfi, dev, D, precision):
+@pytest.mark.parametrize("D,mass2", [(20.0, 0.0), (1.0, 0.0), (1.0, 0.5)])
+def test_two_stage_screen_and_a_flat_action(bfi, dev, D, mass2, precision):
     """10x2 with 16 subvolumes of 2^23 samples: chunks of 256 rows per
     thread, so the two-stage screen runs.  With the force variance D = 20
     the action is 20 times flatter and over 99% of the samples survive the
     partial action: the survivor queue carries nearly the whole chunk.  At
-    D = 1 about a seventh survive.  Either way the records of the first and
-    last subvolumes match the oracle's, and the totals are the oracle's merge
-    of all records."""
+    D = 1 about a seventh survive.  With mass2 = 0 stage 2 adds the rest of the
+    action to the survivor's partial one; the mass term needs every coordinate,
+    so with mass2 = 0.5 stage 2 screens in full.  In every case the records of
+    the first and last subvolumes match the oracle's, and the totals are the
+    oracle's merge of all records."""
     lo, hi = workloads.bisected_boxes(20, 4)
     job = workloads.Job(10, 2, lo, hi, np.full(16, 1 << 23, dtype=np.uint64), seed=9, D=D)
-    g_s, g_t, plan = run_gpu(bfi, dev, job, precision)
+    g_s, g_t, plan = run_gpu(bfi, dev, job, precision, mass2=mass2)
     assert plan.info().chunk_samples == 256 * 256
     n_eval, _ = plan.stats()
     full, two = plan.screen_stats()
     assert two and n_eval <= full <= job.total_samples
     if D > 1.0:
         assert full > 0.9 * job.total_samples
-    else:
+    elif mass2 == 0.0:  # the mass term, left out of P, lets more samples through
         assert full < 0.35 * job.total_samples
     pick = [0, 15]
-    o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision))
+    o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision), mass2=mass2)
     tol = FP64_RTOL if precision == 0 else FP32_RTOL
     assert_slots_close(g_s[pick], o_s, 6, tol, 1e-9 if precision == 0 else 1e-4)
     assert_totals_close(g_t, oracle.merge(10, g_s), 6, 1e-13, 1e-9)
