@@ -295,19 +295,22 @@ __device__ __forceinline__ float screen_action(uint32_t x, const PhiloxPrefix *p
 // whose P already exceeds the threshold is rejected; the few that survive
 // (about a fifth at 10x2 over the box) are queued and screened 32 at a time
 // by stage 2: for NT = 2 the rest of the action added to P (rest_action),
-// otherwise the full screen.  BP is about 0.6 of the blocks.  The split is used where
-// the lattice has 3 or more blocks and stage 1 covers at least 35% of the
-// residual sites, but not all: measured on GB300, 4x4 (25%) and 6x2 (33%)
-// ran 5-16% slower with it and 6x4 (33%) no faster, while 8x4 (37.5%) and
-// 10x2 (40%) ran 5-15% faster.
+// otherwise the full screen.  BP is about 0.6 of the blocks.
+//
+// The split is used where the lattice has 3 or more blocks and stage 1 covers
+// at least 35% of the residual sites, but not all: measured on GB300, 4x4
+// (25%) and 6x2 (33%) ran 5-16% slower with it and 6x4 (33%) no faster,
+// while 8x4 (37.5%) and 10x2 (40%) ran 5-15% faster.
+//
+// Chunks with fewer than kTwoStageMinRows rows per thread screen in one
+// stage: the survivor queue's final drain costs about one full-screen row per
+// warp, and the smaller jobs that get short chunks have less selective
+// references.  On the batching workload (256 jobs of 2^20-2^28 samples) a
+// threshold of 16 rows cost 4% against one stage, 64 rows 2%, 256 rows
+// nothing.  A per-warp switch back to one stage when too many samples
+// survive was measured and rejected: early in a chunk the reference action
+// is still high, and the switch fired on the 10x2 workload too.
 // ---------------------------------------------------------------------------
-// Chunks with fewer rows per thread screen in one stage: the survivor queue's
-// final drain costs about one full-screen row per warp, and the smaller jobs
-// that get short chunks have less selective references.  Measured on the
-// batching workload (256 jobs, 2^20-2^28 samples each): 16 rows cost 4%
-// against one stage, 64 rows 2%, 256 rows nothing.  (A per-warp switch back to one stage when too many
-// samples survive was measured and rejected: early in a chunk the reference
-// action is still high, and the switch fired on the 10x2 workload too.)
 #ifndef BFI_TWO_STAGE_MIN_ROWS
 #define BFI_TWO_STAGE_MIN_ROWS 256
 #endif
