@@ -55,7 +55,9 @@ struct LogProduct {
             p = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(p));
         }
     }
-    __device__ __forceinline__ double log_value() const { return fma(static_cast<double>(e), 0.6931471805599453, log(p)); }
+    __device__ __forceinline__ double log_value() const {
+        return fma(static_cast<double>(e), 0.6931471805599453, log(p));  // e ln 2 + ln p
+    }
 };
 
 // Compiled for one resident CTA per SM (all 255 registers a thread may
@@ -76,9 +78,8 @@ struct LogProduct {
 // m = +inf and zero sums.
 // ---------------------------------------------------------------------------
 template <int NX, int NT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1) transform_f64(const IntegrandArgs args,
-                                                                                         const LatticeConst<double> lc,
-                                                                                         const RoundKeys rk) {
+__global__ void __launch_bounds__(BLOCK, 1) transform_f64(const IntegrandArgs args, const LatticeConst<double> lc,
+                                                          const RoundKeys rk) {
     constexpr int D = NX * NT;
     constexpr int R = NX / 2 + 1;
     constexpr int K = sum_count(R);
