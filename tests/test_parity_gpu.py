@@ -281,7 +281,7 @@ def test_paper_10x2_full_size_sampled(bfi, dev, precision):
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("D,mass2", [(20.0, 0.0), (1.0, 0.0), (1.0, 0.5)])
 def test_two_stage_screen_and_a_flat_action(bfi, dev, D, mass2, precision):
-    """10x2 with 16 subvolumes of 2^23 samples: chunks of 256 rows per
+    """10x2 with 16 subvolumes of about 2^23 samples: chunks of 256 rows per
     thread, so the two-stage screen runs.  With the force variance D = 20
     the action is 20 times flatter and over 99% of the samples survive the
     partial action: the survivor queue carries nearly the whole chunk.  At
@@ -291,7 +291,9 @@ def test_two_stage_screen_and_a_flat_action(bfi, dev, D, mass2, precision):
     the first and last subvolumes match the oracle's, and the totals are the
     oracle's merge of all records."""
     lo, hi = workloads.bisected_boxes(20, 4)
-    job = workloads.Job(10, 2, lo, hi, np.full(16, 1 << 23, dtype=np.uint64), seed=9, D=D)
+    # 2^23 + 65436 samples per subvolume: 128 full chunks and a ragged one of 65436 (256 rows, the last short by
+    # 100 samples), which still runs in two stages
+    job = workloads.Job(10, 2, lo, hi, np.full(16, (1 << 23) + 65436, dtype=np.uint64), seed=9, D=D)
     g_s, g_t, plan = run_gpu(bfi, dev, job, precision, mass2=mass2)
     assert plan.info().chunk_samples == 256 * 256
     n_eval, _ = plan.stats()
