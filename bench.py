@@ -48,11 +48,34 @@ ISSUE_PEAK_OPS = 128 * SM_COUNT * SM_MAX_MHZ * 1e6   # thread-instructions/s (FP
 FP64_PEAK_OPS = 2 * SM_COUNT * SM_MAX_MHZ * 1e6      # FP64 operations/s
 
 
-# DRAM bytes (read + write) of one full-size launch of the FP64 10x2 integrand
-# kernel, from ncu's dram__bytes_read.sum + dram__bytes_write.sum (a 1-pass
-# capture; profiles/integrand_f64_10x2.md).  Must be reset to None whenever
-# that kernel changes.
-TRAFFIC_FP64_10x2 = 525824
+# DRAM traffic of the FP64 10x2 integrand launch comes from a committed ncu
+# summary that records the hash of the kernel sources it was measured on; the
+# bench reports it only while those sources are unchanged (else null).
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "integrand_f64_10x2_traffic.txt")
+KERNEL_SOURCES = ["bfi_device.cuh", "bfi_kernels.h", "integrand_kernels.cuh", "shapes_table.cuh", "shapes_small.cu"]
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1803_07560_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """(DRAM bytes read + written per full-size launch, note): the value of the
+    committed ncu summary when its kernel-source hash matches, else None."""
+    try:
+        fields = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line and not line.startswith("#"))
+    except OSError:
+        return None, "no committed traffic summary"
+    sha = fields.get("kernel_sources_sha256", "").strip()
+    if sha != kernel_sources_sha256():
+        return None, "kernel sources changed since the ncu traffic capture"
+    return int(fields["dram_bytes_per_launch"].strip()), "ncu dram__bytes_read.sum + dram__bytes_write.sum, " \
+        "one full-size launch (" + os.path.relpath(TRAFFIC_FILE, ROOT) + ")"
 
 
 def screen_ops(nx, nt):
@@ -97,11 +120,27 @@ def rest_ops(nx, nt):
     return blocks * 10 * 4 + 2 * 4 * blocks + 8 * (nx - mc + 2) * nt
 
 
-def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2, screened=None):
-    """Algorithmic work of one launch against the binding resource.  'screened' (two-stage screen only): the
-    samples that survived stage 1; every sample then costs partial_ops and those add rest_ops."""
+def screen_work(work, nx, nt):
+    """FP32/INT operations of the screen in one launch, from the counted work
+    (a dict with samples, stage1, survivors, full_screen): stage 1 for the
+    samples of two-stage chunks, the full screen for the others, and stage 2
+    (the rest of the action, or the full screen) for stage 1's survivors."""
+    rest = rest_ops(nx, nt) if work.get("rest_screen", 1) else screen_ops(nx, nt)
+    return (work["stage1"] * partial_ops(nx, nt) + work["full_screen"] * screen_ops(nx, nt) +
+            work["survivors"] * rest)
+
+
+def one_stage_work(n, n_eval=0):
+    """The work dict of a launch that screened every sample in one stage."""
+    return {"samples": n, "stage1": 0, "survivors": 0, "full_screen": n, "evaluated": n_eval, "rest_screen": 1}
+
+
+def roofline(work, kern_ms, precision, nx=10, nt=2):
+    """Algorithmic work of one launch (the counted work of bfi_plan_get_work)
+    against the binding resource."""
     t = kern_ms * 1e-3
-    w_screen = n * screen_ops(nx, nt) if screened is None else n * partial_ops(nx, nt) + screened * rest_ops(nx, nt)
+    n, n_eval = work["samples"], work["evaluated"]
+    w_screen = screen_work(work, nx, nt)
     if precision == "fp64":
         dp, integer = eval_ops_fp64(nx, nt)
         w_issue = w_screen + n_eval * integer
@@ -118,10 +157,10 @@ def roofline(n, n_eval, kern_ms, precision, nx=10, nt=2, screened=None):
             "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": achieved / peak,
             "traffic": None, "kernel_ms": kern_ms, "samples": n, "evaluated": n_eval,
             "issue_frac": w_issue / t / ISSUE_PEAK_OPS, "fp64_frac": w_dp / t / FP64_PEAK_OPS,
-            "screen_ops_per_sample": screen_ops(nx, nt),
-            "partial_ops_per_sample": None if screened is None else partial_ops(nx, nt),
-            "survivor_ops": None if screened is None else rest_ops(nx, nt),
-            "full_screened": n if screened is None else screened,
+            "screen_ops_per_sample": screen_ops(nx, nt), "partial_ops_per_sample": partial_ops(nx, nt),
+            "survivor_ops": rest_ops(nx, nt) if work.get("rest_screen", 1) else screen_ops(nx, nt),
+            "stage1_samples": work["stage1"], "survivors": work["survivors"],
+            "full_screened": work["full_screen"],
             "peak_source": "unit counts x 2070 MHz: 128 FP32/INT and 2 FP64 lanes per SM, 152 SMs"}
 
 
@@ -273,8 +312,7 @@ def timed_steps(plan, lo, hi, sid, job, steps, warmup, flush_buf, dist, stream):
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    full, two_stage = plan.screen_stats()
-    return total_ms / steps, kern_ms / steps, slots, totals, plan.stats()[0], (full if two_stage else None)
+    return total_ms / steps, kern_ms / steps, slots, totals, plan.work().as_dict()
 
 
 def run_bfi(args):
@@ -303,8 +341,8 @@ def run_bfi(args):
     plan = bfi.Plan(lat, job.samples, bfi.FP64, device=local_rank)
     info = plan.info()
     sampler = ClockSampler(local_rank) if rank == 0 else None
-    ms, kern_ms, slots, totals, n_eval, n_full = timed_steps(plan, lo, hi, sid, job, args.steps, args.warmup,
-                                                     flush_buf, dist, stream)
+    ms, kern_ms, slots, totals, work = timed_steps(plan, lo, hi, sid, job, args.steps, args.warmup, flush_buf, dist,
+                                                   stream)
     clocks = sampler.stop() if sampler else None
 
     # the exchange: gather every rank's subvolume records, merge in FP64
@@ -319,19 +357,19 @@ def run_bfi(args):
 
     samples_all = world * job.total_samples
     value = samples_all / (ms * 1e-3)
-    roof = roofline(job.total_samples, n_eval, kern_ms, "fp64", NX, NT, screened=n_full)
+    roof = roofline(work, kern_ms, "fp64", NX, NT)
     roof["kernel"] = f"hint + integrand FP64 <{NX},{NT}>"
     if (NX, NT) == (10, 2) and args.samples_log2 == 20:
-        roof["traffic"] = TRAFFIC_FP64_10x2
+        roof["traffic"], roof["traffic_source"] = measured_traffic()
 
     # ---- FP32 form of the same job with 2^24 points per subvolume ----
     fp32 = None
     if not args.skip_fp32:
         job32 = make_job(rank, world, 1 << (args.samples_log2 + 4))
         plan32 = bfi.Plan(lat, job32.samples, bfi.FP32, device=local_rank)
-        ms32, kern32, _, tot32, n_eval32, n_full32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
-                                                       max(1, args.warmup // 2), flush_buf, dist, stream)
-        roof32 = roofline(job32.total_samples, n_eval32, kern32, "fp32", NX, NT, screened=n_full32)
+        ms32, kern32, _, tot32, work32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
+                                                     max(1, args.warmup // 2), flush_buf, dist, stream)
+        roof32 = roofline(work32, kern32, "fp32", NX, NT)
         roof32["kernel"] = f"hint + integrand FP32 <{NX},{NT}>"
         plan32.close()
         # the same 2^34-point job in FP64 mode (its own FP64 points): the FP32
@@ -449,11 +487,30 @@ def run_batch(bfi, dev, stream, njobs=256):
     shapes = sorted({(j.nx, j.nt) for j in jobs})
     tuned = {f"{nx}x{nt}": bfi.autotune_grid(bfi.lattice(nx, nt), bfi.FP32) for nx, nt in shapes}
     ok = all(bool(torch.isfinite(t[0]).item()) for t in b.totals)
+    # the ops-weighted roofline of one replay: every job's counted work (its own screen, stage-1 and evaluation
+    # counts) over the replay time, against the FP32/INT issue peak
+    issue, by_shape = 0.0, {}
+    for k, j in enumerate(jobs):
+        w = b.work(k).as_dict()
+        ops = screen_work(w, j.nx, j.nt) + w["evaluated"] * eval_ops_fp32(j.nx, j.nt)
+        issue += ops
+        key = f"{j.nx}x{j.nt}"
+        acc = by_shape.setdefault(key, {"jobs": 0, "samples": 0, "Gops": 0.0, "stage1": 0})
+        acc["jobs"] += 1
+        acc["samples"] += w["samples"]
+        acc["Gops"] += ops / 1e9
+        acc["stage1"] += w["stage1"]
     b.close()
+    achieved = issue / (ms * 1e-3)
+    roof = {"bound": "alu", "resource": "FP32/INT issue", "achieved": achieved / 1e9, "peak": ISSUE_PEAK_OPS / 1e9,
+            "unit": "Gop/s", "frac": achieved / ISSUE_PEAK_OPS, "ops": issue,
+            "note": "each job's counted work (screen, stage 1 and survivors, FP32 evaluations) summed over the "
+                    "256 jobs, over the graph replay time (hint, integrand and merges of every job)"}
     return {"workload": f"{njobs} jobs, Nx in {{4,6,8,10,16,32}}, Nt in {{2,4}}, nu log-uniform [0.1,10], "
                         "64-1024 subvolumes, 2^20-2^28 points (seed 3), FP32 eval / FP64 merge, one CUDA graph",
             "value": samples / (ms * 1e-3), "unit": "samples/s", "ms_per_launch": ms, "samples": samples,
-            "jobs": njobs, "graph_create_s": create_s, "ctas_per_sm": tuned, "all_finite": ok}
+            "jobs": njobs, "graph_create_s": create_s, "ctas_per_sm": tuned, "all_finite": ok, "roofline": roof,
+            "by_shape": by_shape}
 
 
 def run_time_to_error(bfi, dev, stream, log2_budgets=range(10, 25, 2), target=1e-3):
@@ -724,14 +781,16 @@ def run_serving(bfi, seconds, rate=200.0, seed=5):
         delay = t0 + t_next - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        reqs.append(srv.submit(bfi.lattice(job.nx, job.nt, job.nu, job.D, job.a, job.tau), job.lo, job.hi,
-                               job.samples, job.seed, job.job_id))
+        reqs.append((srv.submit(bfi.lattice(job.nx, job.nt, job.nu, job.D, job.a, job.tau), job.lo, job.hi,
+                                job.samples, job.seed, job.job_id), job))
         offered += job.total_samples
     t_submit_end = time.perf_counter()
-    infos = []
-    for r in reqs:
+    infos, issue = [], 0.0
+    for r, job in reqs:
         r.wait(600_000)
         infos.append(r.info())
+        w = r.work().as_dict()
+        issue += screen_work(w, job.nx, job.nt) + w["evaluated"] * eval_ops_fp32(job.nx, job.nt)
         r.release()
     t_end = time.perf_counter()
     lat = np.array([i.latency_ms for i in infos])
@@ -740,12 +799,16 @@ def run_serving(bfi, seconds, rate=200.0, seed=5):
     srv.close()
     return {"workload": f"Poisson {rate:g} jobs/s for {seconds:g} s, batching sizes + 5% 64x8 (seed 5), FP32, "
                         "8 slots, 40 GB budget, split at Var(Z_s)/Z_s^2 > 1e-2 (1 round)",
-            "jobs": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "rate": rate, "jobs": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "samples_per_s": samples / (t_end - t0), "samples": samples,
             "offered_samples_per_s_first_pass": offered / (t_submit_end - t0),
             "wall_s": t_end - t0, "passes": int(sum(i.passes for i in infos)),
             "leaves": int(sum(i.nsub_final for i in infos)), "completed": int(st.completed),
-            "failed": int(st.failed), "peak_device_bytes": int(st.bytes_peak)}
+            "failed": int(st.failed), "peak_device_bytes": int(st.bytes_peak),
+            "roofline": {"bound": "alu", "resource": "FP32/INT issue", "achieved": issue / (t_end - t0) / 1e9,
+                         "peak": ISSUE_PEAK_OPS / 1e9, "unit": "Gop/s", "frac": issue / (t_end - t0) / ISSUE_PEAK_OPS,
+                         "note": "every pass's counted work (screen, stage 1 and survivors, FP32 evaluations) "
+                                 "over the wall time from the first submission to the last result"}}
 
 
 def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, fp32, job, batch=None,
@@ -772,7 +835,40 @@ def report(args, rank, world, value, ms, roof, cpu, e2e, clocks, info, merged, f
             "time_to_error": tte,
             "next_rows": next_rows,
         }
+        line["summary"] = summary(value, roof, e2e, fp32, batch, serving, tte)
         print(json.dumps(line), flush=True)
+
+
+def _sig(x, digits=4):
+    return None if x is None else float(f"{x:.{digits}g}")
+
+
+def summary(value, roof, e2e, fp32, batch, serving, tte):
+    """The figures of every workload in a few hundred characters, last in the
+    line: config 2 (FP64), config 3 (FP32 at 2^34 points), config 4 (the
+    batch), config 5 (serving) and the time to a 1e-3 stated error."""
+    out = {"fp64_samples_per_s": _sig(value), "fp64_frac": _sig(roof["frac"], 3),
+           "e2e_samples_per_s": _sig(e2e["value"]) if e2e else None}
+    if fp32:
+        out.update({"fp32_samples_per_s": _sig(fp32["value"]), "fp32_frac": _sig(fp32["roofline"]["frac"], 3),
+                    "fp32_vs_fp64_Z_rel": _sig(fp32["vs_fp64_mode"]["Z_rel"], 3),
+                    "fp32_vs_fp64_C_rel_max": _sig(max(abs(x) for x in fp32["vs_fp64_mode"]["C_rel_to_C0"]), 3)})
+        if "err_bound" in fp32:
+            out.update({"fp32_err_bound_Z": _sig(fp32["err_bound"]["Z_rel"], 3),
+                        "fp32_err_bound_C": _sig(max(fp32["err_bound"]["C_rel_to_C0"]), 3)})
+    if batch:
+        out.update({"batch_samples_per_s": _sig(batch["value"]), "batch_frac": _sig(batch["roofline"]["frac"], 3),
+                    "batch_ms": _sig(batch["ms_per_launch"])})
+    if serving:
+        out.update({"serving_rate": serving.get("rate"), "serving_jobs": serving["jobs"],
+                    "serving_p50_ms": _sig(serving["p50_ms"]), "serving_p99_ms": _sig(serving["p99_ms"]),
+                    "serving_samples_per_s": _sig(serving["samples_per_s"]), "serving_failed": serving["failed"]})
+        if "roofline" in serving:
+            out["serving_frac"] = _sig(serving["roofline"]["frac"], 3)
+    if tte:
+        out.update({"tte_samples_to_1e-3_C0": _sig(tte["samples_to_target_C_err_over_C0_max"], 3),
+                    "tte_seconds_to_1e-3_C0": _sig(tte["seconds_to_target_C_err_over_C0_max"], 3)})
+    return out
 
 
 def main():

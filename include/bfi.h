@@ -196,12 +196,6 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi,
  * chunk only), only the speed.  Errors: BFI_E_INVALID. */
 bfi_status bfi_plan_set_grid(bfi_plan *plan, int32_t ctas_per_sm);
 
-/* Per-stage timing of bfi_plan_execute with CUDA events recorded on the
- * execution stream.  After bfi_plan_set_timing(plan, 1), each execution
- * records events around its integrand kernel and around its merge kernels;
- * bfi_plan_get_timing waits for the last execution's events and writes
- * ms[0] = integrand kernel, ms[1] = merges (milliseconds).  Off by default.
- * Errors: BFI_E_INVALID (NULL, or no timed execution yet), BFI_E_CUDA. */
 /* Samplers: how the unit point u (from Philox, see Conventions) becomes the
  * field v.  The box sampler (the default) takes v uniform in each box.  The
  * other two run in FP64 only (the FP32 screen's error bound does not hold
@@ -252,7 +246,6 @@ bfi_status bfi_plan_set_sampler(bfi_plan *plan, const bfi_sampler *sampler);
  * (d > 64). */
 bfi_status bfi_gaussian_proposal(const bfi_lattice *lattice, double zero_mode_sigma, double *factor);
 
-bfi_status bfi_plan_set_timing(bfi_plan *plan, int enable);
 /* Samples fully evaluated (point, action, products, weight) by the last
  * execution, and the plan's negligible-weight window (see "Negligible
  * weights").  Waits for the device.  Either pointer may be NULL.
@@ -268,12 +261,42 @@ bfi_status bfi_plan_get_stats(bfi_plan *plan, uint64_t *evaluated, float *skip_w
  * Stage 2 screens the rest with the full FP32 action (for Nt = 2 and
  * mass2 = 0: P plus the residuals stage 1 left out).  Chunks of fewer than
  * 256 samples per thread (jobs below about 2^27 samples) skip stage 1.
- * *two_stage is 1 when the last execution used the kernel with the split, and
- * *screened is then the number of samples stage 2 examined; otherwise
- * *screened is the plan's total sample count (every sample fully screened or
- * evaluated).  Waits for the device.  Either pointer may be NULL.
- * Errors: BFI_E_INVALID, BFI_E_CUDA. */
+ * *two_stage is 1 when the last execution ran stage 1 on at least one chunk,
+ * and *screened is then the number of samples the full screen or stage 2
+ * examined; otherwise *screened is the plan's total sample count (every
+ * sample fully screened or evaluated).  Waits for the device.  Either
+ * pointer may be NULL.  Errors: BFI_E_INVALID, BFI_E_CUDA. */
 bfi_status bfi_plan_get_screen_stats(bfi_plan *plan, uint64_t *screened, int32_t *two_stage);
+
+/* The work the last execution did, sample by sample, for accounting (the
+ * algorithmic operations of each part are fixed per sample, so these counts
+ * give the work of the launch):
+ *   samples      the plan's budget: every sample's Philox words are drawn
+ *   stage1       samples of chunks that ran stage 1 of the two-stage screen
+ *   survivors    of those, the samples stage 1 let through to stage 2
+ *   full_screen  samples screened in one stage with the full FP32 action
+ *                (samples = stage1 + full_screen for the box sampler)
+ *   evaluated    samples fully evaluated (point, action, products, weight;
+ *                for the TRANSFORM and GAUSSIAN samplers, which have no
+ *                screen, every sample whose weight was computed)
+ *   two_stage_shape  1 when the shape's kernels have the split compiled in
+ *   rest_screen      1 when stage 2 adds the rest of the action to P (Nt = 2,
+ *                    mass2 = 0), 0 when it screens survivors in full
+ * Waits for the device.  Errors: BFI_E_INVALID, BFI_E_CUDA. */
+typedef struct {
+    uint64_t samples, stage1, survivors, full_screen, evaluated;
+    int32_t two_stage_shape, rest_screen;
+} bfi_work;
+
+bfi_status bfi_plan_get_work(bfi_plan *plan, bfi_work *work);
+
+/* Per-stage timing of bfi_plan_execute with CUDA events recorded on the
+ * execution stream.  After bfi_plan_set_timing(plan, 1), each execution
+ * records events around its integrand kernel and around its merge kernels;
+ * bfi_plan_get_timing waits for the last execution's events and writes
+ * ms[0] = integrand kernel, ms[1] = merges (milliseconds).  Off by default.
+ * Errors: BFI_E_INVALID (NULL, or no timed execution yet), BFI_E_CUDA. */
+bfi_status bfi_plan_set_timing(bfi_plan *plan, int enable);
 bfi_status bfi_plan_get_timing(bfi_plan *plan, float *ms);
 
 /* The whole integration without allocating anything, for callers that
@@ -283,15 +306,19 @@ bfi_status bfi_plan_get_timing(bfi_plan *plan, float *ms);
  * start-up.  The paper has no counterpart; this is a deployment variant of
  * bfi_plan_create + bfi_plan_execute + bfi_plan_destroy with the same kernels,
  * chunking and results.
- *   samples          host [nsub]; keep it unchanged until 'stream' has passed
- *                    the call (pageable memory is copied before the call returns)
+ *   samples          host [nsub]; the budgets reach the device by a
+ *                    cudaMemcpyAsync from this array on 'stream': keep it
+ *                    unchanged until 'stream' has passed the call (pageable
+ *                    memory is copied before the call returns)
  *   lo, hi, sub_id, seed, job_id, slots, totals   as for bfi_plan_execute
  *   stream           cudaStream_t of the current device
  * The scratch is one 16 MiB device array that every device that loads the
  * library holds until the process exits; a job whose chunk records, chunk
  * table, hints and merge factors need more is rejected with BFI_E_INVALID and a message
  * giving both sizes.  The first call on a device looks up the array's device
- * address (once per device); make that first call before any stream capture.
+ * address (once per device, kept for the process); make that first call
+ * before any stream capture, and do not use the entry point across a
+ * cudaDeviceReset of the device.
  * Every call uses the same array and leaves its contents behind; each call
  * clears what has to start at zero.  Calls whose work overlaps on the GPU
  * (other streams, other threads) race on the array: serialise them.
@@ -332,6 +359,10 @@ bfi_status bfi_batch_create(bfi_batch **out, const bfi_job *jobs, int32_t njobs,
                             int device, int32_t nstreams, int32_t autotune);
 /* Replays the graph on 'stream' (asynchronous). */
 bfi_status bfi_batch_launch(bfi_batch *batch, void *stream);
+/* The work job 'job' (0-based, in the order given to bfi_batch_create) did in
+ * the last replay, as bfi_plan_get_work counts it.  Waits for the device.
+ * Errors: BFI_E_INVALID, BFI_E_CUDA. */
+bfi_status bfi_batch_get_work(bfi_batch *batch, int32_t job, bfi_work *work);
 bfi_status bfi_batch_destroy(bfi_batch *batch);
 
 /* Autotuner of the persistent grid: times the integrand of a synthetic job of
@@ -389,9 +420,39 @@ typedef struct {
 
 /* Errors: BFI_E_INVALID, BFI_E_CUDA (no such device, stream or pool creation). */
 bfi_status bfi_server_create(bfi_server **out, const bfi_server_config *config);
-/* Cancels queued jobs, waits for running passes, stops the scheduler.  Release
- * every request handle of the server before destroying it. */
+/* Stops admitting passes, cancels queued jobs and waits at most timeout_ms
+ * (< 0: no limit) for the running passes to end and the scheduler to stop.
+ * Passes wait on nothing but their own kernels, so they end; the limit is
+ * for callers that must not block.  BFI_OK when stopped, BFI_E_TIMEOUT if
+ * passes were still running (call it again, or destroy). */
+bfi_status bfi_server_shutdown(bfi_server *server, int64_t timeout_ms);
+/* bfi_server_shutdown without a limit, then frees the server (its streams
+ * synchronised first).  Release every request handle of the server before
+ * destroying it. */
 bfi_status bfi_server_destroy(bfi_server *server);
+
+/* Failure handling.  A pass that fails after admission fails its job alone,
+ * with a status and a message, and its memory returns to the budget:
+ *   - its device allocation from the pool fails: BFI_E_NOMEM;
+ *   - a launch or copy fails: BFI_E_CUDA (what was enqueued is drained);
+ *   - the stream reports an error when the pass completes, or while it is in
+ *     flight (polled by the scheduler): BFI_E_CUDA, its records are not read.
+ * If the scheduler thread itself stops on an error (a failed host
+ * allocation), every queued and running job fails with BFI_E_NOMEM, waits
+ * return, and bfi_submit answers BFI_E_BUSY.  bfi_server_inject_fault makes
+ * one of these happen on the host, for tests of this path: the nth pass
+ * (0-based, counting from the call) to reach 'point' fails there as if the
+ * CUDA call had returned an error (no device work fails).  One fault at a
+ * time; BFI_FAULT_NONE clears it.  Errors: BFI_E_INVALID. */
+typedef enum {
+    BFI_FAULT_NONE = 0,
+    BFI_FAULT_POOL_ALLOC = 1,   /* the pass's device allocation */
+    BFI_FAULT_LAUNCH = 2,       /* a launch of the pass (its merges) */
+    BFI_FAULT_COMPLETION = 3,   /* the stream status read when the pass completes */
+    BFI_FAULT_SCHEDULER = 4     /* the scheduler thread, after a pass completes */
+} bfi_fault_point;
+
+bfi_status bfi_server_inject_fault(bfi_server *server, int32_t point, int64_t nth);
 bfi_status bfi_server_get_stats(bfi_server *server, bfi_server_stats *stats);
 
 /* Queues a job; host arrays (lo, hi [nsub * d], samples [nsub]) are copied
@@ -415,6 +476,10 @@ bfi_status bfi_request_get_info(bfi_request *request, bfi_request_info *info);
  * done), BFI_E_CANCELLED, the failure status. */
 bfi_status bfi_request_get_result(bfi_request *request, double *totals, double *slots, double *lo, double *hi,
                                   uint32_t *sub_id);
+/* The counted work (as bfi_plan_get_work counts it) of every pass of the
+ * request that has completed so far, split parents included.
+ * Errors: BFI_E_INVALID. */
+bfi_status bfi_request_get_work(bfi_request *request, bfi_work *work);
 /* Drops the caller's handle (a job still queued or running is cancelled). */
 bfi_status bfi_request_release(bfi_request *request);
 
@@ -545,6 +610,32 @@ bfi_status bfi_adaptive_integrate(bfi_ctx *ctx, const bfi_lattice *lattice, cons
  * several executions, devices or processes (Sec. 1: the integral over a
  * region is the sum of the integrals over its parts).  Errors: BFI_E_INVALID. */
 bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double *totals);
+
+/* ------------------------------------------------------------------------ */
+/* Stated arithmetic error of a result.                                     */
+/* ------------------------------------------------------------------------ */
+
+/* A bound on the arithmetic error of one result of the box sampler: how far
+ * its Z and C(r) can lie from the same Monte Carlo estimator (Sec. 3: V mean f
+ * over each subvolume, summed) evaluated in exact arithmetic on the same
+ * points -- in BFI_FP32 the same float points -- including the
+ * negligible-weight truncation.  It adds up first-order rounding bounds of
+ * each step of the path in the given precision: the action of Eq. (Gen2), the
+ * weight (with the documented accuracy of CUDA's exp and expf), the products
+ * P_r, the per-thread sums and the FP64 merges.  The statistical error (totals
+ * [1] and [4 + R + r]) is separate and usually far larger.
+ *   lattice, precision   those the result was computed with
+ *   nsub, slots          host [nsub * bfi_slot_len(nx)]: the result's
+ *                        subvolume records (their shifts and budgets enter)
+ *   vmax                 the largest |coordinate| of any subvolume box (5 for
+ *                        boxes inside [-5, 5]^d)
+ *   bound                host [1 + R] out: bound[0] on |dZ| / Z, bound[1 + r]
+ *                        on |dC(r)| / C(0)
+ * In BFI_FP32 the bound is below 1e-6 for the lattices and boxes of the
+ * workloads.  Errors: BFI_E_INVALID (bad arguments, records without
+ * weight). */
+bfi_status bfi_error_bound(const bfi_lattice *lattice, bfi_precision precision, int64_t nsub, const double *slots,
+                           double vmax, double *bound);
 
 /* ------------------------------------------------------------------------ */
 /* Single steps of the path, for step-by-step checks.                        */

@@ -48,6 +48,16 @@ class PlanInfo(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32)]
 
 
+class Work(ctypes.Structure):
+    """Work of the last execution, sample by sample (bfi_work)."""
+    _fields_ = [("samples", ctypes.c_uint64), ("stage1", ctypes.c_uint64), ("survivors", ctypes.c_uint64),
+                ("full_screen", ctypes.c_uint64), ("evaluated", ctypes.c_uint64),
+                ("two_stage_shape", ctypes.c_int32), ("rest_screen", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32), ("memory_budget", ctypes.c_uint64),
                 ("precision", ctypes.c_int), ("split_rel_var", ctypes.c_double),
@@ -76,6 +86,7 @@ class Job(ctypes.Structure):
 
 
 SAMPLE_BOX, SAMPLE_TRANSFORM, SAMPLE_GAUSSIAN = 0, 1, 2
+FAULT_NONE, FAULT_POOL_ALLOC, FAULT_LAUNCH, FAULT_COMPLETION, FAULT_SCHEDULER = 0, 1, 2, 3, 4
 
 
 class Sampler(ctypes.Structure):
@@ -149,11 +160,15 @@ _SIGNATURES = {
     "bfi_plan_get_timing": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "bfi_plan_get_stats": (ctypes.c_int, [_vp, _P(ctypes.c_uint64), _P(ctypes.c_float)]),
     "bfi_plan_get_screen_stats": (ctypes.c_int, [_vp, _P(ctypes.c_uint64), _P(ctypes.c_int32)]),
+    "bfi_plan_get_work": (ctypes.c_int, [_vp, _P(Work)]),
+    "bfi_batch_get_work": (ctypes.c_int, [_vp, ctypes.c_int32, _P(Work)]),
     "bfi_integrate_static_scratch": (ctypes.c_int, [_P(Lattice), ctypes.c_int64, _P(ctypes.c_uint64), _vp,
                                                     _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
                                                     _vp, _vp, _vp]),
     "bfi_server_create": (ctypes.c_int, [_P(_vp), _P(ServerConfig)]),
     "bfi_server_destroy": (ctypes.c_int, [_vp]),
+    "bfi_server_shutdown": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "bfi_server_inject_fault": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64]),
     "bfi_server_get_stats": (ctypes.c_int, [_vp, _P(ServerStats)]),
     "bfi_submit": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, ctypes.c_uint32,
                                   ctypes.c_uint32, _P(_vp)]),
@@ -163,6 +178,7 @@ _SIGNATURES = {
     "bfi_request_get_info": (ctypes.c_int, [_vp, _P(RequestInfo)]),
     "bfi_request_get_result": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "bfi_request_release": (ctypes.c_int, [_vp]),
+    "bfi_request_get_work": (ctypes.c_int, [_vp, _P(Work)]),
     "bfi_nsphere": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, _P(ctypes.c_double), _P(ctypes.c_double),
                                    _P(ctypes.c_int32), ctypes.c_int]),
@@ -180,6 +196,7 @@ _SIGNATURES = {
     "bfi_integrate": (ctypes.c_int, [_vp, _P(Lattice), ctypes.c_int64, _vp, _vp, _vp, _vp,
                                      ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _vp, _vp]),
     "bfi_merge_host": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp]),
+    "bfi_error_bound": (ctypes.c_int, [_P(Lattice), ctypes.c_int, ctypes.c_int64, _vp, ctypes.c_double, _vp]),
     "bfi_points": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32,
                                   ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
                                   _vp, _vp]),
@@ -306,12 +323,19 @@ class Plan:
         return int(n.value), float(w.value)
 
     def screen_stats(self):
-        """(samples the full FP32 screen examined in the last execution,
-        whether the two-stage screen ran); see bfi_plan_get_screen_stats."""
+        """(samples the full FP32 screen or stage 2 examined in the last
+        execution, whether stage 1 of the two-stage screen ran on any chunk);
+        see bfi_plan_get_screen_stats."""
         n = ctypes.c_uint64()
         two = ctypes.c_int32()
         _check(_lib.bfi_plan_get_screen_stats(self._h, ctypes.byref(n), ctypes.byref(two)))
         return int(n.value), bool(two.value)
+
+    def work(self) -> Work:
+        """Work of the last execution, sample by sample (bfi_plan_get_work)."""
+        w = Work()
+        _check(_lib.bfi_plan_get_work(self._h, ctypes.byref(w)))
+        return w
 
     def close(self):
         if getattr(self, "_h", None):
@@ -468,6 +492,12 @@ class Batch:
     def launch(self, stream=None):
         _check(_lib.bfi_batch_launch(self._h, _stream_ptr(stream)))
 
+    def work(self, job: int) -> Work:
+        """Work of job 'job' in the last replay (bfi_batch_get_work)."""
+        w = Work()
+        _check(_lib.bfi_batch_get_work(self._h, job, ctypes.byref(w)))
+        return w
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.bfi_batch_destroy(self._h)
@@ -499,6 +529,12 @@ class Request:
 
     def cancel(self):
         _check(_lib.bfi_cancel(self._h))
+
+    def work(self) -> Work:
+        """Counted work of the request's completed passes (bfi_request_get_work)."""
+        w = Work()
+        _check(_lib.bfi_request_get_work(self._h, ctypes.byref(w)))
+        return w
 
     def info(self) -> RequestInfo:
         info = RequestInfo()
@@ -565,6 +601,15 @@ class Server:
         _check(_lib.bfi_server_get_stats(self._h, ctypes.byref(st)))
         return st
 
+    def shutdown(self, timeout_ms: int = -1):
+        """Stop admitting, cancel queued jobs, wait at most timeout_ms for
+        running passes (raises BfiError with BFI_E_TIMEOUT if they run on)."""
+        _check(_lib.bfi_server_shutdown(self._h, int(timeout_ms)))
+
+    def inject_fault(self, point: int, nth: int = 0):
+        """Host-side fault for tests of the failure path (bfi_server_inject_fault)."""
+        _check(_lib.bfi_server_inject_fault(self._h, int(point), int(nth)))
+
     def close(self):
         if getattr(self, "_h", None):
             for r in self._requests:
@@ -606,6 +651,19 @@ def merge_host(nx: int, slots) -> np.ndarray:
     s_a, s_p = _host(np.reshape(slots, (-1, slot_len(nx))), np.float64)
     out = np.empty(totals_len(nx))
     _check(_lib.bfi_merge_host(nx, s_a.shape[0], s_p, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def error_bound(lat: Lattice, precision: int, slots, vmax: float) -> np.ndarray:
+    """Stated arithmetic error of a result from its subvolume records (host
+    array or CUDA tensor [nsub, slot_len]): [bound on |dZ|/Z, bound on
+    |dC(r)|/C(0) for r = 0..R-1]; see bfi_error_bound."""
+    if hasattr(slots, "cpu"):
+        slots = slots.cpu().numpy()
+    s_a, s_p = _host(np.reshape(slots, (-1, slot_len(lat.nx))), np.float64)
+    out = np.empty(1 + num_r(lat.nx))
+    _check(_lib.bfi_error_bound(ctypes.byref(lat), precision, s_a.shape[0], s_p, float(vmax),
+                                ctypes.c_void_p(out.ctypes.data)))
     return out
 
 

@@ -215,10 +215,10 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
     const size_t smp_bytes = sizeof(uint64_t) * nsub;
     const size_t par_bytes = sizeof(double) * static_cast<size_t>(std::max<int64_t>(p->nchunks, 1)) * (p->K + 2);
     const size_t hint_bytes = sizeof(float) * nsub;
-    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + 2 * sizeof(unsigned long long) + sizeof(double) * 2 * nsub;
+    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + 3 * sizeof(unsigned long long) + sizeof(double) * 2 * nsub;
     if (cudaMalloc(&p->d_chunk_off, off_bytes) != cudaSuccess || cudaMalloc(&p->d_samples, smp_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_partials, par_bytes) != cudaSuccess || cudaMalloc(&p->d_hint, hint_bytes) != cudaSuccess ||
-        cudaMalloc(&p->d_stats, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&p->d_stats, 3 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&p->d_fbuf, sizeof(double) * 2 * nsub) != cudaSuccess) {
         cudaGetLastError();
         bfi_plan_destroy(p);
@@ -259,11 +259,11 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
     if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device: %s", cudaGetErrorString(g.err));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[0], st));
-    BFI_CUDA(cudaMemsetAsync(plan->d_stats, 0, 2 * sizeof(unsigned long long), st));
+    BFI_CUDA(cudaMemsetAsync(plan->d_stats, 0, 3 * sizeof(unsigned long long), st));
     if (plan->nchunks > 0) {
         bfi::IntegrandArgs a{lo,           hi,           sub_id,        plan->d_samples,     plan->d_chunk_off,
                              plan->d_partials, plan->d_hint, plan->d_stats, plan->nsub, plan->nchunks,
-                             plan->chunk_samples, plan->skip_window, plan->d_stats + 1};
+                             plan->chunk_samples, plan->skip_window, plan->d_stats + 1, plan->d_stats + 2};
         if (plan->sampler == BFI_SAMPLE_BOX) {
             BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
         } else if (plan->sampler == BFI_SAMPLE_TRANSFORM && plan->shape->transform) {
@@ -456,20 +456,47 @@ bfi_status bfi_plan_get_stats(bfi_plan *plan, uint64_t *evaluated, float *skip_w
     return BFI_OK;
 }
 
+// Counters of the last execution: [0] evaluated, [1] samples the full screen
+// examined (kernels with the split compiled in), [2] samples of chunks that
+// ran stage 1.
+static bfi_status read_counters(bfi_plan *plan, unsigned long long (&c)[3]) {
+    DeviceGuard g(plan->device);
+    BFI_CUDA(cudaMemcpy(c, plan->d_stats, sizeof c, cudaMemcpyDeviceToHost));
+    return BFI_OK;
+}
+
 bfi_status bfi_plan_get_screen_stats(bfi_plan *plan, uint64_t *screened, int32_t *two_stage) {
     if (!plan) return fail(BFI_E_INVALID, "plan is NULL");
-    const bool two = plan->sampler == BFI_SAMPLE_BOX && plan->shape->two_stage != 0;
-    if (two_stage) *two_stage = two ? 1 : 0;
-    if (screened) {
-        if (two) {
-            DeviceGuard g(plan->device);
-            unsigned long long v = 0;
-            BFI_CUDA(cudaMemcpy(&v, plan->d_stats + 1, sizeof v, cudaMemcpyDeviceToHost));
-            *screened = v;
-        } else {
-            *screened = static_cast<uint64_t>(plan->total);
-        }
+    unsigned long long c[3] = {0, 0, 0};
+    const bool box = plan->sampler == BFI_SAMPLE_BOX;
+    if (box) {
+        const bfi_status st = read_counters(plan, c);
+        if (st != BFI_OK) return st;
     }
+    const bool two = box && c[2] > 0;
+    if (two_stage) *two_stage = two ? 1 : 0;
+    if (screened) *screened = two ? static_cast<uint64_t>(c[1]) : static_cast<uint64_t>(plan->total);
+    return BFI_OK;
+}
+
+bfi_status bfi_plan_get_work(bfi_plan *plan, bfi_work *work) {
+    if (!plan || !work) return fail(BFI_E_INVALID, "plan or work is NULL");
+    unsigned long long c[3] = {0, 0, 0};
+    const bfi_status st = read_counters(plan, c);
+    if (st != BFI_OK) return st;
+    const uint64_t total = static_cast<uint64_t>(plan->total);
+    work->samples = total;
+    work->evaluated = c[0];
+    if (plan->sampler != BFI_SAMPLE_BOX) {  // every sample evaluated, no screen
+        work->stage1 = work->full_screen = work->survivors = 0;
+    } else {
+        work->stage1 = c[2];
+        work->full_screen = total - c[2];
+        work->survivors = plan->shape->two_stage ? c[1] - work->full_screen : 0;
+    }
+    work->two_stage_shape = plan->sampler == BFI_SAMPLE_BOX && plan->shape->two_stage ? 1 : 0;
+    work->rest_screen = work->two_stage_shape && plan->lat.nt == 2 && plan->lat.nx % 2 == 0 &&
+                        static_cast<float>(0.5 * plan->lat.mass2) == 0.f;
     return BFI_OK;
 }
 
@@ -711,6 +738,83 @@ bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double 
         totals[4 + r] = C;
         totals[4 + R + r] = inf_err ? INFINITY : std::sqrt(V > 0.0 ? V : 0.0) / Z;
     }
+    return BFI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stated arithmetic error of a result (box sampler).  Every step an evaluated
+// sample goes through has a rounding bound; their first-order sum bounds how
+// far the library's Z and C(r) can lie from the same estimator evaluated in
+// exact arithmetic on the same points (FP32 mode: the same float points), to
+// which the negligible-weight truncation adds at most e^-c.  u is the unit
+// roundoff (2^-24 in FP32, 2^-53 in FP64).  With T a bound on the magnitude
+// of each of the three terms of a residual (from vmax and the lattice
+// constants), inv = 1/(2 D tau), and S_hi a bound on the action of a sample
+// that can carry weight (the records' largest shift plus the window W):
+//   action   |dS| <= 2 k u_a T sqrt(d S_hi inv) + (d + 1) u_a S_hi, with k
+//            operations per residual of relative error u_a each (FP32: the
+//            compensated action, k = 8, u_a = 2^-46; FP64: k = 4, u_a = u),
+//            plus (d + 1) u_a times the mass term
+//   weight   exp's error (CUDA documents expf at 2 ulp and exp at 1 ulp) plus
+//            the argument's rounding (FP32: the split a_h + a_l is exact and
+//            the first-order correction one fma, u (1 + 2^-18); FP64:
+//            u |m - S| <= u (W + 17)) plus |dS|
+//   products FP32: Dot2 kept as hi + lo, 2 (d u)^2 Q_0, then w Q_r =
+//            fma(w, hi, w lo), one rounding; FP64: the FMA chain, gamma_d Q_0
+//            (|Q_r| <= Q_0 by Cauchy-Schwarz), then w Q_r, one rounding
+//   sums     per thread (at most N_t terms per chunk): FP32 Kahan 2u + N_t u^2,
+//            FP64 plain (N_t - 1) u; then the FP64 merges of threads, chunks
+//            and subvolumes, 2^-53 (64 + 4 chunks + 4 nsub)
+//   dropped  e^-c of Z (c = 20 in FP32, 34 in FP64); of N(r), e^-c vmax^2 Z,
+//            since |P_r| <= vmax^2
+// Z: b_Z = weight + sums + merges + e^-c.  N(r) relative to N(0): b_N =
+// weight + products + sums + merges + e^-c vmax^2 / C(0).  C(r) = N(r)/Z
+// relative to C(0): b_N (1 + b_Z) + b_Z (1 + b_Z).
+// ---------------------------------------------------------------------------
+bfi_status bfi_error_bound(const bfi_lattice *lattice, bfi_precision precision, int64_t nsub, const double *slots,
+                           double vmax, double *bound) {
+    bfi_status st = check_lattice(lattice);
+    if (st != BFI_OK) return st;
+    if (precision != BFI_FP64 && precision != BFI_FP32) return fail(BFI_E_INVALID, "unknown precision %d", precision);
+    if (nsub < 1 || !slots || !bound) return fail(BFI_E_INVALID, "nsub must be >= 1 and slots, bound non-NULL");
+    if (!std::isfinite(vmax) || vmax <= 0.0) return fail(BFI_E_INVALID, "vmax must be finite and > 0");
+    const int nx = lattice->nx, R = num_r(nx), SL = 5 + 3 * R;
+    const double d = static_cast<double>(nx) * lattice->nt;
+    std::vector<double> tot(static_cast<size_t>(4 + 2 * R));
+    if ((st = bfi_merge_host(nx, nsub, slots, tot.data())) != BFI_OK) return st;
+    double m_hi = -INFINITY, n_max = 0.0;
+    for (int64_t s = 0; s < nsub; ++s) {
+        const double *q = slots + s * SL;
+        if (q[0] <= 0.0) continue;
+        n_max = std::fmax(n_max, q[0]);
+        if (q[3] > 0.0) m_hi = std::fmax(m_hi, q[1]);
+    }
+    const double C0 = tot[4];
+    if (!std::isfinite(m_hi) || !(C0 > 0.0)) return fail(BFI_E_INVALID, "the records carry no weight");
+    const bfi::ShapeKernels *shape = bfi::find_shape(nx, lattice->nt);
+    const bool f32 = precision == BFI_FP32;
+    const double u = f32 ? 0x1p-24 : 0x1p-53;
+    const double c_adv = lattice->nonlinear * lattice->tau / (2.0 * lattice->a);
+    const double c_dif = lattice->nu * lattice->tau / (lattice->a * lattice->a);
+    const double k1 = 2.0 * c_dif - 1.0, inv = 1.0 / (2.0 * lattice->D * lattice->tau);
+    const double T = vmax * (1.0 + std::fabs(k1) + 2.0 * std::fabs(c_adv) * vmax) + 2.0 * std::fabs(c_dif) * vmax;
+    const double c = f32 ? 20.0 : 34.0;
+    const double W = c + std::log(std::fmax(n_max, 1.0));
+    const double S_hi = 1.001 * (std::fmax(m_hi, 0.0) + 1.0) + W + 2.0;
+    const double ua = f32 ? 0x1p-46 : u, k = f32 ? 8.0 : 4.0;
+    double dS = 2.0 * k * ua * T * std::sqrt(d * S_hi * inv) + (d + 1.0) * ua * S_hi;
+    if (lattice->mass2 > 0.0) dS += (d + 1.0) * ua * 0.5 * lattice->mass2 * d * vmax * vmax;
+    const double e_w = (f32 ? 0x1p-22 : 0x1p-52) + (f32 ? u * (1.0 + 0x1p-18) : u * (W + 17.0)) + dS;
+    const double e_q = (f32 ? 2.0 * (d * u) * (d * u) : d * u / (1.0 - d * u)) + u;
+    // terms per per-thread (per-warp in the warp-per-sample kernel) sum in one chunk
+    const double n_t = shape && shape->kernel == 0 ? 512.0 : 512.0 * bfi::kBlock / 4.0;
+    const double e_sum = f32 ? 2.0 * u + n_t * u * u : (n_t - 1.0) * u;
+    const double e_merge = 0x1p-53 * (64.0 + 4.0 * std::ceil(n_max / 1024.0) + 4.0 * static_cast<double>(nsub));
+    const double drop = std::exp(-c);
+    const double bz = e_w + e_sum + e_merge + drop;
+    const double bn = e_w + e_q + e_sum + e_merge + drop * vmax * vmax / C0;
+    bound[0] = bz;
+    for (int r = 0; r < R; ++r) bound[1 + r] = bn * (1.0 + bz) + bz * (1.0 + bz);
     return BFI_OK;
 }
 

@@ -224,6 +224,12 @@ bfi_status bfi_batch_create(bfi_batch **out, const bfi_job *jobs, int32_t njobs,
     return BFI_OK;
 }
 
+bfi_status bfi_batch_get_work(bfi_batch *batch, int32_t job, bfi_work *work) {
+    if (!batch || job < 0 || job >= static_cast<int32_t>(batch->plans.size()))
+        return bfi::set_error(BFI_E_INVALID, "batch is NULL or job out of range");
+    return bfi_plan_get_work(batch->plans[job], work);
+}
+
 bfi_status bfi_batch_launch(bfi_batch *batch, void *stream) {
     if (!batch || !batch->exec) return bfi::set_error(BFI_E_INVALID, "batch is NULL");
     DeviceScope scope(batch->device);

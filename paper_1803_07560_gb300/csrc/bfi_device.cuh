@@ -248,6 +248,53 @@ __device__ __forceinline__ DF df_add_f(DF a, float b) {
     return fast_two_sum(s.h, s.l);
 }
 
+// Compensated dot product of the FP32 evaluation, Q_r = sum_j u_j u_{j+r}
+// (Dot2 of Ogita, Rump & Oishi: every product split exactly by two_prod, the
+// running sum by two_sum, the errors summed in plain float), returned as
+// hi + lo: |Q_r - (hi + lo)| <= 2^-24 |Q_r| + gamma_d^2 Q_0 with Q_0 >=
+// |Q_r| by Cauchy-Schwarz.  For even NX the r = NX/2 pairs count twice.
+template <int NX, int NT>
+__device__ __forceinline__ DF product_df(const float (&u)[NX * NT], int r) {
+    DF s{0.f, 0.f};
+    const bool half = (2 * r == NX) && r > 0;
+#pragma unroll
+    for (int m = 0; m < (half ? NX / 2 : NX); ++m) {
+#pragma unroll
+        for (int l = 0; l < NT; ++l) {
+            const DF p = two_prod(u[m * NT + l], u[((m + r) % NX) * NT + l]);
+            const DF t = two_sum(s.h, p.h);
+            s.h = t.h;
+            s.l = __fadd_rn(s.l, __fadd_rn(p.l, t.l));
+        }
+    }
+    return half ? DF{2.f * s.h, 2.f * s.l} : s;
+}
+
+// Weight exp(m - S) of the FP32 evaluation with the shift m kept in double
+// and the action S = S.h + S.l in compensated float.  The argument a = m - S
+// is formed in double and split exactly into floats a_h + a_l (|a_l| <=
+// ulp(a_h)/2), and exp(a) = exp(a_h) (1 + a_l + O(a_l^2)): so the weight
+// carries expf's error (at most 2 ulp by CUDA's documented accuracy) and one
+// rounding, whatever the size of the argument.
+__device__ __forceinline__ float weight_f32(double m, DF S) {
+    const double a = (m - static_cast<double>(S.h)) - static_cast<double>(S.l);
+    const float ah = __double2float_rn(a);
+    const float al = __double2float_rn(a - static_cast<double>(ah));
+    const float e = expf(ah);
+    return __fmaf_rn(e, al, e);
+}
+
+// Moving the FP32 evaluation's shift down past an action S: by k ln 2 with
+// k = ceil((m - S) / ln 2), so that every sum scales by exactly 2^-k (first
+// order) or 2^-2k (second order) and no rounding enters; the new shift lies in
+// (S - ln 2, S].  pow2_neg(k) = 2^-k as a float (0 below the normal range: a
+// sum scaled that far is below 2^-126 of the new largest weight).
+constexpr double kLn2 = 0.693147180559945309417232121458;
+__device__ __forceinline__ int shift_steps(double m, double S) {
+    return static_cast<int>(ceil((m - S) * (1.0 / kLn2)));
+}
+__device__ __forceinline__ float pow2_neg(int k) { return k < 127 ? __int_as_float((127 - k) << 23) : 0.f; }
+
 // The constants of the residual split into hi + lo floats.
 struct LatticeConstDF {
     DF c_adv, k1, c_dif, inv_2Dtau, half_mass2;

@@ -39,6 +39,7 @@ struct IntegrandArgs {
     int64_t chunk_samples;
     float skip_window;         // samples above (reference + skip_window) have negligible weight
     unsigned long long *screened;  // [1] samples the full FP32 screen examined after the partial one, or null
+    unsigned long long *stage1;    // [1] samples of chunks that ran stage 1 of the two-stage screen, or null
 };
 
 struct MergeArgs {

@@ -143,7 +143,7 @@ __device__ DF warp_action_df(const float *u, const uint16_t *next, const GenShap
 // (r = lane + 32 i), handed to f(r, Q_r).  Each lane starts its sweep at
 // j = lane, so at every step the lanes read consecutive words (no bank
 // conflicts); the order is fixed per lane, so the result is reproducible.
-// FP32 sums are compensated.
+// FP32 sums are compensated and handed over as hi + lo.
 template <typename F>
 __device__ __forceinline__ void lane_products(const double *u, const GenShape &g, F f) {
     const int lane = threadIdx.x & 31;
@@ -170,7 +170,7 @@ __device__ __forceinline__ void lane_products(const float *u, const GenShape &g,
             j = (j + 1 == g.d) ? 0 : j + 1;
             jr = (jr + 1 == g.d) ? 0 : jr + 1;
         }
-        f(r, q.h + q.l);
+        f(r, q);
     }
 }
 
@@ -380,7 +380,6 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
         const float hint = args.hint[v.s];
         float m_ref = hint;
         double m_acc = static_cast<double>(hint);
-        float m_acc_f = hint;
         unsigned n_eval = 0;
         for (uint64_t k = warp; k < v.cnt; k += kGWarps) {
             const uint64_t i = v.first + k;
@@ -417,19 +416,19 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
                 if (!(S_f <= m_ref + args.skip_window)) continue;
                 if constexpr (SPL > 0)  // the evaluation reads the point from shared memory
                     warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
-                DF S{S_f, 0.f};
-                if (S_f < m_ref + kRefineWindow) {
-                    S = warp_action_df(uf, next, g, ga.cdf);
-                    m_ref = fminf(m_ref, S.h);
-                }
-                if (S.h < m_acc_f - kRescaleMargin) {
-                    const float f = expf(S.h - m_acc_f), f2 = f * f;
+                // every candidate: compensated action, exact power-of-two shift moves, split-argument weight
+                const DF S = warp_action_df(uf, next, g, ga.cdf);
+                m_ref = fminf(m_ref, S.h);
+                const double S_d = static_cast<double>(S.h) + static_cast<double>(S.l);
+                if (S_d < m_acc - kRescaleMargin) {
+                    const int steps = shift_steps(m_acc, S_d);
+                    const float f = pow2_neg(steps), f2 = f * f;
                     for (int kk = lane; kk < g.K; kk += 32) sf[kk] *= second_order(kk, g.R) ? f2 : f;
                     for (int kk = lane; kk < 1 + g.R; kk += 32) cf[kk] *= f;
-                    m_acc_f = S.h;
+                    m_acc -= steps * kLn2;
                     __syncwarp();  // another lane owns some of the sums it rescaled
                 }
-                const float w = expf(__fsub_rn(__fsub_rn(m_acc_f, S.h), S.l));
+                const float w = weight_f32(m_acc, S);
                 auto kahan = [&](int k, int ci, float x) {
                     const float y = x - cf[ci];
                     const float t = sf[k] + y;
@@ -440,13 +439,12 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
                     kahan(0, 0, w);
                     sf[1] += w * w;
                 }
-                lane_products(uf, g, [&](int r, float q) {
-                    const float wq = w * q;
+                lane_products(uf, g, [&](int r, DF q) {
+                    const float wq = __fmaf_rn(w, q.h, w * q.l);  // w Q_r rounded once
                     kahan(2 + r, 1 + r, wq);
                     sf[2 + g.R + r] += w * wq;
                     sf[2 + 2 * g.R + r] += wq * wq;
                 });
-                m_acc = static_cast<double>(m_acc_f);
             }
             ++n_eval;
             __syncwarp();
@@ -679,7 +677,7 @@ __global__ void __launch_bounds__(kGBlock) generic_eval(const EvalArgs a, const 
         } else {
             S = static_cast<double>(warp_action<float>(uf, next, g, ga.cf));
         }
-        lane_products(uf, g, [&](int r, float q) { a.P[i * g.R + r] = static_cast<double>(q) / g.d; });
+        lane_products(uf, g, [&](int r, DF q) { a.P[i * g.R + r] = static_cast<double>(q.h + q.l) / g.d; });
     }
     if (lane == 0) a.S[i] = S;
 }

@@ -455,6 +455,11 @@ __device__ __forceinline__ void add_screened(unsigned long long *screened, unsig
     if (threadIdx.x == 0) atomicAdd(screened, static_cast<unsigned long long>(*s_cnt));
 }
 
+// The samples of a chunk that ran stage 1 of the two-stage screen.
+__device__ __forceinline__ void add_stage1(unsigned long long *stage1, uint64_t cnt) {
+    if (stage1 && threadIdx.x == 0) atomicAdd(stage1, static_cast<unsigned long long>(cnt));
+}
+
 // ---------------------------------------------------------------------------
 // Negligible weights.  A sample whose action exceeds the subvolume's
 // smallest action by more than args.skip_window has weight below
@@ -593,6 +598,25 @@ __device__ __forceinline__ void accumulate(SmemSums<Real, K, BLOCK> &acc, Real w
     }
 }
 
+// The FP32 evaluation's sums with the products formed on the way: w Q_r =
+// fma(w, hi, w lo) from the compensated Q_r = hi + lo, so w Q_r is rounded
+// once; no array of products is held.
+template <int NX, int NT, int K, int BLOCK>
+__device__ __forceinline__ void accumulate_products_df(SmemSums<float, K, BLOCK> &acc, float w,
+                                                       const float (&u)[NX * NT]) {
+    constexpr int R = NX / 2 + 1;
+    acc.add(0, w);
+    acc.add(1, w * w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const DF q = product_df<NX, NT>(u, r);
+        const float wq = __fmaf_rn(w, q.h, w * q.l);
+        acc.add(2 + r, wq);
+        acc.add(2 + R + r, w * wq);
+        acc.add(2 + 2 * R + r, wq * wq);
+    }
+}
+
 template <typename Real, int K, int R, int BLOCK>
 __device__ __forceinline__ void rescale(SmemSums<Real, K, BLOCK> &acc, Real f) {
     const Real f2 = f * f;
@@ -723,7 +747,9 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         chunk_prefixes<D>(v, rk, s_pre);
         const float hint = args.hint[v.s];
         float m_ref = hint;
-        double m_acc = static_cast<double>(hint);
+        // the thread's shift lives in its shared-memory slot (only evaluations touch it)
+        double &m_acc = sh.f[tid];
+        m_acc = static_cast<double>(hint);
         if (tid == 0) {
             sh.min_bits = __float_as_int(hint);
             sh.evaluated = 0u;
@@ -745,11 +771,13 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
             m_ref = fminf(m_ref, __double2float_rn(S));
             double Q[R];
             products<NX, NT, double>(u, Q);
-            if (S < m_acc - kRescaleMargin) {  // rare: move the shift down
-                rescale<double, K, R, BLOCK>(acc, exp(S - m_acc));
-                m_acc = S;
+            double m = m_acc;
+            if (S < m - kRescaleMargin) {  // rare: move the shift down
+                rescale<double, K, R, BLOCK>(acc, exp(S - m));
+                m = S;
+                m_acc = m;
             }
-            accumulate<double, K, R, BLOCK>(acc, exp(m_acc - S), Q);
+            accumulate<double, K, R, BLOCK>(acc, exp(m - S), Q);
             ++n_eval;
         };
         // m_ref changes only where the queue is evaluated (then made uniform
@@ -817,19 +845,22 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
-        chunk_record<double, K, R, BLOCK>(acc, m_acc, sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
+        if (two_stage) add_stage1(args.stage1, v.cnt);
+        chunk_record<double, K, R, BLOCK>(acc, double(m_acc), sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
     }
 }
 
 // ---------------------------------------------------------------------------
-// FP32 integrand.  Points, action, products and weights in float; per-thread
-// Kahan sums; merges in double.  Candidates are queued as above; a candidate
-// whose FP32 action lies within kRefineWindow of m_ref (the weights that
-// matter) gets its action recomputed in compensated FP32 (action_df); all
-// others have weights below e^-kRefineWindow of the largest, where the ~1e-5
-// FP32 action error is harmless.
+// FP32 integrand.  Points, screen, action, products and weights in float;
+// per-thread Kahan sums; the log-weight shift and the merges in double.
+// Candidates are queued as above and each is evaluated with the compensated
+// FP32 action (action_df), the split-argument weight (weight_f32) and the
+// compensated products (accumulate_products_df); the shift moves down by
+// whole powers of two (shift_steps), so rescaling the sums is exact.  Every
+// step of an evaluation then has a bound of a few float roundings, which is
+// what the library's stated arithmetic error of a result adds up
+// (bfi_error_bound).
 // ---------------------------------------------------------------------------
-constexpr float kRefineWindow = 28.f;
 
 template <int NX, int NT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(const IntegrandArgs args,
@@ -859,7 +890,10 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         if (tid < D) BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
         chunk_prefixes<D>(v, rk, s_pre);
         const float hint = args.hint[v.s];
-        float m_acc = hint, m_ref = hint;
+        float m_ref = hint;
+        // the thread's shift (double) lives in its shared-memory slot: only evaluations touch it
+        double &m_acc = sh.f[tid];
+        m_acc = static_cast<double>(hint);
         if (tid == 0) {
             sh.min_bits = __float_as_int(hint);
             sh.evaluated = 0u;
@@ -873,19 +907,17 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         auto evaluate = [&](uint32_t k) {
             float u[D];
             make_point_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, u);
-            const float S_f = action<NX, NT, float>(u, lc);
-            DF S{S_f, 0.f};
-            if (S_f < m_ref + kRefineWindow) {
-                S = action_df<NX, NT>(u, lcd);
-                m_ref = fminf(m_ref, S.h);
+            const DF S = action_df<NX, NT>(u, lcd);
+            m_ref = fminf(m_ref, S.h);
+            const double S_d = static_cast<double>(S.h) + static_cast<double>(S.l);
+            double m = m_acc;
+            if (S_d < m - kRescaleMargin) {  // rare: move the shift down by whole powers of two
+                const int steps = shift_steps(m, S_d);
+                rescale<float, K, R, BLOCK>(acc, pow2_neg(steps));
+                m -= steps * kLn2;
+                m_acc = m;
             }
-            if (S.h < m_acc - kRescaleMargin) {  // rare: move the shift down
-                rescale<float, K, R, BLOCK>(acc, expf(S.h - m_acc));
-                m_acc = S.h;
-            }
-            float Q[R];
-            products<NX, NT, float>(u, Q);
-            accumulate<float, K, R, BLOCK>(acc, expf(__fsub_rn(__fsub_rn(m_acc, S.h), S.l)), Q);
+            accumulate_products_df<NX, NT, K, BLOCK>(acc, weight_f32(m, S), u);
             ++n_eval;
         };
         // m_ref changes only where the queue is evaluated (then made uniform
@@ -948,8 +980,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
         if (lane < count) evaluate(queue[lane]);
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
-        chunk_record<float, K, R, BLOCK>(acc, static_cast<double>(m_acc), sh.f, &sh.mb, args.partials + c * (K + 2),
-                                         v.cnt);
+        if (two_stage) add_stage1(args.stage1, v.cnt);
+        chunk_record<float, K, R, BLOCK>(acc, double(m_acc), sh.f, &sh.mb, args.partials + c * (K + 2), v.cnt);
     }
 }
 

@@ -27,6 +27,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -56,6 +57,7 @@ struct Request {
     uint64_t samples = 0;
     std::vector<double> leaf_slots, leaf_lo, leaf_hi, totals;
     std::vector<uint32_t> leaf_sid;
+    bfi_work work{};  // counted work of every pass so far
     Clock::time_point t_submit, t_start, t_done;
     bool started = false;
     std::atomic<bool> cancel{false};
@@ -84,7 +86,7 @@ Layout layout_for(int64_t nsub, int64_t nchunks, int d, int K, int SL, int TL) {
     L.off = o;   o += round_up(sizeof(int64_t) * (nsub + 1));
     L.smp = o;   o += round_up(sizeof(uint64_t) * nsub);
     L.hint = o;  o += round_up(sizeof(float) * nsub);
-    L.stats = o; o += round_up(sizeof(unsigned long long));
+    L.stats = o; o += round_up(3 * sizeof(unsigned long long));  // evaluated, fully screened, stage 1
     L.fbuf = o;  o += round_up(sizeof(double) * 2 * nsub);
     L.part = o;  o += round_up(sizeof(double) * static_cast<size_t>(nchunks > 0 ? nchunks : 1) * (K + 2));
     L.lo = o;    o += round_up(sizeof(double) * nsub * d);
@@ -131,6 +133,7 @@ struct Slot {
     double *stage = nullptr;  // page-locked: the pass's slots then totals
     size_t stage_cap = 0;     // doubles
     bool busy = false;
+    bool draining = false;    // its pass failed in flight; the slot is reused once the pass's callback arrives
     std::shared_ptr<Pass> pass;
     struct Ctx {
         bfi_server *srv;
@@ -152,6 +155,10 @@ struct bfi_server {
     uint64_t bytes_in_use = 0;
     bfi_server_stats st{};
     bool stopping = false;
+    bool exited = false;      // the scheduler has left its loop (set under m, cv notified)
+    bool broken = false;      // the scheduler stopped on an error: nothing more is admitted
+    int32_t fault_point = 0;  // injected fault (host side): the point and how many passes reach it first
+    int64_t fault_skip = 0;
     std::thread worker;
 };
 
@@ -172,6 +179,18 @@ void end_request(Request &r, int state, bfi_status status, const char *message) 
     r.cv.notify_all();
 }
 
+// True when the injected fault fires at 'point' for this pass (one-shot).
+bool take_fault(bfi_server *s, int32_t point) {
+    std::lock_guard<std::mutex> lock(s->m);
+    if (s->fault_point != point) return false;
+    if (s->fault_skip > 0) {
+        --s->fault_skip;
+        return false;
+    }
+    s->fault_point = 0;
+    return true;
+}
+
 void CUDART_CB on_pass_done(void *p) {
     auto *c = static_cast<Slot::Ctx *>(p);
     std::lock_guard<std::mutex> lock(c->srv->m);
@@ -184,7 +203,7 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
     Slot &sl = s->slots[k];
     Request &r = *p.req;
     cudaStream_t st = sl.stream;
-    const size_t stage_need = static_cast<size_t>(p.nsub) * r.SL + r.TL;
+    const size_t stage_need = static_cast<size_t>(p.nsub) * r.SL + r.TL + 3;  // records, totals, 3 counters
     auto cuda = [&](cudaError_t e, const char *what) {
         if (e != cudaSuccess) msg = std::string(what) + ": " + cudaGetErrorString(e);
         return e == cudaSuccess;
@@ -201,6 +220,10 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
     const bfi::ShapeKernels *shape = bfi::find_shape(r.lat.nx, r.lat.nt);
     const bfi_precision prec = s->cfg.precision;
     void *block = nullptr;
+    if (take_fault(s, BFI_FAULT_POOL_ALLOC)) {
+        msg = "pool allocation: injected failure";
+        return BFI_E_NOMEM;
+    }
     if (!cuda(cudaMallocFromPoolAsync(&block, p.L.total, s->pool, st), "pool allocation")) return BFI_E_NOMEM;
     unsigned char *b = static_cast<unsigned char *>(block);
     auto at = [&](size_t o) { return static_cast<void *>(b + o); };
@@ -209,7 +232,7 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
               cuda(cudaMemcpyAsync(at(p.L.lo), p.lo.data(), sizeof(double) * p.nsub * r.d, cudaMemcpyHostToDevice, st), "copy") &&
               cuda(cudaMemcpyAsync(at(p.L.hi), p.hi.data(), sizeof(double) * p.nsub * r.d, cudaMemcpyHostToDevice, st), "copy") &&
               cuda(cudaMemcpyAsync(at(p.L.sid), p.sid.data(), sizeof(uint32_t) * p.nsub, cudaMemcpyHostToDevice, st), "copy") &&
-              cuda(cudaMemsetAsync(at(p.L.stats), 0, sizeof(unsigned long long), st), "memset");
+              cuda(cudaMemsetAsync(at(p.L.stats), 0, 3 * sizeof(unsigned long long), st), "memset");
     int per_sm = 1;
     if (ok) ok = cuda(shape->occupancy[prec](r.lat.nx, r.lat.nt, &per_sm), "occupancy");
     const bfi::LatticeParams lp{r.lat.nx, r.lat.nt, r.lat.nu, r.lat.D, r.lat.a, r.lat.tau, r.lat.nonlinear, r.lat.mass2};
@@ -229,8 +252,13 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
                              p.nchunks,
                              p.chunk_samples,
                              p.window,
-                             nullptr};
+                             static_cast<unsigned long long *>(at(p.L.stats)) + 1,
+                             static_cast<unsigned long long *>(at(p.L.stats)) + 2};
         ok = cuda(shape->integrand[prec](a, lp, r.seed, r.job_id, static_cast<int>(grid), st), "integrand launch");
+    }
+    if (ok && take_fault(s, BFI_FAULT_LAUNCH)) {
+        msg = "merge launch: injected failure";
+        ok = false;
     }
     if (ok) {
         const bfi::MergeArgs mg{lo, hi, static_cast<const int64_t *>(at(p.L.off)), static_cast<const double *>(at(p.L.part)),
@@ -239,7 +267,9 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
         ok = cuda(bfi::launch_merges(mg, tg, st), "merge launch") &&
              cuda(cudaMemcpyAsync(sl.stage, slots, sizeof(double) * p.nsub * r.SL, cudaMemcpyDeviceToHost, st), "copy") &&
              cuda(cudaMemcpyAsync(sl.stage + static_cast<size_t>(p.nsub) * r.SL, totals, sizeof(double) * r.TL,
-                                  cudaMemcpyDeviceToHost, st), "copy");
+                                  cudaMemcpyDeviceToHost, st), "copy") &&
+             cuda(cudaMemcpyAsync(sl.stage + static_cast<size_t>(p.nsub) * r.SL + r.TL, at(p.L.stats),
+                                  3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st), "copy");
     }
     cudaFreeAsync(block, st);  // stream-ordered: after the copies
     if (!ok) {
@@ -273,7 +303,23 @@ void finish_pass(bfi_server *s, Pass &p, const double *stage) {
     }
     std::unique_lock<std::mutex> rl(r.m);  // leaves and counters are read by bfi_request_get_info
     r.passes++;
-    for (uint64_t n : p.samples) r.samples += n;
+    uint64_t pass_samples = 0;
+    for (uint64_t n : p.samples) pass_samples += n;
+    r.samples += pass_samples;
+    {  // the pass's work counters follow its records and totals in the staging buffer
+        unsigned long long c[3];
+        std::memcpy(c, stage + static_cast<size_t>(p.nsub) * r.SL + r.TL, sizeof c);
+        const bfi::ShapeKernels *shape = bfi::find_shape(r.lat.nx, r.lat.nt);
+        const uint64_t full = pass_samples - c[2];
+        r.work.samples += pass_samples;
+        r.work.evaluated += c[0];
+        r.work.stage1 += c[2];
+        r.work.full_screen += full;
+        r.work.survivors += shape && shape->two_stage ? c[1] - full : 0;
+        r.work.two_stage_shape = shape && shape->two_stage ? 1 : 0;
+        r.work.rest_screen = r.work.two_stage_shape && r.lat.nt == 2 && r.lat.nx % 2 == 0 &&
+                             static_cast<float>(0.5 * r.lat.mass2) == 0.f;
+    }
     auto next = make_pass(p.req, s->cfg.precision);
     const double thr = s->cfg.split_rel_var;
     const bool may_split = thr > 0.0 && r.passes <= s->cfg.max_split_rounds;
@@ -326,14 +372,43 @@ void finish_pass(bfi_server *s, Pass &p, const double *stage) {
     s->st.completed++;
 }
 
-void scheduler(bfi_server *s) {
-    cudaSetDevice(s->cfg.device);
-    std::unique_lock<std::mutex> lk(s->m);
+// A pass that failed after admission: its job fails with 'status', its
+// memory returns to the budget.  The caller holds s->m.
+void fail_running(bfi_server *s, Slot &sl, bfi_status status, const std::string &msg,
+                  std::unique_lock<std::mutex> &lk) {
+    std::shared_ptr<Pass> pass = sl.pass;
+    sl.pass.reset();
+    s->bytes_in_use -= pass->L.total;
+    s->st.running--;
+    s->st.failed++;
+    lk.unlock();
+    end_request(*pass->req, 4, status, msg.c_str());
+    lk.lock();
+}
+
+void scheduler_loop(bfi_server *s, std::unique_lock<std::mutex> &lk) {
     for (;;) {
         while (!s->finished.empty()) {
             const int k = s->finished.front();
             s->finished.pop_front();
             Slot &sl = s->slots[k];
+            if (sl.draining) {  // the late callback of a pass that already failed: the slot is free again
+                sl.draining = false;
+                sl.busy = false;
+                continue;
+            }
+            // The callback ran, so the stream has passed every kernel and copy
+            // of the pass: an error status now is the pass's, and its records
+            // in the staging buffer are not to be read.
+            lk.unlock();
+            cudaError_t e = take_fault(s, BFI_FAULT_COMPLETION) ? cudaErrorLaunchFailure : cudaStreamQuery(sl.stream);
+            if (take_fault(s, BFI_FAULT_SCHEDULER)) throw std::runtime_error("injected scheduler failure");
+            lk.lock();
+            if (e != cudaSuccess && e != cudaErrorNotReady) {
+                sl.busy = false;
+                fail_running(s, sl, BFI_E_CUDA, std::string("pass failed on the device: ") + cudaGetErrorString(e), lk);
+                continue;
+            }
             std::shared_ptr<Pass> pass = sl.pass;
             sl.pass.reset();
             sl.busy = false;
@@ -343,6 +418,16 @@ void scheduler(bfi_server *s) {
             lk.unlock();
             finish_pass(s, *pass, sl.stage);
             lk.lock();
+        }
+        // A pass whose stream reports an error before its callback (after an
+        // asynchronous failure the callback may never run) fails now; its slot
+        // drains until the callback arrives.
+        for (Slot &sl : s->slots) {
+            if (!sl.busy || sl.draining) continue;
+            const cudaError_t e = cudaStreamQuery(sl.stream);
+            if (e == cudaSuccess || e == cudaErrorNotReady) continue;
+            sl.draining = true;
+            fail_running(s, sl, BFI_E_CUDA, std::string("pass failed on the device: ") + cudaGetErrorString(e), lk);
         }
         while (!s->queue.empty()) {
             std::shared_ptr<Pass> pass = s->queue.front();
@@ -387,20 +472,54 @@ void scheduler(bfi_server *s) {
             lk.lock();
             if (rc != BFI_OK) {
                 s->slots[k].busy = false;
-                s->slots[k].pass.reset();
-                s->bytes_in_use -= pass->L.total;
-                s->st.running--;
-                s->st.failed++;
-                lk.unlock();
-                end_request(r, 4, rc, msg.c_str());
-                lk.lock();
+                fail_running(s, s->slots[k], rc, msg, lk);
             }
         }
         bool busy = false;
-        for (const Slot &sl : s->slots) busy = busy || sl.busy;
+        for (const Slot &sl : s->slots) busy = busy || (sl.busy && !sl.draining);
         if (s->stopping && s->queue.empty() && !busy && s->finished.empty()) break;
         s->cv.wait_for(lk, std::chrono::milliseconds(2));
     }
+}
+
+// The scheduler thread.  If its loop stops on an exception (a failed host
+// allocation, or an injected fault), every job still queued or running fails
+// with BFI_E_NOMEM and a message, so that no wait is left without an end, and
+// the server admits nothing more.
+void scheduler(bfi_server *s) {
+    cudaSetDevice(s->cfg.device);
+    std::unique_lock<std::mutex> lk(s->m);
+    std::string why;
+    try {
+        scheduler_loop(s, lk);
+    } catch (const std::exception &e) {
+        why = e.what();
+    } catch (...) {
+        why = "unknown exception";
+    }
+    if (!lk.owns_lock()) lk.lock();
+    if (!why.empty()) {
+        s->broken = true;
+        const std::string msg = "the server's scheduler stopped: " + why;
+        std::vector<std::shared_ptr<Request>> ended;
+        for (auto &p : s->queue) ended.push_back(p->req);
+        s->st.failed += s->queue.size();
+        s->st.queued = 0;
+        s->queue.clear();
+        for (Slot &sl : s->slots)
+            if (sl.busy && !sl.draining && sl.pass) {
+                ended.push_back(sl.pass->req);
+                s->st.failed++;
+                s->st.running--;
+                sl.draining = true;  // its stream still finishes; destroy waits for it
+            }
+        s->finished.clear();
+        lk.unlock();
+        for (auto &r : ended) end_request(*r, 4, BFI_E_NOMEM, msg.c_str());
+        lk.lock();
+    }
+    s->exited = true;
+    s->cv.notify_all();
 }
 
 bfi_status fail_msg(bfi_status st, const std::string &m) { return bfi::set_error(st, m.c_str()); }
@@ -451,13 +570,31 @@ bfi_status bfi_server_create(bfi_server **out, const bfi_server_config *config) 
     return BFI_OK;
 }
 
+bfi_status bfi_server_shutdown(bfi_server *s, int64_t timeout_ms) {
+    if (!s) return bfi::set_error(BFI_E_INVALID, "server is NULL");
+    std::unique_lock<std::mutex> lk(s->m);
+    s->stopping = true;
+    s->cv.notify_all();
+    auto done = [&] { return s->exited; };
+    if (timeout_ms < 0)
+        s->cv.wait(lk, done);
+    else if (!s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+        return bfi::set_error(BFI_E_TIMEOUT, "running passes did not finish within the timeout");
+    return BFI_OK;
+}
+
+bfi_status bfi_server_inject_fault(bfi_server *s, int32_t point, int64_t nth) {
+    if (!s || point < BFI_FAULT_NONE || point > BFI_FAULT_SCHEDULER || nth < 0)
+        return bfi::set_error(BFI_E_INVALID, "server is NULL, or unknown fault point, or nth < 0");
+    std::lock_guard<std::mutex> lock(s->m);
+    s->fault_point = point;
+    s->fault_skip = nth;
+    return BFI_OK;
+}
+
 bfi_status bfi_server_destroy(bfi_server *s) {
     if (!s) return BFI_OK;
-    {
-        std::lock_guard<std::mutex> lock(s->m);
-        s->stopping = true;
-        s->cv.notify_all();
-    }
+    bfi_server_shutdown(s, -1);
     if (s->worker.joinable()) s->worker.join();
     int prev = -1;
     cudaGetDevice(&prev);
@@ -518,9 +655,9 @@ bfi_status bfi_submit(bfi_server *s, const bfi_lattice *lattice, int64_t nsub, c
     h->srv = s;
     {
         std::lock_guard<std::mutex> lock(s->m);
-        if (s->stopping) {
+        if (s->stopping || s->broken) {
             delete h;
-            return bfi::set_error(BFI_E_BUSY, "server is stopping");
+            return bfi::set_error(BFI_E_BUSY, s->broken ? "the server's scheduler has stopped" : "server is stopping");
         }
         s->queue.push_back(p);
         s->st.submitted++;
@@ -587,6 +724,13 @@ bfi_status bfi_request_get_result(bfi_request *h, double *totals, double *slots,
     if (lo) std::memcpy(lo, r.leaf_lo.data(), sizeof(double) * r.leaf_lo.size());
     if (hi) std::memcpy(hi, r.leaf_hi.data(), sizeof(double) * r.leaf_hi.size());
     if (sub_id) std::memcpy(sub_id, r.leaf_sid.data(), sizeof(uint32_t) * r.leaf_sid.size());
+    return BFI_OK;
+}
+
+bfi_status bfi_request_get_work(bfi_request *h, bfi_work *work) {
+    if (!h || !work) return bfi::set_error(BFI_E_INVALID, "request or work is NULL");
+    std::lock_guard<std::mutex> lock(h->r->m);
+    *work = h->r->work;
     return BFI_OK;
 }
 

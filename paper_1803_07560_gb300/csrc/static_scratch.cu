@@ -32,7 +32,9 @@ std::mutex g_setup_mutex;
 void *g_address[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// device (the first call on a device does this set-up) and kept for the
+// process: a cudaDeviceReset of that device (which unloads the module holding
+// the array) invalidates it, so the entry point must not be used across one.
 bfi_status scratch_address(int device, void **out) {
     if (device < 0 || device >= kMaxDevices) return bfi::set_error(BFI_E_INVALID, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -113,6 +115,7 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
         total += samples[s];
         n_max = samples[s] > n_max ? samples[s] : n_max;
     }
+    if (total >= (1ull << 62)) return bfi::set_error(BFI_E_INVALID, "total sample budget too large");
     const int R = lattice->nx / 2 + 1, K = 2 + 3 * R, d = lattice->nx * lattice->nt;
     const int64_t chunk_samples = bfi::plan_chunk_samples(total);
     int64_t nchunks = 0;

@@ -70,7 +70,7 @@ def test_adaptive_lattice_matches_oracle(bfi, nx, nt, n, seed, conv, half):
     assert np.array_equal(llo, np.array(out.leaves_lo)) and np.array_equal(lhi, np.array(out.leaves_hi))
     o_sl = np.array(out.kept)
     R = nx // 2 + 1
-    assert_slots_close(lsl, o_sl, R, FP64_RTOL, 1e-9)
+    assert_slots_close(lsl, o_sl, R, FP64_RTOL)
     assert_totals_close(g_tot, o_tot, R, FP64_RTOL, 1e-9, m=o_sl[:, 1].max())
 
 

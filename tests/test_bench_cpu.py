@@ -29,20 +29,54 @@ def test_partial_work_is_a_fraction_of_the_full_screen_where_the_split_is_compil
 
 def test_roofline_counts_stage_one_for_all_and_the_rest_for_survivors():
     n, n_eval, ms = 1 << 30, 1_750_000, 14.0
-    one = bench.roofline(n, n_eval, ms, "fp64", 10, 2)
-    two = bench.roofline(n, n_eval, ms, "fp64", 10, 2, screened=n // 5)
+    one = bench.roofline(bench.one_stage_work(n, n_eval), ms, "fp64", 10, 2)
+    two_w = {"samples": n, "stage1": n, "survivors": n // 5, "full_screen": 0, "evaluated": n_eval, "rest_screen": 1}
+    two = bench.roofline(two_w, ms, "fp64", 10, 2)
     t = ms * 1e-3
     integer = bench.eval_ops_fp64(10, 2)[1]
     assert abs(one["achieved"] * 1e9 * t - (n * 400 + n_eval * integer)) < 1e3
     # a survivor draws blocks 0, 2, 3, 4 again: 160 + 32 points + the 12 residuals of sites 0 and 5..9
     assert bench.rest_ops(10, 2) == 160 + 32 + 96
     assert abs(two["achieved"] * 1e9 * t - (n * 208 + (n // 5) * 288 + n_eval * integer)) < 1e3
-    assert two["full_screened"] == n // 5 and one["full_screened"] == n
-    assert two["partial_ops_per_sample"] == 208 and one["partial_ops_per_sample"] is None
+    assert two["survivors"] == n // 5 and one["full_screened"] == n and two["full_screened"] == 0
     assert one["bound"] == "alu" and one["resource"] == "FP32/INT issue"
     assert 0 < two["frac"] < one["frac"]
 
 
+def test_roofline_of_mixed_chunks_and_full_survivor_screens():
+    # a job whose last chunks are too short for stage 1, and survivors screened in full (mass2 != 0)
+    w = {"samples": 1000, "stage1": 700, "survivors": 100, "full_screen": 300, "evaluated": 0, "rest_screen": 0}
+    assert bench.screen_work(w, 10, 2) == 700 * 208 + 300 * 400 + 100 * 400
+    w["rest_screen"] = 1
+    assert bench.screen_work(w, 10, 2) == 700 * 208 + 300 * 400 + 100 * 288
+
+
 def test_fp32_roofline_has_no_fp64_work():
-    r = bench.roofline(1 << 34, 3_000_000, 216.0, "fp32", 10, 2, screened=3_300_000_000)
+    w = {"samples": 1 << 34, "stage1": 1 << 34, "survivors": 3_300_000_000, "full_screen": 0,
+         "evaluated": 3_000_000, "rest_screen": 1}
+    r = bench.roofline(w, 216.0, "fp32", 10, 2)
     assert r["fp64_frac"] == 0 and r["resource"] == "FP32/INT issue"
+
+
+def test_traffic_is_reported_only_for_the_kernel_sources_it_was_measured_on(tmp_path, monkeypatch):
+    f = tmp_path / "t.txt"
+    f.write_text("# a summary\ndram_bytes_per_launch: 12345\nkernel_sources_sha256: " + bench.kernel_sources_sha256() +
+                 "\n")
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.measured_traffic()[0] == 12345
+    f.write_text("dram_bytes_per_launch: 12345\nkernel_sources_sha256: 0000\n")
+    assert bench.measured_traffic()[0] is None
+
+
+def test_summary_is_short_and_last():
+    roof = {"frac": 0.5}
+    fp32 = {"value": 8e10, "roofline": {"frac": 0.53}, "vs_fp64_mode": {"Z_rel": 1e-6, "C_rel_to_C0": [1e-7, -2e-7]},
+            "err_bound": {"Z_rel": 4e-7, "C_rel_to_C0": [5e-7, 6e-7]}}
+    batch = {"value": 3e10, "roofline": {"frac": 0.4}, "ms_per_launch": 340.0}
+    serving = {"rate": 200.0, "jobs": 2000, "p50_ms": 4000.0, "p99_ms": 8000.0, "samples_per_s": 1.6e10, "failed": 0,
+               "roofline": {"frac": 0.3}}
+    tte = {"samples_to_target_C_err_over_C0_max": 1.5e14, "seconds_to_target_C_err_over_C0_max": 1850.0}
+    s = bench.summary(7.7e10, roof, {"value": 7.6e10}, fp32, batch, serving, tte)
+    import json
+    assert len(json.dumps({"summary": s})) < 1000
+    assert s["fp32_err_bound_C"] == 6e-7 and s["fp32_vs_fp64_C_rel_max"] == 2e-7 and s["serving_frac"] == 0.3

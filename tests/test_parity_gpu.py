@@ -1,20 +1,21 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances.  FP64 mode: every sum within 1e-12 relative of the oracle, where
-sums that can cancel (those with P_r, |P_r| <= P_0 per sample) are measured
-against their P_0 counterpart; C(r) within 1e-12 of C(0).  FP32 mode is
-compared with the oracle's FP32-points mode (the identical float points
-evaluated in FP64), within FP32_RTOL = 1e-6, the bound the FP32 path states.
-The records of the two sides use different shifts m_s (the device starts from
-a hint), so sums are compared after moving them to the oracle's shift.
-Statistical error estimates are variances that cancel (to ~0 when one sample
-dominates): the variance of C(r) is a difference of sums of size ~C(0)^2, so
-its square root has an absolute floor of about sqrt(eps) C(0); errors are
-compared at 1e-9 relative or FP64_ERR_ATOL C(0) (FP64), FP32_ERR_ATOL C(0)
-(FP32).  The second-order sums (w^2, w^2 P, w^2 P^2) only feed those errors
-and are compared at the errors' tolerance.  For lattices whose smallest
-action S is large, exp(-S) cannot be reproduced to better than ~eps S
-relative by any FP64 evaluation: the FP64 bound is max(1e-12, 16 eps S).
+Tolerances.  FP64 mode: every per-subvolume sum within 1e-12 relative of the
+oracle, first order (w, w P_r) and second order (w^2, w^2 P_r, w^2 P_r^2)
+alike, where sums with P_r (|P_r| <= P_0 per sample, so their terms are
+bounded by their r = 0 member's) are measured against their P_0 counterpart;
+C(r) within 1e-12 of C(0).  FP32 mode is compared with the oracle's
+FP32-points mode (the identical float points evaluated in FP64), every sum
+within FP32_RTOL = 1e-6, the bound the FP32 path states.  The records of the
+two sides use different shifts m_s (the device starts from a hint), so sums
+are compared after moving them to the oracle's shift.  The stated statistical
+errors are square roots of differences of sums (n sum w^2 - (sum w)^2, and the
+delta-method combination for C(r)) that cancel when the weights are nearly
+equal or one sample dominates C(r)'s variance, so they carry the rounding of
+those sums magnified: they are compared at 1e-9 relative or FP64_ERR_ATOL C(0)
+(FP64) and 1e-4 or FP32_ERR_ATOL C(0) (FP32).  For lattices whose smallest
+action S is large, exp(-S) cannot be reproduced to better than ~eps S relative
+by any FP64 evaluation: the FP64 bound is max(1e-12, 16 eps S).
 """
 import numpy as np
 import pytest
@@ -76,29 +77,50 @@ def cond_rtol(rtol, m, eps):
     return np.maximum(rtol, 16.0 * eps * np.abs(m))
 
 
-def assert_slots_close(g, o, R, rtol, rtol_var, eps=2.0 ** -52):
-    assert np.array_equal(g[:, 0], o[:, 0]), "sample counts differ"
+def slot_deviations(g, o, R, eps=2.0 ** -52):
+    """Largest deviation of each group of sums from the oracle's, after moving
+    the GPU sums to the oracle's shift, relative to the group's scale: the sum
+    itself for sum w and sum w^2 (non-negative terms), the r = 0 member for the
+    sums with P_r (|P_r| <= P_0 per sample, so sum |w^k P_r| <= sum w^k P_0 and
+    sum w^2 P_r^2 <= sum w^2 P_0^2).  Also returns the conditioning bound
+    max(1, 16 eps S_min / rtol) factor per subvolume (see cond_rtol)."""
     used = o[:, 0] > 0
     g, o = g[used], o[used]
-    # the device shift starts at a hint and moves only when beaten by more than
-    # 16: it lies within [min S - 1e-3, min S + 16] (the oracle's is min S)
-    assert np.all(g[:, 1] >= o[:, 1] - 1e-3) and np.all(g[:, 1] <= o[:, 1] + 16.0 + 1e-3)
-    np.testing.assert_allclose(g[:, 2], o[:, 2], rtol=1e-14, atol=1e-14)    # log V_s
-    rt = cond_rtol(rtol, o[:, 1], eps)[:, None]
-    dm = g[:, 1] - o[:, 1]                                                  # express GPU sums in the oracle's shift
+    dm = g[:, 1] - o[:, 1]
     f1, f2 = np.exp(-dm)[:, None], np.exp(-2 * dm)[:, None]
-    sw, sw2 = g[:, 3:4] * f1, g[:, 4:5] * f2
-    swp = g[:, 5:5 + R] * f1
-    sw2p = g[:, 5 + R:5 + 2 * R] * f2
-    sw2p2 = g[:, 5 + 2 * R:] * f2
-    assert np.all(np.abs(sw - o[:, 3:4]) <= rt * o[:, 3:4])
-    # |P_r| <= P_0 per sample: scale the sums with P_r by their r = 0 member
-    assert np.all(np.abs(swp - o[:, 5:5 + R]) <= rt * o[:, 5:6])
-    # second-order sums only feed the error estimates
-    rv = np.maximum(rt, rtol_var)
-    assert np.all(np.abs(sw2 - o[:, 4:5]) <= rv * o[:, 4:5])
-    assert np.all(np.abs(sw2p - o[:, 5 + R:5 + 2 * R]) <= rv * o[:, 5 + R:5 + R + 1])
-    assert np.all(np.abs(sw2p2 - o[:, 5 + 2 * R:]) <= rv * o[:, 5 + 2 * R:5 + 2 * R + 1])
+    sc = lambda x: np.where(x > 0, x, 1.0)
+    dev = {
+        "sw": np.abs(g[:, 3:4] * f1 - o[:, 3:4]) / sc(o[:, 3:4]),
+        "sw2": np.abs(g[:, 4:5] * f2 - o[:, 4:5]) / sc(o[:, 4:5]),
+        "swp": np.abs(g[:, 5:5 + R] * f1 - o[:, 5:5 + R]) / sc(o[:, 5:6]),
+        "sw2p": np.abs(g[:, 5 + R:5 + 2 * R] * f2 - o[:, 5 + R:5 + 2 * R]) / sc(o[:, 5 + R:5 + R + 1]),
+        "sw2p2": np.abs(g[:, 5 + 2 * R:] * f2 - o[:, 5 + 2 * R:]) / sc(o[:, 5 + 2 * R:5 + 2 * R + 1]),
+    }
+    return dev, o[:, 1]
+
+
+def assert_slots_close(g, o, R, rtol, rtol_var=None, eps=2.0 ** -52):
+    """Every sum within rtol of the oracle's (scaled as in slot_deviations),
+    widened only by the conditioning of exp(-S) for large actions.  The
+    first-order sums (w, w P_r) and the second-order ones (w^2, w^2 P_r,
+    w^2 P_r^2) are all sums of terms bounded by their group's scale, so one
+    tolerance holds for all of them; rtol_var, if given, applies to the
+    second-order sums instead.""" 
+    assert np.array_equal(g[:, 0], o[:, 0]), "sample counts differ"
+    used = o[:, 0] > 0
+    # the device shift starts at a hint (an FP32 action, rounded by up to ~4 d 2^-24 S, d <= 512) and moves
+    # down only when beaten by more than 16: to the action in FP64, by whole multiples of ln 2 to within ln 2
+    # below it in FP32; so it lies within [min S - ln 2 - slack, min S + 16 + slack] (the oracle's is min S)
+    gu, ou = g[used], o[used]
+    slack = 1e-3 + 1.2e-4 * np.abs(ou[:, 1])
+    assert np.all(gu[:, 1] >= ou[:, 1] - np.log(2.0) - slack) and np.all(gu[:, 1] <= ou[:, 1] + 16.0 + slack)
+    np.testing.assert_allclose(gu[:, 2], ou[:, 2], rtol=1e-14, atol=1e-14)    # log V_s
+    dev, m = slot_deviations(g, o, R, eps)
+    rt = cond_rtol(rtol, m, eps)[:, None]
+    rv = rt if rtol_var is None else np.maximum(rt, rtol_var)
+    for key, tol in (("sw", rt), ("swp", rt), ("sw2", rv), ("sw2p", rv), ("sw2p2", rv)):
+        bad = dev[key] > tol
+        assert not np.any(bad), f"{key}: deviation {dev[key].max():.3e} > tolerance {np.min(tol):.1e}"
 
 
 def assert_totals_close(g, o, R, rtol, rtol_var, err_atol=None, m=0.0, eps=2.0 ** -52):
@@ -162,19 +184,25 @@ def test_integrate_fp64_ragged(bfi, dev, nx, nt):
     info = plan.info()
     assert info.chunks >= 3 * 2  # several chunks per subvolume, ragged last ones
     assert info.kernel == (1 if (nx, nt) in GENERIC else 0)
-    # the two-stage screen (compiled shapes with >= 3 Philox blocks whose first ~60% complete the neighbourhoods
-    # of at least 35% of the sites, but not all): the full screen sees at least every evaluated sample and at most
-    # all of them
+    # the two-stage screen is compiled for shapes with >= 3 Philox blocks whose first ~60% complete the
+    # neighbourhoods of at least 35% of the sites, but not all; these jobs' chunks hold fewer than 256 rows per
+    # thread, so stage 1 does not run and every sample is screened in one stage (the two-stage runs are
+    # test_two_stage_screen_and_a_flat_action and test_parity_params_gpu.py)
     n_eval, _ = plan.stats()
     full, two = plan.screen_stats()
+    work = plan.work()
     d = nx * nt
     bp = (3 * ((d + 3) // 4) + 4) // 5
     mc = min(4 * bp // nt, nx)
-    assert two == ((nx, nt) not in GENERIC and (d + 3) // 4 >= 3 and mc < nx and 20 * (mc - 2) >= 7 * nx)
-    assert n_eval <= full <= job.total_samples and (two or full == job.total_samples)
+    assert work.two_stage_shape == ((nx, nt) not in GENERIC and (d + 3) // 4 >= 3 and mc < nx and
+                                    20 * (mc - 2) >= 7 * nx)
+    assert not two and full == job.total_samples
+    assert (work.samples, work.stage1, work.survivors, work.full_screen, work.evaluated) == \
+        (job.total_samples, 0, 0, job.total_samples, n_eval)
+    assert n_eval <= job.total_samples
     o_s, o_t = run_oracle(job)
     R = nx // 2 + 1
-    assert_slots_close(g_s, o_s, R, FP64_RTOL, 1e-9)
+    assert_slots_close(g_s, o_s, R, FP64_RTOL)
     assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9, m=o_s[:, 1].max())
 
 
@@ -187,7 +215,7 @@ def test_integrate_fp64_parameters(bfi, dev, nonlinear, mass2, params):
     job.sub_id = np.array([17, 4_000_000_000], dtype=np.uint32)
     g_s, g_t, _ = run_gpu(bfi, dev, job, 0, nonlinear, mass2)
     o_s, o_t = run_oracle(job, False, nonlinear, mass2)
-    assert_slots_close(g_s, o_s, 3, FP64_RTOL, 1e-9)
+    assert_slots_close(g_s, o_s, 3, FP64_RTOL)
     assert_totals_close(g_t, o_t, 3, FP64_RTOL, 1e-9)
 
 
@@ -197,7 +225,7 @@ def test_integrate_fp32_against_fp32_points(bfi, dev, nx, nt):
     g_s, g_t, _ = run_gpu(bfi, dev, job, 1)
     o_s, o_t = run_oracle(job, fp32_points=True)
     R = nx // 2 + 1
-    assert_slots_close(g_s, o_s, R, FP32_RTOL, 1e-4)
+    assert_slots_close(g_s, o_s, R, FP32_RTOL)
     assert_totals_close(g_t, o_t, R, FP32_RTOL, 1e-4, FP32_ERR_ATOL)
 
 
@@ -208,7 +236,7 @@ def test_edge_cases_empty_single_and_tiny(bfi, dev):
     o_s, o_t = run_oracle(job)
     assert g_s[0, 0] == 0 and g_s[0, 3] == 0
     assert np.isinf(g_t[1]) and np.isinf(o_t[1])
-    assert_slots_close(g_s, o_s, 3, FP64_RTOL, 1e-9)
+    assert_slots_close(g_s, o_s, 3, FP64_RTOL)
     assert g_t[0] == pytest.approx(o_t[0], rel=1e-12)
     # without the one-sample subvolume the errors are finite again
     sub = job.subset([0, 2, 3])
@@ -258,7 +286,7 @@ def test_plain_4x2_full_size(bfi, dev):
     job = workloads.plain_4x2()
     g_s, g_t, _ = run_gpu(bfi, dev, job, 0)
     o_s, o_t = run_oracle(job)
-    assert_slots_close(g_s, o_s, 3, FP64_RTOL, 1e-9)
+    assert_slots_close(g_s, o_s, 3, FP64_RTOL)
     assert_totals_close(g_t, o_t, 3, FP64_RTOL, 1e-9)
 
 
@@ -266,10 +294,11 @@ def test_plain_4x2_full_size(bfi, dev):
 def test_paper_10x2_full_size_sampled(bfi, dev, precision):
     job = workloads.paper_10x2()
     g_s, g_t, _ = run_gpu(bfi, dev, job, precision)
-    pick = [0, 517, 1023]
+    # a fixed random subset of 64 of the 1024 subvolumes (subvolumes are independent, so subset parity is exact)
+    pick = np.sort(np.random.default_rng(64).choice(1024, 64, replace=False))
     o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision))
     tol = FP64_RTOL if precision == 0 else FP32_RTOL
-    assert_slots_close(g_s[pick], o_s, 6, tol, 1e-9 if precision == 0 else 1e-4)
+    assert_slots_close(g_s[pick], o_s, 6, tol)
     # totals: the device merge of all 1024 records equals the oracle's merge of them
     o_t = oracle.merge(10, g_s)
     assert_totals_close(g_t, o_t, 6, 1e-13, 1e-9)
@@ -299,6 +328,10 @@ def test_two_stage_screen_and_a_flat_action(bfi, dev, D, mass2, precision):
     n_eval, _ = plan.stats()
     full, two = plan.screen_stats()
     assert two and n_eval <= full <= job.total_samples
+    # every chunk holds 256 rows, so every sample runs stage 1 and 'full' counts the survivors
+    work = plan.work()
+    assert (work.stage1, work.full_screen, work.survivors, work.evaluated) == (job.total_samples, 0, full, n_eval)
+    assert work.two_stage_shape == 1 and work.rest_screen == (1 if mass2 == 0.0 else 0)
     if D > 1.0:
         assert full > 0.9 * job.total_samples
     elif mass2 == 0.0:  # the mass term, left out of P, lets more samples through
@@ -306,5 +339,5 @@ def test_two_stage_screen_and_a_flat_action(bfi, dev, D, mass2, precision):
     pick = [0, 15]
     o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision), mass2=mass2)
     tol = FP64_RTOL if precision == 0 else FP32_RTOL
-    assert_slots_close(g_s[pick], o_s, 6, tol, 1e-9 if precision == 0 else 1e-4)
+    assert_slots_close(g_s[pick], o_s, 6, tol)
     assert_totals_close(g_t, oracle.merge(10, g_s), 6, 1e-13, 1e-9)

@@ -70,7 +70,7 @@ def test_transform_matches_oracle(bfi, nx, nt, mass2, nonlinear):
     o_s, o_t = integrate_mapped(oracle.lattice(nx, nt, nonlinear=nonlinear, mass2=mass2), lo, hi, samples, 7,
                                 sub_id=sid, kind=TRANSFORM)
     R = nx // 2 + 1
-    assert_slots_close(g_s, o_s, R, FP64_RTOL, 1e-9)
+    assert_slots_close(g_s, o_s, R, FP64_RTOL)
     assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9, m=np.abs(o_s[:, 1]).max())
 
 
@@ -92,7 +92,7 @@ def test_transform_ragged_counts_and_edge_boxes(bfi, nx, nt):
     o_s, o_t = integrate_mapped(oracle.lattice(nx, nt), lo, hi, samples, 11, kind=TRANSFORM)
     R = nx // 2 + 1
     assert g_s[0, 0] == 0 and g_s[0, 1] == math.inf and np.all(g_s[0, 3:] == 0.0)
-    assert_slots_close(g_s, o_s, R, FP64_RTOL, 1e-9)
+    assert_slots_close(g_s, o_s, R, FP64_RTOL)
     assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9, m=np.abs(o_s[1:, 1]).max())
 
 
@@ -133,7 +133,7 @@ def test_gaussian_matches_oracle(bfi, nx, nt, sigma, with_mean, factor):
     used = np.isfinite(o_s[:, 1])
     assert np.array_equal(used, np.isfinite(g_s[:, 1]))
     assert np.array_equal(g_s[~used], o_s[~used])
-    assert_slots_close(g_s[used], o_s[used], R, FP64_RTOL, 1e-9)
+    assert_slots_close(g_s[used], o_s[used], R, FP64_RTOL)
     assert_totals_close(g_t, o_t, R, FP64_RTOL, 1e-9, m=np.abs(o_s[used, 1]).max())
 
 

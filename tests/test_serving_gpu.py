@@ -69,8 +69,11 @@ def test_adaptive_splitting_agrees_with_the_oracle_on_the_leaves(bfi, dev):
     req = srv.submit(_lat(bfi, job), job.lo, job.hi, job.samples, job.seed, job.job_id)
     req.wait(60_000)
     info = req.info()
+    work = req.work()
     totals, slots, lo, hi, sid = req.result(leaves=True)
     srv.close()
+    # the counted work covers every pass, split parents included
+    assert work.samples == info.samples and work.full_screen == work.samples and 0 < work.evaluated <= work.samples
     assert info.passes >= 2 and info.nsub_final > job.nsub  # something was split
     # the leaves tile the original boxes
     vol = lambda a, b: np.prod(b - a, axis=1)
@@ -121,3 +124,87 @@ def test_memory_budget(bfi, dev):
         r.wait(60_000)
     assert e.value.status == 2  # BFI_E_NOMEM: can never be admitted
     tiny.close()
+
+
+def _run_all(bfi, srv, jobs, timeout_ms=120_000):
+    """Submits every job, waits for each: {job_id: (totals, leaf slots)} of
+    the jobs that completed and {job_id: status} of those that failed."""
+    reqs = [(j.job_id, srv.submit(_lat(bfi, j), j.lo, j.hi, j.samples, j.seed, j.job_id)) for j in jobs]
+    done, failed = {}, {}
+    for jid, r in reqs:
+        try:
+            r.wait(timeout_ms)
+        except bfi.BfiError as e:
+            failed[jid] = e.status
+            continue
+        t, s, *_ = r.result(leaves=True)
+        done[jid] = (t, s)
+    return done, failed
+
+
+@pytest.mark.parametrize("point,status", [(1, 2), (2, 3), (3, 3)])
+def test_injected_pass_failure_fails_its_job_alone(bfi, dev, point, status):
+    """A pass that fails after admission (its pool allocation, a launch, or the
+    stream status when it completes; the fault is made on the host) fails its
+    own job with a status; every other job completes with the same bits as in
+    a server without the fault; the memory goes back to the budget; shutdown
+    returns within its bound."""
+    import time
+    jobs = _mix(8)
+    ref_srv = bfi.Server(slots=4, precision=1)
+    ref, ref_failed = _run_all(bfi, ref_srv, jobs)
+    ref_srv.close()
+    assert not ref_failed
+    srv = bfi.Server(slots=4, precision=1)
+    srv.inject_fault(point, 3)  # the fourth pass to reach the point fails there
+    done, failed = _run_all(bfi, srv, jobs)
+    assert list(failed.values()) == [status]
+    for jid, (t, s) in done.items():
+        assert np.array_equal(t, ref[jid][0]) and np.array_equal(s, ref[jid][1]), jid
+    st = srv.stats()
+    assert (st.completed, st.failed, st.running, st.queued, st.bytes_in_use) == (len(jobs) - 1, 1, 0, 0, 0)
+    t0 = time.perf_counter()
+    srv.shutdown(10_000)
+    assert time.perf_counter() - t0 < 10.0
+    srv.close()
+
+
+def test_scheduler_failure_ends_every_pending_job(bfi, dev):
+    """If the scheduler thread stops on an error (injected after the third
+    completed pass), the jobs it finished keep their results, every other job
+    fails with BFI_E_NOMEM (no wait is left without an end), new submissions
+    are refused with BFI_E_BUSY, and shutdown returns within its bound."""
+    import time
+    jobs = _mix(12)
+    srv = bfi.Server(slots=2, precision=1)
+    srv.inject_fault(bfi.FAULT_SCHEDULER, 2)
+    done, failed = _run_all(bfi, srv, jobs)
+    assert len(done) == 2 and len(failed) == len(jobs) - 2 and set(failed.values()) == {2}
+    st = srv.stats()
+    assert st.completed == 2 and st.failed == len(jobs) - 2
+    with pytest.raises(bfi.BfiError) as e:
+        srv.submit(_lat(bfi, jobs[0]), jobs[0].lo, jobs[0].hi, jobs[0].samples, 1, 0)
+    assert e.value.status == 6  # BFI_E_BUSY
+    t0 = time.perf_counter()
+    srv.shutdown(10_000)
+    assert time.perf_counter() - t0 < 10.0
+    srv.close()
+
+
+def test_shutdown_is_bounded_while_passes_run(bfi, dev):
+    """shutdown with a short limit while a long pass runs returns BFI_E_TIMEOUT
+    in time; the queued job is cancelled; a later shutdown completes."""
+    import time
+    big = workloads.paper_10x2(1 << 22)  # 2^32 samples in FP64: tens of milliseconds on the device
+    srv = bfi.Server(slots=1, precision=0)
+    a = srv.submit(bfi.lattice(10, 2), big.lo, big.hi, big.samples, big.seed, 1)
+    b = srv.submit(bfi.lattice(10, 2), big.lo, big.hi, big.samples, big.seed, 2)
+    while a.info().state == 0:  # until the first pass is admitted
+        time.sleep(0.001)
+    t0 = time.perf_counter()
+    with pytest.raises(bfi.BfiError) as e:
+        srv.shutdown(1)
+    assert e.value.status == 4 and time.perf_counter() - t0 < 1.0  # BFI_E_TIMEOUT
+    srv.shutdown(60_000)
+    assert a.info().state == 2 and b.info().state == 3
+    srv.close()

@@ -60,6 +60,32 @@ def test_static_scratch_matches_plan_twice(bfi, dev, precision):
             np.testing.assert_allclose(s_slots.cpu().numpy()[:, 3], p_slots[:, 3], rtol=rtol)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_static_scratch_two_stage_screen(bfi, dev, precision):
+    """10x2 with 16 subvolumes of 2^23 samples (2^27 in all, 2048 chunk
+    records, well inside the array): chunks of 256 rows per thread, so the
+    two-stage screen and its survivor queue run on the static scratch's hint
+    and counter layout.  Two calls in a row, each against the plan path."""
+    rtol = FP64_RTOL if precision == 0 else FP32_RTOL
+    lo_np, hi_np = workloads.bisected_boxes(20, 4)
+    samples = np.full(16, 1 << 23, dtype=np.uint64)
+    lat = bfi.lattice(10, 2)
+    lo = torch.tensor(lo_np, device=dev)
+    hi = torch.tensor(hi_np, device=dev)
+    plan = bfi.Plan(lat, samples, precision)
+    p_slots, p_tot = plan.execute(lo, hi, 6)
+    torch.cuda.synchronize()
+    assert plan.screen_stats()[1] and plan.info().chunk_samples == 256 * 256
+    p_slots, p_tot = p_slots.cpu().numpy(), p_tot.cpu().numpy()
+    for _ in range(2):
+        s_slots, s_tot = bfi.integrate_static_scratch(lat, samples, lo, hi, 6, precision=precision)
+        torch.cuda.synchronize()
+        s_slots, s_tot = s_slots.cpu().numpy(), s_tot.cpu().numpy()
+        _close(s_tot, p_tot, rtol, 6)
+        # the same kernels on the same chunks: the records agree bit for bit
+        np.testing.assert_array_equal(s_slots, p_slots)
+
+
 def test_static_scratch_refuses_jobs_beyond_its_size(bfi, dev):
     job = workloads.paper_10x2(1 << 24)   # 2^34 samples: ~131k chunk records, more than 16 MiB
     lat = bfi.lattice(job.nx, job.nt)
