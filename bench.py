@@ -367,8 +367,9 @@ def run_bfi(args):
     if not args.skip_fp32:
         job32 = make_job(rank, world, 1 << (args.samples_log2 + 4))
         plan32 = bfi.Plan(lat, job32.samples, bfi.FP32, device=local_rank)
-        ms32, kern32, _, tot32, work32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
-                                                     max(1, args.warmup // 2), flush_buf, dist, stream)
+        ms32, kern32, slots32, tot32, work32 = timed_steps(plan32, lo, hi, sid, job32, max(1, args.steps // 2),
+                                                           max(1, args.warmup // 2), flush_buf, dist, stream)
+        bound32 = bfi.error_bound(lat, bfi.FP32, slots32, 5.0)
         roof32 = roofline(work32, kern32, "fp32", NX, NT)
         roof32["kernel"] = f"hint + integrand FP32 <{NX},{NT}>"
         plan32.close()
@@ -383,6 +384,8 @@ def run_bfi(args):
                 "ms_per_step": ms32, "samples_per_subvolume": int(job32.samples[0]),
                 "dtype": "f32 (compensated sums, f64 shift and merge)", "roofline": roof32,
                 "logZ": float(t32[0]), "C": [float(x) for x in t32[4:4 + R]],
+                "err_bound": {"Z_rel": float(bound32[0]), "C_rel_to_C0": [float(x) for x in bound32[1:]],
+                              "note": "stated arithmetic error of this result (bfi_error_bound)"},
                 "vs_fp64_mode": {"Z_rel": float(np.expm1(t32[0] - t64[0])),
                                  "C_rel_to_C0": [float(x) for x in (t32[4:4 + R] - t64[4:4 + R]) / t64[4]],
                                  "note": "FP64 mode draws FP64 points; the FP32 arithmetic bound (1e-6) is "

@@ -50,18 +50,21 @@
  *    weight (the FP32 screen under Negligible weights decides which):
  *    its FP64 point, action, products and weight, accumulated in double.
  *    BFI_FP32 evaluates the points, the action, the products and the weights
- *    in float, accumulates per thread in Kahan-compensated float, and merges
- *    in double.  In both the shift m_s starts at the smallest FP32 action
- *    among the subvolume's first n_s/32 samples (256 to 4096) and moves down
- *    only when a sample beats it by more than 16, so it lies within
- *    [min S - 1e-3, min S + 16] (the records do not depend on its exact
- *    value beyond rounding).  In BFI_FP32, samples whose
- *    FP32 action lies within 28 of the smallest action seen get the action
- *    recomputed in compensated FP32 (pairs of floats carrying the rounding
- *    error, about 2^-44 relative); every other sample has a weight below
- *    e^-28 of the largest.  The stated bound of the FP32 path, against the
- *    FP64 evaluation of the same float points, is 1e-6 relative on Z and on
- *    C(r) (relative to C(0)).
+ *    in float, accumulates per thread in Kahan-compensated float, and keeps
+ *    the log-weight shift and the merges in double: the action in
+ *    compensated float (pairs of floats carrying the rounding error), the
+ *    weight from an exactly split argument, the products as compensated dot
+ *    products.  In both the shift m_s starts at the smallest FP32 action
+ *    among the subvolume's first n_s/32 samples (256 to 4096; that action is
+ *    rounded by up to ~4 d 2^-24 S) and moves down only when a sample beats
+ *    it by more than 16: in BFI_FP64 to that sample's action, in BFI_FP32 by
+ *    whole multiples of ln 2 to within ln 2 below it, so that the float sums
+ *    rescale exactly (the records do not depend on its exact value beyond
+ *    rounding).  The stated arithmetic error of each result, against the
+ *    same estimator evaluated exactly on the same points, is what
+ *    bfi_error_bound returns: in BFI_FP32 below 1e-6 relative on Z and on
+ *    C(r) (relative to C(0)) for the 4x2 and 10x2 lattices, larger for big
+ *    lattices at large actions.
  *  - Negligible weights: a sample whose action exceeds the subvolume's
  *    smallest action by more than W = c + ln(n_max) (n_max the largest
  *    budget of the plan; c = 34 in BFI_FP64, 20 in BFI_FP32) has weight below
