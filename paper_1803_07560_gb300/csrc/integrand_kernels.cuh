@@ -646,18 +646,13 @@ struct ChunkShared {
 // ---------------------------------------------------------------------------
 constexpr int kQueueCap = 64;
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
 // Appends this lane's candidate (if any) to the warp's queue; returns the new
-// count.  Needs count < 32 on entry (then count < 64 = kQueueCap on exit).
-__device__ __forceinline__ int enqueue(uint32_t *q, int count, bool cand, uint32_t k) {
+// count.  lt = the lanes below this one ((1 << lane) - 1, computed once per
+// kernel).  Needs count < 32 on entry (then count < 64 = kQueueCap on exit).
+__device__ __forceinline__ int enqueue(uint32_t *q, int count, bool cand, uint32_t k, unsigned lt) {
     const unsigned mask = __ballot_sync(0xffffffffu, cand);
     if (mask == 0u) return count;  // the common case: no candidate in the row (warp-uniform)
-    if (cand) q[count + __popc(mask & lanemask_lt())] = k;
+    if (cand) q[count + __popc(mask & lt)] = k;
     __syncwarp();
     return count + __popc(mask);
 }
@@ -674,11 +669,12 @@ __device__ __forceinline__ int dequeue32(uint32_t *q, int count) {
 
 // The same for a queue that carries a float beside each entry (a survivor
 // and its partial action).
-__device__ __forceinline__ int enqueue_pair(uint32_t *q, float *pq, int count, bool cand, uint32_t k, float p) {
+__device__ __forceinline__ int enqueue_pair(uint32_t *q, float *pq, int count, bool cand, uint32_t k, float p,
+                                            unsigned lt) {
     const unsigned mask = __ballot_sync(0xffffffffu, cand);
     if (mask == 0u) return count;
     if (cand) {
-        const int at = count + __popc(mask & lanemask_lt());
+        const int at = count + __popc(mask & lt);
         q[at] = k;
         pq[at] = p;
     }
@@ -730,6 +726,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
     __shared__ uint32_t s_squeue[PartialScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];
     __shared__ float s_pqueue[RestScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];  // survivors' partial actions
     const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;  // the lanes below this one
     uint32_t *queue = s_queue[tid >> 5];
     uint32_t *squeue = s_squeue[PartialScreen<NX, NT>::enabled ? tid >> 5 : 0];
     float *pqueue = s_pqueue[RestScreen<NX, NT>::enabled ? tid >> 5 : 0];
@@ -760,10 +757,12 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
 
         unsigned n_eval = 0;
         int count = 0;
+        // low index word of the chunk's first sample: sample offset k has word xb + k (chunks never cross 2^32)
+        const uint32_t xb = static_cast<uint32_t>(v.first);
         // FP64 evaluation of queue entry 'lane' (a sample offset in the chunk)
         auto evaluate = [&](uint32_t k) {
             uint32_t w[D];
-            sample_words_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, w);
+            sample_words_pre<D>(xb + k, s_pre, rk, w);
             double u[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) u[j] = Coord<double>::map(w[j], s_lo[j], s_w[j]);
@@ -792,12 +791,12 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
             bool cand = false;
             if (valid) {
                 ++n_full;
-                const uint32_t x = static_cast<uint32_t>(v.first + k);
+                const uint32_t x = xb + k;
                 const float S_f = rest ? P_f + rest_action<NX, NT, MapScreen>(x, s_pre, rk, s_box, lcf)
                                        : screen_action<NX, NT, MapScreen>(x, s_pre, rk, s_box, lcf);
                 cand = __fmaf_rn(-1e-3f, S_f, S_f) <= thr;  // S_f <= m_ref + window + 1 + 0.1% of S_f
             }
-            count = enqueue(queue, count, cand, k);
+            count = enqueue(queue, count, cand, k, lt);
             if (count >= 32) {
                 evaluate(queue[lane]);
                 count = dequeue32(queue, count);
@@ -806,38 +805,53 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
             }
         };
         int scount = 0;  // stage-1 survivors waiting for the full screen
-        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
+        const uint32_t nrows = static_cast<uint32_t>((v.cnt + BLOCK - 1) / BLOCK);
+        const uint32_t nfull = static_cast<uint32_t>(v.cnt / BLOCK);  // rows in which every thread has a sample
         const bool two_stage = PartialScreen<NX, NT>::enabled && nrows >= kTwoStageMinRows;
-        for (uint64_t row = 0; row < nrows; ++row) {
-            const uint64_t k = row * BLOCK + tid;
-            if (two_stage) {
-                bool surv = false;
-                float P_f = 0.f;
-                if (k < v.cnt) {
-                    P_f = partial_action<NX, NT, MapScreen>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box,
-                                                            lcf);
-                    surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
-                }
-                if constexpr (RestScreen<NX, NT>::enabled) {
-                    scount = enqueue_pair(squeue, pqueue, scount, surv, static_cast<uint32_t>(k), P_f);
-                    if (scount >= 32) {
-                        screen(squeue[lane], true, rest_ok, pqueue[lane]);
-                        scount = dequeue32_pair(squeue, pqueue, scount);
-                    }
-                } else {
-                    scount = enqueue(squeue, scount, surv, static_cast<uint32_t>(k));
-                    if (scount >= 32) {
-                        screen(squeue[lane], true, false, 0.f);
-                        scount = dequeue32(squeue, scount);
-                    }
+        // Stage 1 of one row: this thread's sample offset k ('valid' false past the chunk's end), its partial
+        // action, the survivor queue.
+        auto stage1_row = [&](uint32_t k, bool valid) {
+            bool surv = false;
+            float P_f = 0.f;
+            if (valid) {
+                P_f = partial_action<NX, NT, MapScreen>(xb + k, s_pre, rk, s_box, lcf);
+                surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
+            }
+            if constexpr (RestScreen<NX, NT>::enabled) {
+                scount = enqueue_pair(squeue, pqueue, scount, surv, k, P_f, lt);
+                if (scount >= 32) {
+                    screen(squeue[lane], true, rest_ok, pqueue[lane]);
+                    scount = dequeue32_pair(squeue, pqueue, scount);
                 }
             } else {
-                screen(static_cast<uint32_t>(k), k < v.cnt, false, 0.f);
+                scount = enqueue(squeue, scount, surv, k, lt);
+                if (scount >= 32) {
+                    screen(squeue[lane], true, false, 0.f);
+                    scount = dequeue32(squeue, scount);
+                }
             }
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
-                share_min(&sh.min_bits, m_ref);
-                thr = m_ref + args.skip_window + 1.0f;
+        };
+        auto one_stage_row = [&](uint32_t k, bool valid) { screen(k, valid, false, 0.f); };
+        // The rows in blocks of kShareRows, the CTA sharing its smallest action between blocks; in each block the
+        // full rows first (no bounds check), then the chunk's ragged last row if it falls there.
+        auto rows = [&](auto step) {
+            for (uint32_t r0 = 0; r0 < nrows; r0 += kShareRows) {
+                const uint32_t r1 = min(r0 + static_cast<uint32_t>(kShareRows), nrows), rf = min(r1, nfull);
+                for (uint32_t row = r0; row < rf; ++row) step(row * BLOCK + tid, true);
+                for (uint32_t row = rf; row < r1; ++row) step(row * BLOCK + tid, row * BLOCK + tid < v.cnt);
+                if (r1 < nrows) {
+                    share_min(&sh.min_bits, m_ref);
+                    thr = m_ref + args.skip_window + 1.0f;
+                }
             }
+        };
+        if constexpr (PartialScreen<NX, NT>::enabled) {
+            if (two_stage)
+                rows(stage1_row);
+            else
+                rows(one_stage_row);
+        } else {
+            rows(one_stage_row);
         }
         if (scount > 0)  // survivors still queued
             screen(lane < scount ? squeue[lane] : 0u, lane < scount, rest_ok,
@@ -880,6 +894,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
     __shared__ uint32_t s_squeue[PartialScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];
     __shared__ float s_pqueue[RestScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];  // survivors' partial actions
     const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;  // the lanes below this one
     uint32_t *queue = s_queue[tid >> 5];
     uint32_t *squeue = s_squeue[PartialScreen<NX, NT>::enabled ? tid >> 5 : 0];
     float *pqueue = s_pqueue[RestScreen<NX, NT>::enabled ? tid >> 5 : 0];
@@ -904,9 +919,11 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
 
         unsigned n_eval = 0;
         int count = 0;
+        // low index word of the chunk's first sample: sample offset k has word xb + k (chunks never cross 2^32)
+        const uint32_t xb = static_cast<uint32_t>(v.first);
         auto evaluate = [&](uint32_t k) {
             float u[D];
-            make_point_pre<D>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, u);
+            make_point_pre<D>(xb + k, s_pre, rk, s_box, u);
             const DF S = action_df<NX, NT>(u, lcd);
             m_ref = fminf(m_ref, S.h);
             const double S_d = static_cast<double>(S.h) + static_cast<double>(S.l);
@@ -929,11 +946,11 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
             n_full += valid ? 1u : 0u;
             bool cand = false;
             if (valid) {
-                const uint32_t x = static_cast<uint32_t>(v.first + k);
+                const uint32_t x = xb + k;
                 cand = (rest ? P_f + rest_action<NX, NT, MapF32>(x, s_pre, rk, s_box, lc)
                              : screen_action<NX, NT, MapF32>(x, s_pre, rk, s_box, lc)) <= thr;
             }
-            count = enqueue(queue, count, cand, k);
+            count = enqueue(queue, count, cand, k, lt);
             if (count >= 32) {
                 evaluate(queue[lane]);
                 count = dequeue32(queue, count);
@@ -942,37 +959,53 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
             }
         };
         int scount = 0;  // stage-1 survivors waiting for the full screen
-        const uint64_t nrows = (v.cnt + BLOCK - 1) / BLOCK;
+        const uint32_t nrows = static_cast<uint32_t>((v.cnt + BLOCK - 1) / BLOCK);
+        const uint32_t nfull = static_cast<uint32_t>(v.cnt / BLOCK);  // rows in which every thread has a sample
         const bool two_stage = PartialScreen<NX, NT>::enabled && nrows >= kTwoStageMinRows;
-        for (uint64_t row = 0; row < nrows; ++row) {
-            const uint64_t k = row * BLOCK + tid;
-            if (two_stage) {
-                bool surv = false;
-                float P_f = 0.f;
-                if (k < v.cnt) {  // 0.1% slack: the partial and full sums add in different orders
-                    P_f = partial_action<NX, NT, MapF32>(static_cast<uint32_t>(v.first + k), s_pre, rk, s_box, lc);
-                    surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
-                }
-                if constexpr (RestScreen<NX, NT>::enabled) {
-                    scount = enqueue_pair(squeue, pqueue, scount, surv, static_cast<uint32_t>(k), P_f);
-                    if (scount >= 32) {
-                        screen(squeue[lane], true, rest_ok, pqueue[lane]);
-                        scount = dequeue32_pair(squeue, pqueue, scount);
-                    }
-                } else {
-                    scount = enqueue(squeue, scount, surv, static_cast<uint32_t>(k));
-                    if (scount >= 32) {
-                        screen(squeue[lane], true, false, 0.f);
-                        scount = dequeue32(squeue, scount);
-                    }
+        // Stage 1 of one row: this thread's sample offset k ('valid' false past the chunk's end), its partial
+        // action, the survivor queue.
+        auto stage1_row = [&](uint32_t k, bool valid) {
+            bool surv = false;
+            float P_f = 0.f;
+            if (valid) {
+                P_f = partial_action<NX, NT, MapF32>(xb + k, s_pre, rk, s_box, lc);
+                surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
+            }
+            if constexpr (RestScreen<NX, NT>::enabled) {
+                scount = enqueue_pair(squeue, pqueue, scount, surv, k, P_f, lt);
+                if (scount >= 32) {
+                    screen(squeue[lane], true, rest_ok, pqueue[lane]);
+                    scount = dequeue32_pair(squeue, pqueue, scount);
                 }
             } else {
-                screen(static_cast<uint32_t>(k), k < v.cnt, false, 0.f);
+                scount = enqueue(squeue, scount, surv, k, lt);
+                if (scount >= 32) {
+                    screen(squeue[lane], true, false, 0.f);
+                    scount = dequeue32(squeue, scount);
+                }
             }
-            if ((row % kShareRows) == kShareRows - 1 && row + 1 < nrows) {
-                share_min(&sh.min_bits, m_ref);
-                thr = m_ref + args.skip_window;
+        };
+        auto one_stage_row = [&](uint32_t k, bool valid) { screen(k, valid, false, 0.f); };
+        // The rows in blocks of kShareRows, the CTA sharing its smallest action between blocks; in each block the
+        // full rows first (no bounds check), then the chunk's ragged last row if it falls there.
+        auto rows = [&](auto step) {
+            for (uint32_t r0 = 0; r0 < nrows; r0 += kShareRows) {
+                const uint32_t r1 = min(r0 + static_cast<uint32_t>(kShareRows), nrows), rf = min(r1, nfull);
+                for (uint32_t row = r0; row < rf; ++row) step(row * BLOCK + tid, true);
+                for (uint32_t row = rf; row < r1; ++row) step(row * BLOCK + tid, row * BLOCK + tid < v.cnt);
+                if (r1 < nrows) {
+                    share_min(&sh.min_bits, m_ref);
+                    thr = m_ref + args.skip_window;
+                }
             }
+        };
+        if constexpr (PartialScreen<NX, NT>::enabled) {
+            if (two_stage)
+                rows(stage1_row);
+            else
+                rows(one_stage_row);
+        } else {
+            rows(one_stage_row);
         }
         if (scount > 0)  // survivors still queued
             screen(lane < scount ? squeue[lane] : 0u, lane < scount, rest_ok,
