@@ -70,8 +70,9 @@
  *    budget of the plan; c = 34 in BFI_FP64, 20 in BFI_FP32) has weight below
  *    e^-W of the largest, and all such samples together move any sum by less
  *    than e^-c relative.  They are counted in n_s but left out of the sums.
- *    BFI_FP64 decides this from the FP32 action of the FP32 point with a
- *    margin of 1 + 0.1% of S, far above the difference between the two.
+ *    Both modes decide this from an FP32 action of a float point with a
+ *    margin of 1 + 0.1% of S, far above its difference from the action the
+ *    evaluation computes.
  *    The reference action starts at the smallest FP32 action among each
  *    subvolume's first n_s/32 samples (256 to 4096) and follows the smallest evaluated
  *    action, shared at fixed points of the sample loop, so the outcome is

@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
                     sd[2 + 2 * g.R + r] += wq * wq;
                 });
             } else {
-                if (!(S_f <= m_ref + args.skip_window)) continue;
+                // the screen's margin, as in FP64 mode: no sample within the window is dropped
+                if (!(S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f)) continue;
                 if constexpr (SPL > 0)  // the evaluation reads the point from shared memory
                     warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
                 // every candidate: compensated action, exact power-of-two shift moves, split-argument weight

@@ -249,14 +249,12 @@ __device__ __forceinline__ void make_pairs_pre(uint32_t x, const PhiloxPrefix *p
     }
 }
 
-// The FP32 point (Coord<float>::map), and the FP64 kernel's screen point
-// y = fmaf(1.m, w, lo') with 1.m the word's top 23 bits as a float in [1,2)
-// and lo' = lo - (1 - 2^-24) w folded per chunk into the box table, one
-// operation fewer per coordinate; it differs from the FP32 point by the
-// rounding of lo' (under 1e-6 here), which the screen's margin covers.
-struct MapF32 {
-    __device__ __forceinline__ float operator()(uint32_t w, float2 bw) const { return Coord<float>::map(w, bw.x, bw.y); }
-};
+// The screen point of both kernels: y = fmaf(1.m, w, lo') with 1.m the
+// word's top 23 bits as a float in [1,2) and lo' = lo - (1 - 2^-24) w folded
+// per chunk into the screen's box table, one operation fewer per coordinate
+// than the exact FP32 point (Coord<float>::map, which the FP32 evaluation
+// uses); it differs from that point by the rounding of lo' (under 1e-6 here),
+// which the screen's margin covers.
 struct MapScreen {
     __device__ __forceinline__ float operator()(uint32_t w, float2 bw) const {
         return __fmaf_rn(__uint_as_float(0x3f800000u | (w >> 9)), bw.y, bw.x);
@@ -485,6 +483,7 @@ __device__ __forceinline__ void add_stage1(unsigned long long *stage1, uint64_t 
 // enough for three CTAs per SM.
 // ---------------------------------------------------------------------------
 constexpr int kShareRows = 64;
+constexpr float kMarginInv = 1.0f / 0.999f;  // the screen's 0.1% margin folded into its threshold
 constexpr float kRescaleMargin = 16.f;
 
 __device__ __forceinline__ float warp_min(float x) {
@@ -719,7 +718,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
     constexpr int WARPS = BLOCK / 32;
     __shared__ ChunkShared<BLOCK> sh;
     __shared__ double s_lo[D], s_w[D];
-    __shared__ float2 s_box[D];  // (lo', width) as floats for the FP32 screen (MapScreen)
+    __shared__ __align__(16) float2 s_box[D];  // (lo', width) as floats for the FP32 screen (MapScreen)
     __shared__ PhiloxPrefix s_pre[(D + 3) / 4];
     __shared__ double s_sums[K * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
@@ -782,6 +781,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         // m_ref changes only where the queue is evaluated (then made uniform
         // across the warp) and where the CTA shares it; thr follows it
         float thr = m_ref + args.skip_window + 1.0f;
+        // x (1 - 1e-3) <= thr, the screen's 0.1% margin, as x <= thr / (1 - 1e-3)
+        float thr_m = thr * kMarginInv;
         // full screen of sample offset k (valid lanes) and the candidate queue
         unsigned n_full = 0;
         // full screen of sample offset k (valid lanes), or with rest (warp-uniform) the survivor's partial
@@ -794,7 +795,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
                 const uint32_t x = xb + k;
                 const float S_f = rest ? P_f + rest_action<NX, NT, MapScreen>(x, s_pre, rk, s_box, lcf)
                                        : screen_action<NX, NT, MapScreen>(x, s_pre, rk, s_box, lcf);
-                cand = __fmaf_rn(-1e-3f, S_f, S_f) <= thr;  // S_f <= m_ref + window + 1 + 0.1% of S_f
+                cand = S_f <= thr_m;  // S_f <= m_ref + window + 1 + 0.1% of S_f
             }
             count = enqueue(queue, count, cand, k, lt);
             if (count >= 32) {
@@ -802,6 +803,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
                 count = dequeue32(queue, count);
                 m_ref = warp_min(m_ref);
                 thr = m_ref + args.skip_window + 1.0f;
+                thr_m = thr * kMarginInv;
             }
         };
         int scount = 0;  // stage-1 survivors waiting for the full screen
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
             float P_f = 0.f;
             if (valid) {
                 P_f = partial_action<NX, NT, MapScreen>(xb + k, s_pre, rk, s_box, lcf);
-                surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
+                surv = P_f <= thr_m;
             }
             if constexpr (RestScreen<NX, NT>::enabled) {
                 scount = enqueue_pair(squeue, pqueue, scount, surv, k, P_f, lt);
@@ -842,6 +844,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
                 if (r1 < nrows) {
                     share_min(&sh.min_bits, m_ref);
                     thr = m_ref + args.skip_window + 1.0f;
+                    thr_m = thr * kMarginInv;
                 }
             }
         };
@@ -887,7 +890,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
     constexpr int WARPS = BLOCK / 32;
     using Sums = SmemSums<float, K, BLOCK>;
     __shared__ ChunkShared<BLOCK> sh;
-    __shared__ float2 s_box[D];  // (lo, width) as floats; every thread reads the same word
+    __shared__ __align__(16) float2 s_box[D];  // (lo, width) as floats: the evaluation's exact points
+    __shared__ __align__(16) float2 s_scr[D];  // (lo', width): the screen's points (MapScreen)
     __shared__ PhiloxPrefix s_pre[(D + 3) / 4];
     __shared__ float s_sums[Sums::WORDS * BLOCK];
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
@@ -902,7 +906,12 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
 
     for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
         const ChunkView v = chunk_view(args, c, D);
-        if (tid < D) BoxPair<float>::load(v.lo, v.hi, tid, s_box[tid].x, s_box[tid].y);
+        if (tid < D) {
+            float lo_f, w_f;
+            BoxPair<float>::load(v.lo, v.hi, tid, lo_f, w_f);
+            s_box[tid] = make_float2(lo_f, w_f);
+            s_scr[tid] = make_float2(__fmaf_rn(-0.99999994f, w_f, lo_f), w_f);
+        }
         chunk_prefixes<D>(v, rk, s_pre);
         const float hint = args.hint[v.s];
         float m_ref = hint;
@@ -938,8 +947,14 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
             ++n_eval;
         };
         // m_ref changes only where the queue is evaluated (then made uniform
-        // across the warp) and where the CTA shares it; thr follows it
-        float thr = m_ref + args.skip_window;
+        // across the warp) and where the CTA shares it; thr follows it.  The
+        // screen keeps a sample when its screen action, less 0.1%, is within
+        // the window plus 1 of m_ref: that margin bounds the screen's error
+        // against the evaluation's exact float action (its own rounding,
+        // ~(d + 10) 2^-24 S, and the folded point, |dy| < 2^-22 |y|), so no
+        // sample within the window is dropped.
+        float thr = m_ref + args.skip_window + 1.0f;
+        float thr_m = thr * kMarginInv;
         unsigned n_full = 0;
         const bool rest_ok = RestScreen<NX, NT>::enabled && lc.half_mass2 == 0.f;
         auto screen = [&](uint32_t k, bool valid, bool rest, float P_f) {
@@ -947,15 +962,16 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
             bool cand = false;
             if (valid) {
                 const uint32_t x = xb + k;
-                cand = (rest ? P_f + rest_action<NX, NT, MapF32>(x, s_pre, rk, s_box, lc)
-                             : screen_action<NX, NT, MapF32>(x, s_pre, rk, s_box, lc)) <= thr;
+                cand = (rest ? P_f + rest_action<NX, NT, MapScreen>(x, s_pre, rk, s_scr, lc)
+                             : screen_action<NX, NT, MapScreen>(x, s_pre, rk, s_scr, lc)) <= thr_m;
             }
             count = enqueue(queue, count, cand, k, lt);
             if (count >= 32) {
                 evaluate(queue[lane]);
                 count = dequeue32(queue, count);
                 m_ref = warp_min(m_ref);
-                thr = m_ref + args.skip_window;
+                thr = m_ref + args.skip_window + 1.0f;
+                thr_m = thr * kMarginInv;
             }
         };
         int scount = 0;  // stage-1 survivors waiting for the full screen
@@ -968,8 +984,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
             bool surv = false;
             float P_f = 0.f;
             if (valid) {
-                P_f = partial_action<NX, NT, MapF32>(xb + k, s_pre, rk, s_box, lc);
-                surv = __fmaf_rn(-1e-3f, P_f, P_f) <= thr;
+                P_f = partial_action<NX, NT, MapScreen>(xb + k, s_pre, rk, s_scr, lc);
+                surv = P_f <= thr_m;
             }
             if constexpr (RestScreen<NX, NT>::enabled) {
                 scount = enqueue_pair(squeue, pqueue, scount, surv, k, P_f, lt);
@@ -995,7 +1011,8 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
                 for (uint32_t row = rf; row < r1; ++row) step(row * BLOCK + tid, row * BLOCK + tid < v.cnt);
                 if (r1 < nrows) {
                     share_min(&sh.min_bits, m_ref);
-                    thr = m_ref + args.skip_window;
+                    thr = m_ref + args.skip_window + 1.0f;
+                    thr_m = thr * kMarginInv;
                 }
             }
         };
@@ -1030,7 +1047,7 @@ __global__ void __launch_bounds__(kBlock) hint_f32(const IntegrandArgs args, con
                                                    const RoundKeys rk) {
     constexpr int D = NX * NT;
     __shared__ int s_min;
-    __shared__ float2 s_box[D];
+    __shared__ __align__(16) float2 s_box[D];
     const int64_t s = blockIdx.x;
     if (threadIdx.x == 0) s_min = __float_as_int(INFINITY);
     if (threadIdx.x < D) BoxPair<float>::load(args.lo + s * D, args.hi + s * D, threadIdx.x, s_box[threadIdx.x].x,
