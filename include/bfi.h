@@ -459,8 +459,11 @@ typedef enum {
 bfi_status bfi_server_inject_fault(bfi_server *server, int32_t point, int64_t nth);
 bfi_status bfi_server_get_stats(bfi_server *server, bfi_server_stats *stats);
 
-/* Queues a job; host arrays (lo, hi [nsub * d], samples [nsub]) are copied
- * before the call returns.  *out is the caller's handle (release it with
+/* Queues a job: the integration request of Sec. 3 (the lattice of Eq. (Gen2)
+ * with the parameters of Sec. 2, the extents of its subvolumes and their
+ * sample budgets), to be subdivided further where it has not converged, as
+ * the paper's wrapper does.  Host arrays (lo, hi [nsub * d], samples [nsub])
+ * are copied before the call returns.  *out is the caller's handle (release it with
  * bfi_request_release).  Errors: BFI_E_INVALID, BFI_E_UNSUPPORTED, BFI_E_BUSY
  * (server stopping). */
 bfi_status bfi_submit(bfi_server *server, const bfi_lattice *lattice, int64_t nsub, const double *lo,
@@ -492,8 +495,10 @@ bfi_status bfi_request_release(bfi_request *request);
 /* ------------------------------------------------------------------------ */
 
 /* A context binds a device and a CUDA stream it creates, and caches the plan
- * and device buffers of the last job shape it ran.  A context is used by one
- * thread at a time; a concurrent call returns BFI_E_BUSY.
+ * and device buffers of the last job shape it ran: it stands for the paper's
+ * integrand program (Sec. 3), which is started once and then answers one
+ * integration request after another.  A context is used by one thread at a
+ * time; a concurrent call returns BFI_E_BUSY.
  * Errors: BFI_E_INVALID, BFI_E_NOMEM, BFI_E_CUDA. */
 typedef struct bfi_ctx bfi_ctx;
 
@@ -506,8 +511,12 @@ bfi_status bfi_ctx_destroy(bfi_ctx *ctx);
  * bfi_integrate. */
 bfi_status bfi_ctx_set_sampler(bfi_ctx *ctx, const bfi_sampler *sampler, int32_t d);
 
-/* Integrate one job with host inputs and outputs: copies the bounds in, runs
- * the plan (re-planned only when the lattice, precision or budgets change),
+/* Integrate one job with host inputs and outputs, the request of Sec. 3 (a
+ * number of samples and the extent of each integration volume in, the
+ * result and its error out), for the lattice of Eq. (Gen2) with the
+ * parameters of Sec. 2, over the subvolumes whose results add up to the
+ * integral over their union (Sec. 1 and 3): copies the bounds in, runs the
+ * plan (re-planned only when the lattice, precision or budgets change),
  * copies the results out and waits for them.
  *   lo, hi   host [nsub * d]     samples host [nsub]     sub_id host [nsub] or NULL
  *   slots    host [nsub * slot_len] or NULL (then not copied back)

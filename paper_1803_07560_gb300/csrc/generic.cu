@@ -39,7 +39,7 @@ GenShape gen_shape(int nx, int nt) {
 
 // Dynamic shared memory layout of one CTA (byte offsets, 16-aligned).
 struct GenLayout {
-    int next, box_f, lo_d, w_d, uf, ud, sums, mw, fac, mean, zb, total;
+    int next, box_f, lo_d, w_d, uf, ud, sums, mw, pre4, pre1, fac, mean, zb, total;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
@@ -59,6 +59,8 @@ __host__ __device__ inline GenLayout gen_layout(const GenShape &g, int mapped = 
     L.ud = o;    o = align16(o + 8 * g.dpad * kGWarps);       // double point per warp
     L.sums = o;  o = align16(o + 8 * (g.K + g.R + 1) * kGWarps);  // per-warp sums (FP64, or FP32 sums + comps)
     L.mw = o;    o = align16(o + 8 * kGWarps + 8);             // per-warp shift, counter
+    L.pre4 = o;  o = align16(o + 16 * g.nq);                   // Philox prefixes of the chunk (lane screen):
+    L.pre1 = o;  o = align16(o + 4 * g.nq);                    //   words a, g, fk, h as uint4, then l3
     L.fac = o;   if (gauss) o = align16(o + 8 * g.d * g.d);   // factor F, row-major
     L.mean = o;  if (gauss) o = align16(o + 8 * g.d);         // mean
     L.zb = o;    if (mapped) o = align16(o + 8 * g.dpad * kGWarps);  // per warp: y of the range map, or u then z
@@ -252,15 +254,19 @@ struct LaneScreen {
         }
     }
 
-    __device__ __forceinline__ float action(uint64_t i, uint32_t sid, const RoundKeys &rk,
+    // Where block q = lane (C/4) + b of the chunk keeps its Philox prefix: at
+    // b 32 + lane, so that the lanes of a warp read consecutive words.
+    __host__ __device__ static int prefix_slot(int q) { return (q % (C / 4)) * 32 + q / (C / 4); }
+
+    __device__ __forceinline__ float action(uint64_t i, const uint4 *pre4, const uint32_t *pre1, const RoundKeys &rk,
                                             const LatticeConst<float> &cf) const {
         const int lane = threadIdx.x & 31;
         float X[C];  // X[s NT + l]
 #pragma unroll
         for (int b = 0; b < C / 4; ++b) {
-            const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(lane * (C / 4) + b), static_cast<uint32_t>(i),
-                                                     static_cast<uint32_t>(i >> 32), sid),
-                                          rk);
+            const uint4 a = pre4[b * 32 + lane];
+            const PhiloxPrefix p{a.x, a.y, a.z, a.w, pre1[b * 32 + lane], {0u, 0u, 0u}};
+            const uint4 r = philox_from_prefix(static_cast<uint32_t>(i), p, rk);
             X[4 * b + 0] = Coord<float>::map(r.x, lo[4 * b + 0], w[4 * b + 0]);
             X[4 * b + 1] = Coord<float>::map(r.y, lo[4 * b + 1], w[4 * b + 1]);
             X[4 * b + 2] = Coord<float>::map(r.z, lo[4 * b + 2], w[4 * b + 2]);
@@ -329,6 +335,7 @@ struct LaneScreen {
 // Placeholder screen of the shared-memory path (SPL = 0).
 struct NoLaneScreen {
     __device__ __forceinline__ void load(const float2 *) {}
+    __host__ __device__ static int prefix_slot(int q) { return q; }
 };
 template <int SPL, int NT>
 struct ScreenOf {
@@ -377,6 +384,19 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
         __syncthreads();
         typename ScreenOf<SPL, NT>::type scr;
         scr.load(bf);
+        // the chunk's Philox prefixes: the sample index's high word and the sub_id are fixed within a chunk
+        uint4 *pre4 = reinterpret_cast<uint4 *>(sm + L.pre4);
+        uint32_t *pre1 = reinterpret_cast<uint32_t *>(sm + L.pre1);
+        if constexpr (SPL > 0) {
+            for (int q = tid; q < g.nq; q += kGBlock) {
+                const PhiloxPrefix p = philox_prefix(static_cast<uint32_t>(q), static_cast<uint32_t>(v.first >> 32),
+                                                     v.sid, ga.rk);
+                const int at = decltype(scr)::prefix_slot(q);
+                pre4[at] = make_uint4(p.a, p.g, p.fk, p.h);
+                pre1[at] = p.l3;
+            }
+            __syncthreads();
+        }
         const float hint = args.hint[v.s];
         float m_ref = hint;
         double m_acc = static_cast<double>(hint);
@@ -385,7 +405,7 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
             const uint64_t i = v.first + k;
             float S_f;
             if constexpr (SPL > 0) {
-                S_f = scr.action(i, v.sid, ga.rk, ga.cf);
+                S_f = scr.action(i, pre4, pre1, ga.rk, ga.cf);
             } else {
                 warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
                 S_f = warp_action<float>(uf, next, g, ga.cf);
