@@ -489,6 +489,19 @@ def run_batch(bfi, dev, stream, njobs=256):
     samples = sum(j.total_samples for j in jobs)
     shapes = sorted({(j.nx, j.nt) for j in jobs})
     tuned = {f"{nx}x{nt}": bfi.autotune_grid(bfi.lattice(nx, nt), bfi.FP32) for nx, nt in shapes}
+    # the same jobs one after another, each alone on the device with its own plan and the same grid: the
+    # sum of their CUDA-event times, against which the graph's replay shows what overlapping them gains
+    alone_ms = 0.0
+    for j, dsc in zip(jobs, descs):
+        plan = bfi.Plan(dsc["lattice"], j.samples, bfi.FP32)
+        plan.set_grid(tuned[f"{j.nx}x{j.nt}"])
+        plan.execute(dsc["lo"], dsc["hi"], j.seed, j.job_id, stream=stream)
+        ev0.record(stream)
+        plan.execute(dsc["lo"], dsc["hi"], j.seed, j.job_id, stream=stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        alone_ms += ev0.elapsed_time(ev1)
+        plan.close()
     ok = all(bool(torch.isfinite(t[0]).item()) for t in b.totals)
     # the ops-weighted roofline of one replay: every job's counted work (its own screen, stage-1 and evaluation
     # counts) over the replay time, against the FP32/INT issue peak
@@ -513,6 +526,7 @@ def run_batch(bfi, dev, stream, njobs=256):
                         "64-1024 subvolumes, 2^20-2^28 points (seed 3), FP32 eval / FP64 merge, one CUDA graph",
             "value": samples / (ms * 1e-3), "unit": "samples/s", "ms_per_launch": ms, "samples": samples,
             "jobs": njobs, "graph_create_s": create_s, "ctas_per_sm": tuned, "all_finite": ok, "roofline": roof,
+            "alone_sum_ms": alone_ms,
             "by_shape": by_shape}
 
 
@@ -861,7 +875,7 @@ def summary(value, roof, e2e, fp32, batch, serving, tte):
                         "fp32_err_bound_C": _sig(max(fp32["err_bound"]["C_rel_to_C0"]), 3)})
     if batch:
         out.update({"batch_samples_per_s": _sig(batch["value"]), "batch_frac": _sig(batch["roofline"]["frac"], 3),
-                    "batch_ms": _sig(batch["ms_per_launch"])})
+                    "batch_ms": _sig(batch["ms_per_launch"]), "batch_alone_sum_ms": _sig(batch.get("alone_sum_ms"))})
     if serving:
         out.update({"serving_rate": serving.get("rate"), "serving_jobs": serving["jobs"],
                     "serving_p50_ms": _sig(serving["p50_ms"]), "serving_p99_ms": _sig(serving["p99_ms"]),
