@@ -55,12 +55,27 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "integrand_f64_10x2_traffic.txt")
 KERNEL_SOURCES = ["bfi_device.cuh", "bfi_kernels.h", "integrand_kernels.cuh", "shapes_table.cuh", "shapes_small.cu"]
 
 
-def kernel_sources_sha256():
+def code_only(text):
+    """Source text without comments and with whitespace runs collapsed: what a
+    change to the compiled kernel would change."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_sources_sha256(read=None):
+    """SHA-256 of the kernel sources' code (comments and layout ignored);
+    'read' (name -> text) defaults to the files in the tree."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1803_07560_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_1803_07560_gb300", "csrc", name)) as f:
+                text = f.read()
+        else:
+            text = read(name)
+        h.update(code_only(text).encode())
     return h.hexdigest()
 
 

@@ -474,13 +474,15 @@ __device__ __forceinline__ void add_stage1(unsigned long long *stage1, uint64_t 
 //
 // Shift.  Both kernels accumulate w = exp(m_acc - S) with m_acc starting at
 // the hint and moving down only when a sample beats it by more than
-// kRescaleMargin, so the sums are rescaled a handful of times and the
-// threads of a CTA mostly share one shift (cheap merges).  w <= e^16.
+// kRescaleMargin (FP64: to that sample's action; FP32: by whole multiples of
+// ln 2, so the float sums rescale exactly), so the sums are rescaled a
+// handful of times and the threads of a CTA mostly share one shift (cheap
+// merges).  w <= e^16.
 //
 // Sums.  The per-thread sums live in shared memory ([k][thread], no bank
 // conflicts); they are touched only by the few samples that pass the screen,
 // which keeps the registers of the hot loop (Philox, point, FP32 action) low
-// enough for three CTAs per SM.
+// enough for four CTAs per SM at 10x2.
 // ---------------------------------------------------------------------------
 // Rows between the CTA's shares of its smallest action.  A share is a
 // barrier: a warp that has just evaluated a queue batch in FP64 (hundreds of
@@ -703,8 +705,8 @@ __device__ __forceinline__ int dequeue32_pair(uint32_t *q, float *pq, int count)
 // ---------------------------------------------------------------------------
 // FP64 integrand, thread per sample.  One CTA processes chunks blockIdx.x,
 // blockIdx.x + gridDim.x, ...; within a chunk thread t screens samples
-// first + t, first + t + B, ... with the FP32 action of the FP32 point (fast
-// pipes).  Samples that may carry weight (within skip_window of m_ref, plus
+// first + t, first + t + B, ... with the FP32 action of the screen point
+// (fast pipes; two stages where the split is compiled, see PartialScreen).  Samples that may carry weight (within skip_window of m_ref, plus
 // a margin of 1 + 0.1% of S) go to the warp's
 // queue and are evaluated in FP64: Philox words drawn again, FP64 point,
 // action, products and weight.  The margin bounds |S_f32(y_f32) - S(y_f64)|:
