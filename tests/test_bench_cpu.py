@@ -80,3 +80,13 @@ def test_summary_is_short_and_last():
     import json
     assert len(json.dumps({"summary": s})) < 1000
     assert s["fp32_err_bound_C"] == 6e-7 and s["fp32_vs_fp64_C_rel_max"] == 2e-7 and s["serving_frac"] == 0.3
+
+
+def test_kernel_hash_follows_code_not_comments():
+    src = {name: "// a\nint f(int x) { return x + 1; } /* b */\n" for name in bench.KERNEL_SOURCES}
+    base = bench.kernel_sources_sha256(lambda n: src[n])
+    commented = {n: t.replace("// a", "// another comment") + "\n\n// more\n" for n, t in src.items()}
+    assert bench.kernel_sources_sha256(lambda n: commented[n]) == base
+    changed = dict(src)
+    changed[bench.KERNEL_SOURCES[0]] = src[bench.KERNEL_SOURCES[0]].replace("x + 1", "x + 2")
+    assert bench.kernel_sources_sha256(lambda n: changed[n]) != base
