@@ -79,9 +79,10 @@ def kernel_sources_sha256(read=None):
     return h.hexdigest()
 
 
-def measured_traffic():
+def measured_traffic(chunk_samples=None):
     """(DRAM bytes read + written per full-size launch, note): the value of the
-    committed ncu summary when its kernel-source hash matches, else None."""
+    committed ncu summary when its kernel-source hash matches and it was taken
+    with the chunk size the timed plan uses, else None."""
     try:
         fields = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line and not line.startswith("#"))
     except OSError:
@@ -89,6 +90,8 @@ def measured_traffic():
     sha = fields.get("kernel_sources_sha256", "").strip()
     if sha != kernel_sources_sha256():
         return None, "kernel sources changed since the ncu traffic capture"
+    if chunk_samples is not None and fields.get("chunk_samples", "").strip() != str(chunk_samples):
+        return None, "chunk size changed since the ncu traffic capture"
     return int(fields["dram_bytes_per_launch"].strip()), "ncu dram__bytes_read.sum + dram__bytes_write.sum, " \
         "one full-size launch (" + os.path.relpath(TRAFFIC_FILE, ROOT) + ")"
 
@@ -375,7 +378,7 @@ def run_bfi(args):
     roof = roofline(work, kern_ms, "fp64", NX, NT)
     roof["kernel"] = f"hint + integrand FP64 <{NX},{NT}>"
     if (NX, NT) == (10, 2) and args.samples_log2 == 20:
-        roof["traffic"], roof["traffic_source"] = measured_traffic()
+        roof["traffic"], roof["traffic_source"] = measured_traffic(info.chunk_samples)
 
     # ---- FP32 form of the same job with 2^24 points per subvolume ----
     fp32 = None

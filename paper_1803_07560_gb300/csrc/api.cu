@@ -72,11 +72,18 @@ int num_r(int nx) { return nx / 2 + 1; }
 
 // Samples per chunk: a multiple of the block size, chosen from the job alone
 // (never from the device or from other jobs) so that a job's rounding is the
-// same wherever and with whatever else it runs.
+// same wherever and with whatever else it runs.  At least 2048 chunks and up
+// to 512 rows per thread; a job large enough to keep 4096 chunks at 1024 rows
+// takes 1024: every chunk pays a warm-up (its running reference starts at the
+// subvolume's hint, so the screen passes more points until the chunk finds
+// its own minimum) and an end-of-chunk drain and record, while 4096 chunks
+// still keep the tail of the last wave short.
 int64_t choose_chunk_samples(uint64_t total) {
-    uint64_t per_thread = total / (static_cast<uint64_t>(bfi::kBlock) * 2048u);
+    const uint64_t block = static_cast<uint64_t>(bfi::kBlock);
+    uint64_t per_thread = total / (block * 2048u);
     uint64_t spt = 4;
     while (spt * 2 <= per_thread && spt < 512) spt *= 2;
+    if (spt == 512 && total / (block * 1024u) >= 4096u) spt = 1024;
     return static_cast<int64_t>(spt) * bfi::kBlock;
 }
 
@@ -806,8 +813,9 @@ bfi_status bfi_error_bound(const bfi_lattice *lattice, bfi_precision precision, 
     if (lattice->mass2 > 0.0) dS += (d + 1.0) * ua * 0.5 * lattice->mass2 * d * vmax * vmax;
     const double e_w = (f32 ? 0x1p-22 : 0x1p-52) + (f32 ? u * (1.0 + 0x1p-18) : u * (W + 17.0)) + dS;
     const double e_q = (f32 ? 2.0 * (d * u) * (d * u) : d * u / (1.0 - d * u)) + u;
-    // terms per per-thread (per-warp in the warp-per-sample kernel) sum in one chunk
-    const double n_t = shape && shape->kernel == 0 ? 512.0 : 512.0 * bfi::kBlock / 4.0;
+    // terms per per-thread (per-warp in the warp-per-sample kernel) sum in one
+    // chunk: at most 1024 rows per thread
+    const double n_t = shape && shape->kernel == 0 ? 1024.0 : 1024.0 * bfi::kBlock / 4.0;
     const double e_sum = f32 ? 2.0 * u + n_t * u * u : (n_t - 1.0) * u;
     const double e_merge = 0x1p-53 * (64.0 + 4.0 * std::ceil(n_max / 1024.0) + 4.0 * static_cast<double>(nsub));
     const double drop = std::exp(-c);

@@ -66,6 +66,11 @@ def test_traffic_is_reported_only_for_the_kernel_sources_it_was_measured_on(tmp_
     assert bench.measured_traffic()[0] == 12345
     f.write_text("dram_bytes_per_launch: 12345\nkernel_sources_sha256: 0000\n")
     assert bench.measured_traffic()[0] is None
+    # keyed to the chunk size of the capture as well
+    f.write_text("dram_bytes_per_launch: 12345\nchunk_samples: 262144\nkernel_sources_sha256: " +
+                 bench.kernel_sources_sha256() + "\n")
+    assert bench.measured_traffic(262144)[0] == 12345
+    assert bench.measured_traffic(131072)[0] is None
 
 
 def test_summary_is_short_and_last():

@@ -290,10 +290,28 @@ def test_plain_4x2_full_size(bfi, dev):
     assert_totals_close(g_t, o_t, 3, FP64_RTOL, 1e-9)
 
 
+@pytest.mark.parametrize("total,rows", [(1 << 12, 4), (1 << 20, 4), (1 << 24, 32), (1 << 27, 256), (1 << 28, 512),
+                                        (1 << 29, 512), ((1 << 30) - 256, 512), (1 << 30, 1024), (1 << 36, 1024)])
+def test_chunk_size_follows_the_job_alone(bfi, dev, total, rows):
+    """Rows per thread in a chunk: at least 2048 chunks, up to 512 rows, and
+    1024 rows where 4096 chunks remain; the same for either precision and
+    for any split of the job into subvolumes."""
+    lat = bfi.lattice(10, 2)
+    for precision in (0, 1):
+        for nsub in (1, 64):
+            smp = np.full(nsub, total // nsub, dtype=np.uint64)
+            smp[0] += total - int(smp.sum())
+            plan = bfi.Plan(lat, smp, precision)
+            info = plan.info()
+            plan.close()
+            assert info.chunk_samples == rows * 256 and info.total_samples == total
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_paper_10x2_full_size_sampled(bfi, dev, precision):
     job = workloads.paper_10x2()
-    g_s, g_t, _ = run_gpu(bfi, dev, job, precision)
+    g_s, g_t, plan = run_gpu(bfi, dev, job, precision)
+    assert plan.info().chunk_samples == 1024 * 256   # 4096 chunks of 1024 rows per thread
     # a fixed random subset of 64 of the 1024 subvolumes (subvolumes are independent, so subset parity is exact)
     pick = np.sort(np.random.default_rng(64).choice(1024, 64, replace=False))
     o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision))
