@@ -73,17 +73,18 @@ int num_r(int nx) { return nx / 2 + 1; }
 // Samples per chunk: a multiple of the block size, chosen from the job alone
 // (never from the device or from other jobs) so that a job's rounding is the
 // same wherever and with whatever else it runs.  At least 2048 chunks and up
-// to 512 rows per thread; a job large enough to keep 4096 chunks at 1024 rows
-// takes 1024: every chunk pays a warm-up (its running reference starts at the
-// subvolume's hint, so the screen passes more points until the chunk finds
-// its own minimum) and an end-of-chunk drain and record, while 4096 chunks
-// still keep the tail of the last wave short.
+// to 512 rows per thread; from there the rows double, up to 2048, while the
+// job keeps at least 4096 chunks.  Longer chunks screen fewer points: a
+// chunk's running reference starts at the subvolume's hint and falls as the
+// chunk finds lower actions, so the screen passes more points early in every
+// chunk, and each chunk ends with a queue drain and a record.  4096 chunks
+// keep the end of the launch, where CTAs run out of chunks, short.
 int64_t choose_chunk_samples(uint64_t total) {
     const uint64_t block = static_cast<uint64_t>(bfi::kBlock);
     uint64_t per_thread = total / (block * 2048u);
     uint64_t spt = 4;
     while (spt * 2 <= per_thread && spt < 512) spt *= 2;
-    if (spt == 512 && total / (block * 1024u) >= 4096u) spt = 1024;
+    while (spt >= 512 && spt < 2048 && total / (block * spt * 2) >= 4096u) spt *= 2;
     return static_cast<int64_t>(spt) * bfi::kBlock;
 }
 
@@ -222,10 +223,10 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
     const size_t smp_bytes = sizeof(uint64_t) * nsub;
     const size_t par_bytes = sizeof(double) * static_cast<size_t>(std::max<int64_t>(p->nchunks, 1)) * (p->K + 2);
     const size_t hint_bytes = sizeof(float) * nsub;
-    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + 3 * sizeof(unsigned long long) + sizeof(double) * 2 * nsub;
+    p->scratch_bytes = off_bytes + smp_bytes + par_bytes + hint_bytes + 4 * sizeof(unsigned long long) + sizeof(double) * 2 * nsub;
     if (cudaMalloc(&p->d_chunk_off, off_bytes) != cudaSuccess || cudaMalloc(&p->d_samples, smp_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_partials, par_bytes) != cudaSuccess || cudaMalloc(&p->d_hint, hint_bytes) != cudaSuccess ||
-        cudaMalloc(&p->d_stats, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&p->d_stats, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&p->d_fbuf, sizeof(double) * 2 * nsub) != cudaSuccess) {
         cudaGetLastError();
         bfi_plan_destroy(p);
@@ -266,11 +267,12 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
     if (g.err != cudaSuccess) return fail(BFI_E_CUDA, "cannot select device: %s", cudaGetErrorString(g.err));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (plan->timing) BFI_CUDA(cudaEventRecord(plan->ev[0], st));
-    BFI_CUDA(cudaMemsetAsync(plan->d_stats, 0, 3 * sizeof(unsigned long long), st));
+    BFI_CUDA(cudaMemsetAsync(plan->d_stats, 0, 4 * sizeof(unsigned long long), st));
     if (plan->nchunks > 0) {
         bfi::IntegrandArgs a{lo,           hi,           sub_id,        plan->d_samples,     plan->d_chunk_off,
                              plan->d_partials, plan->d_hint, plan->d_stats, plan->nsub, plan->nchunks,
-                             plan->chunk_samples, plan->skip_window, plan->d_stats + 1, plan->d_stats + 2};
+                             plan->chunk_samples, plan->skip_window, plan->d_stats + 1, plan->d_stats + 2,
+                             plan->d_stats + 3};
         if (plan->sampler == BFI_SAMPLE_BOX) {
             BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
         } else if (plan->sampler == BFI_SAMPLE_TRANSFORM && plan->shape->transform) {
@@ -814,8 +816,8 @@ bfi_status bfi_error_bound(const bfi_lattice *lattice, bfi_precision precision, 
     const double e_w = (f32 ? 0x1p-22 : 0x1p-52) + (f32 ? u * (1.0 + 0x1p-18) : u * (W + 17.0)) + dS;
     const double e_q = (f32 ? 2.0 * (d * u) * (d * u) : d * u / (1.0 - d * u)) + u;
     // terms per per-thread (per-warp in the warp-per-sample kernel) sum in one
-    // chunk: at most 1024 rows per thread
-    const double n_t = shape && shape->kernel == 0 ? 1024.0 : 1024.0 * bfi::kBlock / 4.0;
+    // chunk: at most 2048 rows per thread
+    const double n_t = shape && shape->kernel == 0 ? 2048.0 : 2048.0 * bfi::kBlock / 4.0;
     const double e_sum = f32 ? 2.0 * u + n_t * u * u : (n_t - 1.0) * u;
     const double e_merge = 0x1p-53 * (64.0 + 4.0 * std::ceil(n_max / 1024.0) + 4.0 * static_cast<double>(nsub));
     const double drop = std::exp(-c);

@@ -40,6 +40,8 @@ struct IntegrandArgs {
     float skip_window;         // samples above (reference + skip_window) have negligible weight
     unsigned long long *screened;  // [1] samples the full FP32 screen examined after the partial one, or null
     unsigned long long *stage1;    // [1] samples of chunks that ran stage 1 of the two-stage screen, or null
+    unsigned long long *next_chunk;  // [1] zeroed per execution: after its first chunk (blockIdx.x) a CTA takes
+                                     // the next chunk not yet taken; null: CTA b takes b, b + grid, ...
 };
 
 struct MergeArgs {

@@ -58,7 +58,7 @@ __host__ __device__ inline GenLayout gen_layout(const GenShape &g, int mapped = 
     L.uf = o;    o = align16(o + 4 * g.dpad * kGWarps);       // float point per warp
     L.ud = o;    o = align16(o + 8 * g.dpad * kGWarps);       // double point per warp
     L.sums = o;  o = align16(o + 8 * (g.K + g.R + 1) * kGWarps);  // per-warp sums (FP64, or FP32 sums + comps)
-    L.mw = o;    o = align16(o + 8 * kGWarps + 8);             // per-warp shift, counter
+    L.mw = o;    o = align16(o + 8 * kGWarps + 16);            // per-warp shift, counter, next chunk
     L.pre4 = o;  o = align16(o + 16 * g.nq);                   // Philox prefixes of the chunk (lane screen):
     L.pre1 = o;  o = align16(o + 4 * g.nq);                    //   words a, g, fk, h as uint4, then l3
     L.fac = o;   if (gauss) o = align16(o + 8 * g.d * g.d);   // factor F, row-major
@@ -367,13 +367,14 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
     double *ud = reinterpret_cast<double *>(sm + L.ud) + warp * g.dpad;
     double *mw = reinterpret_cast<double *>(sm + L.mw);
     unsigned *cnt_all = reinterpret_cast<unsigned *>(mw + kGWarps);
+    long long *next_slot = reinterpret_cast<long long *>(mw + kGWarps + 1);
     // per-warp sums: FP64 -> double[K]; FP32 -> float[K] then float comps[1 + R]
     double *sd = reinterpret_cast<double *>(sm + L.sums) + warp * (g.K + g.R + 1);
     float *sf = reinterpret_cast<float *>(sm + L.sums) + warp * 2 * (g.K + g.R + 1);
     float *cf = sf + g.K;
     build_next(sm, L, g);
 
-    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+    for (int64_t c = blockIdx.x; c < args.nchunks; c = next_chunk(args, c, next_slot)) {
         const ChunkView v = chunk_view(args, c, g.d);
         __syncthreads();  // the previous chunk's readers of box and sums are done
         load_box(sm, L, g, v.lo, v.hi);
@@ -537,6 +538,7 @@ __global__ void __launch_bounds__(kGBlock) generic_mapped(const GenArgs ga, cons
     double *mean = reinterpret_cast<double *>(sm + L.mean);
     double *mw = reinterpret_cast<double *>(sm + L.mw);
     unsigned *cnt_all = reinterpret_cast<unsigned *>(mw + kGWarps);
+    long long *next_slot = reinterpret_cast<long long *>(mw + kGWarps + 1);
     double *sd = reinterpret_cast<double *>(sm + L.sums) + warp * (g.K + g.R + 1);
     build_next(sm, L, g);
     if (KIND == 2) {  // the factor transposed (fac[j d + r] = F[r][j]): lane r reads consecutive words
@@ -544,7 +546,7 @@ __global__ void __launch_bounds__(kGBlock) generic_mapped(const GenArgs ga, cons
         for (int k = tid; k < g.d; k += kGBlock) mean[k] = mp.mean ? mp.mean[k] : 0.0;
     }
 
-    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+    for (int64_t c = blockIdx.x; c < args.nchunks; c = next_chunk(args, c, next_slot)) {
         const ChunkView v = chunk_view(args, c, g.d);
         __syncthreads();  // the previous chunk's readers of box and sums are done
         for (int j = tid; j < g.d; j += kGBlock) {

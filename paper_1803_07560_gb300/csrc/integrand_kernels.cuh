@@ -635,10 +635,25 @@ template <int BLOCK>
 struct ChunkShared {
     double f[BLOCK];  // per-thread shift factors of the chunk record
     double mb;
+    long long next;   // the chunk this CTA takes next
     int min_bits;
     unsigned evaluated;
     unsigned screened;
 };
+
+// The chunk a CTA takes after chunk c.  With a counter, chunks beyond the
+// first grid go to CTAs in the order they finish, so the CTAs that drew
+// cheaper chunks take more and the launch ends more evenly; a chunk's record
+// depends on the chunk alone, so which CTA takes it changes no result.  Every
+// thread of the CTA calls this at the end of the chunk; 'slot' is a
+// shared-memory word that nothing else reads, and the next chunk's first
+// barrier separates this read from the next write.
+__device__ __forceinline__ int64_t next_chunk(const IntegrandArgs &args, int64_t c, long long *slot) {
+    if (!args.next_chunk) return c + gridDim.x;
+    if (threadIdx.x == 0) *slot = static_cast<long long>(gridDim.x + atomicAdd(args.next_chunk, 1ull));
+    __syncthreads();
+    return *slot;
+}
 
 // ---------------------------------------------------------------------------
 // Candidate queues.  The few samples that pass the screen are not evaluated
@@ -703,8 +718,8 @@ __device__ __forceinline__ int dequeue32_pair(uint32_t *q, float *pq, int count)
 }
 
 // ---------------------------------------------------------------------------
-// FP64 integrand, thread per sample.  One CTA processes chunks blockIdx.x,
-// blockIdx.x + gridDim.x, ...; within a chunk thread t screens samples
+// FP64 integrand, thread per sample.  One CTA processes chunk blockIdx.x,
+// then the chunks next_chunk hands it; within a chunk thread t screens samples
 // first + t, first + t + B, ... with the FP32 action of the screen point
 // (fast pipes; two stages where the split is compiled, see PartialScreen).  Samples that may carry weight (within skip_window of m_ref, plus
 // a margin of 1 + 0.1% of S) go to the warp's
@@ -738,7 +753,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
     float *pqueue = s_pqueue[RestScreen<NX, NT>::enabled ? tid >> 5 : 0];
     SmemSums<double, K, BLOCK> acc{s_sums + tid};
 
-    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+    for (int64_t c = blockIdx.x; c < args.nchunks; c = next_chunk(args, c, &sh.next)) {
         const ChunkView v = chunk_view(args, c, D);
         if (tid < D) {
             s_lo[tid] = v.lo[tid];
@@ -911,7 +926,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f32(con
     float *pqueue = s_pqueue[RestScreen<NX, NT>::enabled ? tid >> 5 : 0];
     Sums acc{s_sums + tid};
 
-    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+    for (int64_t c = blockIdx.x; c < args.nchunks; c = next_chunk(args, c, &sh.next)) {
         const ChunkView v = chunk_view(args, c, D);
         if (tid < D) {
             float lo_f, w_f;

@@ -66,7 +66,7 @@ struct LogProduct {
 // occupancy buys nothing and spilling the d FP64 coordinates would cost.
 
 // ---------------------------------------------------------------------------
-// One CTA processes chunks blockIdx.x, blockIdx.x + gridDim.x, ...; thread t
+// One CTA processes chunk blockIdx.x, then the chunks next_chunk hands it; thread t
 // evaluates samples first + t, first + t + B, ... of the chunk.  The Philox
 // words, the point y = lo + (hi - lo) u (the FP64 point of the box sampler)
 // and 1 - y^2 = (1 - y)(1 + y) are those of the definition; v_j = y_j r_j
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(BLOCK, 1) transform_f64(const IntegrandArgs ar
     const int tid = threadIdx.x;
     SmemSums<double, K, BLOCK> acc{s_sums + tid};
 
-    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+    for (int64_t c = blockIdx.x; c < args.nchunks; c = next_chunk(args, c, &sh.next)) {
         const ChunkView v = chunk_view(args, c, D);
         if (tid < D) {
             s_lo[tid] = v.lo[tid];
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(BLOCK, 1) gaussian_f64(const IntegrandArgs arg
     for (int k = tid; k < D * D; k += BLOCK) s_ft[(k % D) * D + k / D] = factor[k];
     for (int k = tid; k < D; k += BLOCK) s_mean[k] = mean ? mean[k] : 0.0;
 
-    for (int64_t c = blockIdx.x; c < args.nchunks; c += gridDim.x) {
+    for (int64_t c = blockIdx.x; c < args.nchunks; c = next_chunk(args, c, &sh.next)) {
         const ChunkView v = chunk_view(args, c, D);
         if (tid < D) {
             s_lo[tid] = v.lo[tid];

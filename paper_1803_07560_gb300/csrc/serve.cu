@@ -86,7 +86,7 @@ Layout layout_for(int64_t nsub, int64_t nchunks, int d, int K, int SL, int TL) {
     L.off = o;   o += round_up(sizeof(int64_t) * (nsub + 1));
     L.smp = o;   o += round_up(sizeof(uint64_t) * nsub);
     L.hint = o;  o += round_up(sizeof(float) * nsub);
-    L.stats = o; o += round_up(3 * sizeof(unsigned long long));  // evaluated, fully screened, stage 1
+    L.stats = o; o += round_up(4 * sizeof(unsigned long long));  // evaluated, fully screened, stage 1, next chunk
     L.fbuf = o;  o += round_up(sizeof(double) * 2 * nsub);
     L.part = o;  o += round_up(sizeof(double) * static_cast<size_t>(nchunks > 0 ? nchunks : 1) * (K + 2));
     L.lo = o;    o += round_up(sizeof(double) * nsub * d);
@@ -232,7 +232,7 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
               cuda(cudaMemcpyAsync(at(p.L.lo), p.lo.data(), sizeof(double) * p.nsub * r.d, cudaMemcpyHostToDevice, st), "copy") &&
               cuda(cudaMemcpyAsync(at(p.L.hi), p.hi.data(), sizeof(double) * p.nsub * r.d, cudaMemcpyHostToDevice, st), "copy") &&
               cuda(cudaMemcpyAsync(at(p.L.sid), p.sid.data(), sizeof(uint32_t) * p.nsub, cudaMemcpyHostToDevice, st), "copy") &&
-              cuda(cudaMemsetAsync(at(p.L.stats), 0, 3 * sizeof(unsigned long long), st), "memset");
+              cuda(cudaMemsetAsync(at(p.L.stats), 0, 4 * sizeof(unsigned long long), st), "memset");
     int per_sm = 1;
     if (ok) ok = cuda(shape->occupancy[prec](r.lat.nx, r.lat.nt, &per_sm), "occupancy");
     const bfi::LatticeParams lp{r.lat.nx, r.lat.nt, r.lat.nu, r.lat.D, r.lat.a, r.lat.tau, r.lat.nonlinear, r.lat.mass2};
@@ -253,7 +253,8 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
                              p.chunk_samples,
                              p.window,
                              static_cast<unsigned long long *>(at(p.L.stats)) + 1,
-                             static_cast<unsigned long long *>(at(p.L.stats)) + 2};
+                             static_cast<unsigned long long *>(at(p.L.stats)) + 2,
+                             static_cast<unsigned long long *>(at(p.L.stats)) + 3};
         ok = cuda(shape->integrand[prec](a, lp, r.seed, r.job_id, static_cast<int>(grid), st), "integrand launch");
     }
     if (ok && take_fault(s, BFI_FAULT_LAUNCH)) {

@@ -124,7 +124,7 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
     const size_t off_bytes = round_up(sizeof(int64_t) * (nsub + 1));
     const size_t smp_bytes = round_up(sizeof(uint64_t) * nsub);
     const size_t hint_bytes = round_up(sizeof(float) * nsub);
-    const size_t stat_bytes = round_up(sizeof(unsigned long long));
+    const size_t stat_bytes = round_up(2 * sizeof(unsigned long long));  // evaluated, next chunk
     const size_t fbuf_bytes = round_up(sizeof(double) * 2 * nsub);
     const size_t par_bytes = round_up(sizeof(double) * static_cast<size_t>(nchunks > 0 ? nchunks : 1) * (K + 2));
     const size_t need = off_bytes + smp_bytes + hint_bytes + stat_bytes + fbuf_bytes + par_bytes;
@@ -156,13 +156,13 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
     int64_t grid = static_cast<int64_t>(sms) * (per_sm > 0 ? per_sm : 1);
     grid = grid < nchunks ? grid : (nchunks > 0 ? nchunks : 1);
 
-    // Everything below is ordered on 'stream'.  The counter must start at
-    // zero; every other scratch word is written before it is read.
+    // Everything below is ordered on 'stream'.  The two counters must start
+    // at zero; every other scratch word is written before it is read.
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     if ((e = cudaMemcpyAsync(d_samples, samples, sizeof(uint64_t) * nsub, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
         return cuda_fail("copy of the budgets", e);
-    if ((e = cudaMemsetAsync(d_stats, 0, sizeof(unsigned long long), cs)) != cudaSuccess)
-        return cuda_fail("clearing the counter", e);
+    if ((e = cudaMemsetAsync(d_stats, 0, 2 * sizeof(unsigned long long), cs)) != cudaSuccess)
+        return cuda_fail("clearing the counters", e);
     chunk_table<<<1, kScanThreads, 0, cs>>>(d_samples, nsub, chunk_samples, d_off);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("chunk table launch", e);
     const bfi::LatticeParams lp{lattice->nx, lattice->nt, lattice->nu, lattice->D,
@@ -170,7 +170,7 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
     if (nchunks > 0) {
         bfi::IntegrandArgs a{lo,         hi,     sub_id, d_samples, d_off,         d_partials,
                              d_hint,     d_stats, nsub,  nchunks,   chunk_samples, bfi::plan_negligible_window(precision, n_max),
-                             nullptr};
+                             nullptr,    nullptr, d_stats + 1};
         if ((e = shape->integrand[precision](a, lp, seed, job_id, static_cast<int>(grid), cs)) != cudaSuccess)
             return cuda_fail("integrand launch", e);
     }

@@ -291,11 +291,12 @@ def test_plain_4x2_full_size(bfi, dev):
 
 
 @pytest.mark.parametrize("total,rows", [(1 << 12, 4), (1 << 20, 4), (1 << 24, 32), (1 << 27, 256), (1 << 28, 512),
-                                        (1 << 29, 512), ((1 << 30) - 256, 512), (1 << 30, 1024), (1 << 36, 1024)])
+                                        (1 << 29, 512), ((1 << 30) - 256, 512), (1 << 30, 1024),
+                                        ((1 << 31) - 256, 1024), (1 << 31, 2048), (1 << 36, 2048)])
 def test_chunk_size_follows_the_job_alone(bfi, dev, total, rows):
-    """Rows per thread in a chunk: at least 2048 chunks, up to 512 rows, and
-    1024 rows where 4096 chunks remain; the same for either precision and
-    for any split of the job into subvolumes."""
+    """Rows per thread in a chunk: at least 2048 chunks, up to 512 rows, then
+    doubling up to 2048 while 4096 chunks remain; the same for either
+    precision and for any split of the job into subvolumes."""
     lat = bfi.lattice(10, 2)
     for precision in (0, 1):
         for nsub in (1, 64):
@@ -305,6 +306,49 @@ def test_chunk_size_follows_the_job_alone(bfi, dev, total, rows):
             info = plan.info()
             plan.close()
             assert info.chunk_samples == rows * 256 and info.total_samples == total
+
+
+@pytest.mark.parametrize("nx,nt,precision,sampler", [(10, 2, 0, 0), (10, 2, 1, 0), (6, 4, 0, 0), (32, 4, 1, 0),
+                                                      (64, 8, 0, 0), (4, 2, 0, 1), (4, 2, 0, 2), (5, 3, 0, 2)])
+def test_results_do_not_depend_on_which_cta_takes_a_chunk(bfi, dev, nx, nt, precision, sampler):
+    """After its first chunk a CTA takes the next chunk not yet taken, so the
+    chunk-to-CTA map changes from run to run and with the grid.  A chunk's
+    record depends on the chunk alone: every grid (1 CTA per SM up to the
+    occupancy limit) and a repeat give bitwise the same slots, totals and work
+    counts.  The job has 2^21 samples, 2048 chunks, so each CTA takes several
+    (thread-per-sample, warp-per-sample, range-map and Gaussian kernels)."""
+    d = nx * nt
+    nsub = 16
+    lo = np.full((nsub, d), -3.0 if sampler != 1 else -0.9)
+    hi = np.full((nsub, d), 3.0 if sampler != 1 else 0.9)
+    lo[:, 0] = np.linspace(lo[0, 0], hi[0, 0], nsub + 1)[:-1]
+    hi[:, 0] = np.linspace(lo[0, 0], hi[0, 0], nsub + 1)[1:]
+    samples = np.full(nsub, (1 << 21) // nsub, dtype=np.uint64)
+    samples[3] += 777
+    samples[5] -= 1000
+    lat = bfi.lattice(nx, nt)
+    plan = bfi.Plan(lat, samples, precision)
+    if sampler:
+        plan.set_sampler(sampler, mean=np.zeros(d) if sampler == 2 else None,
+                         factor=np.eye(d) * 0.8 if sampler == 2 else None)
+    assert plan.info().chunks >= 2048
+    lo_t, hi_t = torch.tensor(lo, device=dev), torch.tensor(hi, device=dev)
+
+    def run():
+        s, t = plan.execute(lo_t, hi_t, 5, 3)
+        torch.cuda.synchronize()
+        return s.cpu().numpy(), t.cpu().numpy(), plan.work().as_dict()
+
+    ref = run()
+    assert ref[2]["samples"] == int(samples.sum())
+    for g in sorted({1, 2, plan.info().ctas_per_sm_max}):
+        if g > plan.info().ctas_per_sm_max:
+            continue
+        plan.set_grid(g)
+        for _ in range(2):
+            out = run()
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]) and out[2] == ref[2], g
+    plan.close()
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -87,7 +87,7 @@ def test_static_scratch_two_stage_screen(bfi, dev, precision):
 
 
 def test_static_scratch_refuses_jobs_beyond_its_size(bfi, dev):
-    job = workloads.paper_10x2(1 << 25)   # 2^35 samples: ~131k chunk records, more than 16 MiB
+    job = workloads.paper_10x2(1 << 26)   # 2^36 samples: ~131k chunk records, more than 16 MiB
     lat = bfi.lattice(job.nx, job.nt)
     lo = torch.tensor(job.lo, device=dev)
     hi = torch.tensor(job.hi, device=dev)
