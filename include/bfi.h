@@ -175,9 +175,39 @@ typedef struct {
     size_t scratch_bytes;      /* device scratch owned by the plan */
     int32_t ctas_per_sm_max;   /* occupancy limit of the integrand kernel */
     int32_t ctas_per_sm;       /* CTAs per SM the grid uses now */
+    int64_t tail_subvolume;    /* subvolumes from this one on (nsub: none) are cut into ... */
+    int64_t tail_chunk_samples;  /* ... chunks of this many samples (see bfi_chunking_of) */
 } bfi_plan_info;
 
 bfi_status bfi_plan_get_info(const bfi_plan *plan, bfi_plan_info *info);
+
+/* How a job's budgets are cut into chunks, the work units of the integrand
+ * kernels (host arithmetic only; no device is touched).  bfi_plan_create,
+ * bfi_integrate_static_scratch and the server all cut a job this way, and
+ * the cut depends on the budgets alone, so a job's rounding is the same on
+ * any device and beside any other job.
+ *   chunk_samples = 256 x rows, rows a power of two: at least 2048 chunks and
+ *     at most 512 rows, then doubling up to 2048 rows while the job keeps at
+ *     least 4096 chunks;
+ *   the longest suffix of subvolumes holding at most 1/8 of the samples and
+ *     at most 512 x chunk_samples (tail_subvolume .. nsub - 1) is cut into
+ *     chunks of tail_chunk_samples = max(chunk_samples / 4, 256 x 256) when
+ *     chunk_samples exceeds 256 x 256 (else tail_subvolume = nsub);
+ *   subvolume s gives ceil(n_s / its chunk size) chunks, the last ragged;
+ *     chunks are numbered subvolume by subvolume, and the kernels hand them
+ *     out in that order, so the short ones run last.
+ *   nsub, samples   as for bfi_plan_create
+ *   out             chunk_samples, tail_subvolume, tail_chunk_samples, chunks
+ * Errors: BFI_E_INVALID (nsub < 1, NULL pointer, a budget >= 2^48, total
+ * budget >= 2^62). */
+typedef struct {
+    int64_t chunk_samples;
+    int64_t tail_subvolume;
+    int64_t tail_chunk_samples;
+    int64_t chunks;
+} bfi_chunking;
+
+bfi_status bfi_chunking_of(int64_t nsub, const uint64_t *samples, bfi_chunking *out);
 
 /* Run the whole hot path on 'stream' (a cudaStream_t; NULL = legacy default
  * stream): points, action, weights, products, per-subvolume reduction and

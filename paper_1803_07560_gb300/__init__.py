@@ -45,7 +45,14 @@ class PlanInfo(ctypes.Structure):
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("slot_len", ctypes.c_int32), ("totals_len", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_size_t), ("ctas_per_sm_max", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("tail_subvolume", ctypes.c_int64),
+                ("tail_chunk_samples", ctypes.c_int64)]
+
+
+class Chunking(ctypes.Structure):
+    """How a job's budgets are cut into chunks (bfi_chunking)."""
+    _fields_ = [("chunk_samples", ctypes.c_int64), ("tail_subvolume", ctypes.c_int64),
+                ("tail_chunk_samples", ctypes.c_int64), ("chunks", ctypes.c_int64)]
 
 
 class Work(ctypes.Structure):
@@ -148,6 +155,7 @@ _SIGNATURES = {
                                        ctypes.c_int, ctypes.c_int]),
     "bfi_plan_destroy": (ctypes.c_int, [_vp]),
     "bfi_plan_get_info": (ctypes.c_int, [_vp, _P(PlanInfo)]),
+    "bfi_chunking_of": (ctypes.c_int, [ctypes.c_int64, _P(ctypes.c_uint64), _P(Chunking)]),
     "bfi_plan_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32,
                                         _vp, _vp, _vp]),
     "bfi_plan_set_grid": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -651,6 +659,15 @@ def merge_host(nx: int, slots) -> np.ndarray:
     s_a, s_p = _host(np.reshape(slots, (-1, slot_len(nx))), np.float64)
     out = np.empty(totals_len(nx))
     _check(_lib.bfi_merge_host(nx, s_a.shape[0], s_p, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def chunking(samples) -> Chunking:
+    """How a job with these per-subvolume budgets is cut into chunks
+    (bfi_chunking_of; host only)."""
+    smp = np.ascontiguousarray(np.atleast_1d(samples), dtype=np.uint64)
+    out = Chunking()
+    _check(_lib.bfi_chunking_of(smp.size, smp.ctypes.data_as(_P(ctypes.c_uint64)), ctypes.byref(out)))
     return out
 
 

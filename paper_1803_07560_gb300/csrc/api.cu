@@ -105,7 +105,34 @@ bfi_status set_error(bfi_status status, const char *message) {
     return status;
 }
 bfi_status validate_lattice(const bfi_lattice *lattice) { return check_lattice(lattice); }
-int64_t plan_chunk_samples(uint64_t total) { return choose_chunk_samples(total); }
+// The chunks a CTA takes last are the shortest.  Once the chunks run out, each
+// CTA still finishes the chunk it holds, and an SM stops only when its last
+// CTA does; the slowest of the SMs sets the end of the launch, which comes
+// about a third of a chunk's duration after the average SM would finish.  So
+// the last subvolumes, the longest suffix holding at most an eighth of the
+// samples and at most 512 full chunks' worth, are cut into chunks a quarter
+// as long (never below 256 rows per thread, where the two-stage screen
+// stops); chunks are handed out in index order, so these come last.
+ChunkLayout plan_chunk_layout(const uint64_t *samples, int64_t nsub) {
+    uint64_t total = 0;
+    for (int64_t s = 0; s < nsub; ++s) total += samples[s];
+    ChunkLayout L;
+    L.chunk_samples = choose_chunk_samples(total);
+    L.tail_chunk_samples = L.chunk_samples;
+    L.tail_sub = nsub;
+    const int64_t min_tail = static_cast<int64_t>(kTwoStageMinRows) * kBlock;
+    if (L.chunk_samples > min_tail) {
+        const uint64_t limit = std::min<uint64_t>(total / 8, 512u * static_cast<uint64_t>(L.chunk_samples));
+        uint64_t tail = 0;
+        int64_t s = nsub;
+        while (s > 0 && tail + samples[s - 1] <= limit) tail += samples[--s];
+        if (s < nsub && tail > 0) {
+            L.tail_sub = s;
+            L.tail_chunk_samples = std::max<int64_t>(L.chunk_samples / 4, min_tail);
+        }
+    }
+    return L;
+}
 float plan_negligible_window(bfi_precision precision, uint64_t n_max) { return negligible_window(precision, n_max); }
 }  // namespace bfi
 
@@ -115,6 +142,7 @@ struct bfi_plan {
     bfi_precision precision = BFI_FP64;
     const bfi::ShapeKernels *shape = nullptr;
     int64_t nsub = 0, nchunks = 0, chunk_samples = 0, total = 0;
+    bfi::ChunkLayout layout;
     int grid = 1;
     int sms = 1, per_sm_max = 1, per_sm = 1;
     int R = 0, K = 0, d = 0;
@@ -197,13 +225,14 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
     p->d = lattice->nx * lattice->nt;
     p->total = static_cast<int64_t>(total);
     p->samples.assign(samples, samples + nsub);
-    p->chunk_samples = choose_chunk_samples(total);
+    p->layout = bfi::plan_chunk_layout(samples, nsub);
+    p->chunk_samples = p->layout.chunk_samples;
     uint64_t n_max = 1;
     for (int64_t s = 0; s < nsub; ++s) n_max = std::max<uint64_t>(n_max, samples[s]);
     p->skip_window = negligible_window(precision, n_max);
     std::vector<int64_t> off(nsub + 1, 0);
     for (int64_t s = 0; s < nsub; ++s)
-        off[s + 1] = off[s] + static_cast<int64_t>((samples[s] + p->chunk_samples - 1) / p->chunk_samples);
+        off[s + 1] = off[s] + p->layout.chunks_of(s, samples[s]);
     p->nchunks = off[nsub];
 
     int sms = 0, per_sm = 0;
@@ -242,11 +271,33 @@ bfi_status bfi_plan_create(bfi_plan **out, const bfi_lattice *lattice, int64_t n
     return BFI_OK;
 }
 
+bfi_status bfi_chunking_of(int64_t nsub, const uint64_t *samples, bfi_chunking *out) {
+    if (!out || !samples) return fail(BFI_E_INVALID, "samples or out is NULL");
+    if (nsub < 1) return fail(BFI_E_INVALID, "nsub must be >= 1 (got %lld)", static_cast<long long>(nsub));
+    uint64_t total = 0;
+    for (int64_t s = 0; s < nsub; ++s) {
+        if (samples[s] >= (1ull << 48))
+            return fail(BFI_E_INVALID, "samples[%lld] = %llu must be < 2^48", static_cast<long long>(s),
+                        static_cast<unsigned long long>(samples[s]));
+        total += samples[s];
+    }
+    if (total >= (1ull << 62)) return fail(BFI_E_INVALID, "total sample budget too large");
+    const bfi::ChunkLayout L = bfi::plan_chunk_layout(samples, nsub);
+    out->chunk_samples = L.chunk_samples;
+    out->tail_subvolume = L.tail_sub;
+    out->tail_chunk_samples = L.tail_chunk_samples;
+    out->chunks = 0;
+    for (int64_t s = 0; s < nsub; ++s) out->chunks += L.chunks_of(s, samples[s]);
+    return BFI_OK;
+}
+
 bfi_status bfi_plan_get_info(const bfi_plan *plan, bfi_plan_info *info) {
     if (!plan || !info) return fail(BFI_E_INVALID, "plan or info is NULL");
     info->nsub = plan->nsub;
     info->chunks = plan->nchunks;
     info->chunk_samples = plan->chunk_samples;
+    info->tail_subvolume = plan->layout.tail_sub;
+    info->tail_chunk_samples = plan->layout.tail_chunk_samples;
     info->total_samples = plan->total;
     info->grid = plan->grid;
     info->block = bfi::kBlock;
@@ -272,7 +323,7 @@ bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi, 
         bfi::IntegrandArgs a{lo,           hi,           sub_id,        plan->d_samples,     plan->d_chunk_off,
                              plan->d_partials, plan->d_hint, plan->d_stats, plan->nsub, plan->nchunks,
                              plan->chunk_samples, plan->skip_window, plan->d_stats + 1, plan->d_stats + 2,
-                             plan->d_stats + 3};
+                             plan->d_stats + 3, plan->layout.tail_sub, plan->layout.tail_chunk_samples};
         if (plan->sampler == BFI_SAMPLE_BOX) {
             BFI_CUDA(plan->shape->integrand[plan->precision](a, plan->lat, seed, job_id, plan->grid, st));
         } else if (plan->sampler == BFI_SAMPLE_TRANSFORM && plan->shape->transform) {

@@ -12,8 +12,20 @@ namespace bfi {
 bfi_status set_error(bfi_status status, const char *message);
 // Argument checks of a lattice (BFI_OK or BFI_E_INVALID with a message).
 bfi_status validate_lattice(const bfi_lattice *lattice);
-// Samples per chunk for a job of 'total' samples (depends on the job only).
-int64_t plan_chunk_samples(uint64_t total);
+// How a job's budgets are cut into chunks (depends on the job only).
+// Subvolume s is cut into chunks of samples_of(s), the last one ragged;
+// chunk indices run subvolume by subvolume.
+struct ChunkLayout {
+    int64_t chunk_samples = 0;       // subvolumes s < tail_sub
+    int64_t tail_chunk_samples = 0;  // subvolumes s >= tail_sub
+    int64_t tail_sub = 0;            // nsub: no tail
+    int64_t samples_of(int64_t s) const { return s >= tail_sub ? tail_chunk_samples : chunk_samples; }
+    int64_t chunks_of(int64_t s, uint64_t n_s) const {
+        const uint64_t c = static_cast<uint64_t>(samples_of(s));
+        return static_cast<int64_t>((n_s + c - 1) / c);
+    }
+};
+ChunkLayout plan_chunk_layout(const uint64_t *samples, int64_t nsub);
 // Negligible-weight window for the largest per-subvolume budget n_max.
 float plan_negligible_window(bfi_precision precision, uint64_t n_max);
 

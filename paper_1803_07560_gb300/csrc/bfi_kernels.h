@@ -9,6 +9,11 @@ namespace bfi {
 
 constexpr int kBlock = 256;   // threads per CTA of the integrand kernels
 constexpr int kMaxD = 512;    // largest lattice (d = nx * nt) the library accepts
+#ifndef BFI_TWO_STAGE_MIN_ROWS
+#define BFI_TWO_STAGE_MIN_ROWS 256
+#endif
+// rows per thread from which a chunk runs the two-stage screen
+constexpr uint64_t kTwoStageMinRows = BFI_TWO_STAGE_MIN_ROWS;
 
 // Lattice shapes with compiled thread-per-sample kernels (NX, NT), in five
 // translation units of about equal compile time that compile in parallel
@@ -42,6 +47,8 @@ struct IntegrandArgs {
     unsigned long long *stage1;    // [1] samples of chunks that ran stage 1 of the two-stage screen, or null
     unsigned long long *next_chunk;  // [1] zeroed per execution: after its first chunk (blockIdx.x) a CTA takes
                                      // the next chunk not yet taken; null: CTA b takes b, b + grid, ...
+    int64_t tail_sub;              // subvolumes s >= tail_sub are cut into chunks of tail_chunk_samples
+    int64_t tail_chunk_samples;    // (0: every subvolume into chunks of chunk_samples)
 };
 
 struct MergeArgs {

@@ -86,8 +86,10 @@ __device__ __forceinline__ ChunkView chunk_view(const IntegrandArgs &args, int64
     ChunkView v;
     v.s = find_subvolume(args.chunk_off, args.nsub, c);
     const uint64_t n_s = args.samples[v.s];
-    v.first = static_cast<uint64_t>(c - args.chunk_off[v.s]) * static_cast<uint64_t>(args.chunk_samples);
-    v.cnt = min(static_cast<uint64_t>(args.chunk_samples), n_s - v.first);
+    const uint64_t cs = static_cast<uint64_t>(
+        args.tail_chunk_samples > 0 && v.s >= args.tail_sub ? args.tail_chunk_samples : args.chunk_samples);
+    v.first = static_cast<uint64_t>(c - args.chunk_off[v.s]) * cs;
+    v.cnt = min(cs, n_s - v.first);
     v.sid = args.sub_id ? args.sub_id[v.s] : static_cast<uint32_t>(v.s);
     v.lo = args.lo + v.s * d;
     v.hi = args.hi + v.s * d;
@@ -308,11 +310,8 @@ __device__ __forceinline__ float screen_action(uint32_t x, const PhiloxPrefix *p
 // nothing.  A per-warp switch back to one stage when too many samples
 // survive was measured and rejected: early in a chunk the reference action
 // is still high, and the switch fired on the 10x2 workload too.
+// (kTwoStageMinRows, in bfi_kernels.h, where the host's chunking reads it.)
 // ---------------------------------------------------------------------------
-#ifndef BFI_TWO_STAGE_MIN_ROWS
-#define BFI_TWO_STAGE_MIN_ROWS 256
-#endif
-constexpr uint64_t kTwoStageMinRows = BFI_TWO_STAGE_MIN_ROWS;
 
 template <int NX, int NT>
 struct PartialScreen {

@@ -75,7 +75,8 @@ struct Pass {
     std::vector<uint64_t> samples;
     std::vector<uint32_t> sid;
     std::vector<int64_t> off;  // chunk table
-    int64_t nchunks = 0, chunk_samples = 0;
+    int64_t nchunks = 0;
+    bfi::ChunkLayout chunks;
     float window = 0.f;
     Layout L{};
 };
@@ -113,10 +114,9 @@ void finalize_pass(Pass &p, bfi_precision precision) {
         total += n;
         n_max = std::max(n_max, n);
     }
-    p.chunk_samples = bfi::plan_chunk_samples(total);
+    p.chunks = bfi::plan_chunk_layout(p.samples.data(), p.nsub);
     p.off.assign(p.nsub + 1, 0);
-    for (int64_t s = 0; s < p.nsub; ++s)
-        p.off[s + 1] = p.off[s] + static_cast<int64_t>((p.samples[s] + p.chunk_samples - 1) / p.chunk_samples);
+    for (int64_t s = 0; s < p.nsub; ++s) p.off[s + 1] = p.off[s] + p.chunks.chunks_of(s, p.samples[s]);
     p.nchunks = p.off[p.nsub];
     p.window = bfi::plan_negligible_window(precision, n_max);
     p.L = layout_for(p.nsub, p.nchunks, r.d, 2 + 3 * r.R, r.SL, r.TL);
@@ -250,11 +250,13 @@ bfi_status launch_pass(bfi_server *s, int k, Pass &p, std::string &msg) {
                              static_cast<unsigned long long *>(at(p.L.stats)),
                              p.nsub,
                              p.nchunks,
-                             p.chunk_samples,
+                             p.chunks.chunk_samples,
                              p.window,
                              static_cast<unsigned long long *>(at(p.L.stats)) + 1,
                              static_cast<unsigned long long *>(at(p.L.stats)) + 2,
-                             static_cast<unsigned long long *>(at(p.L.stats)) + 3};
+                             static_cast<unsigned long long *>(at(p.L.stats)) + 3,
+                             p.chunks.tail_sub,
+                             p.chunks.tail_chunk_samples};
         ok = cuda(shape->integrand[prec](a, lp, r.seed, r.job_id, static_cast<int>(grid), st), "integrand launch");
     }
     if (ok && take_fault(s, BFI_FAULT_LAUNCH)) {

@@ -62,13 +62,17 @@ size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr int kScanThreads = 256;
 
 __global__ void __launch_bounds__(kScanThreads) chunk_table(const uint64_t *samples, int64_t nsub,
-                                                            int64_t chunk_samples, int64_t *off) {
+                                                            bfi::ChunkLayout layout, int64_t *off) {
     __shared__ int64_t part[kScanThreads];
     const int t = threadIdx.x;
     const int64_t per = (nsub + kScanThreads - 1) / kScanThreads;
     const int64_t b = min(nsub, t * per), e = min(nsub, b + per);
+    auto chunks_of = [&](int64_t s) {
+        const uint64_t c = static_cast<uint64_t>(s >= layout.tail_sub ? layout.tail_chunk_samples : layout.chunk_samples);
+        return static_cast<int64_t>((samples[s] + c - 1) / c);
+    };
     int64_t sum = 0;
-    for (int64_t s = b; s < e; ++s) sum += static_cast<int64_t>((samples[s] + chunk_samples - 1) / chunk_samples);
+    for (int64_t s = b; s < e; ++s) sum += chunks_of(s);
     part[t] = sum;
     __syncthreads();
     if (t == 0) {
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(kScanThreads) chunk_table(const uint64_t *samp
     int64_t run = part[t];
     for (int64_t s = b; s < e; ++s) {
         off[s] = run;
-        run += static_cast<int64_t>((samples[s] + chunk_samples - 1) / chunk_samples);
+        run += chunks_of(s);
     }
 }
 
@@ -117,10 +121,9 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
     }
     if (total >= (1ull << 62)) return bfi::set_error(BFI_E_INVALID, "total sample budget too large");
     const int R = lattice->nx / 2 + 1, K = 2 + 3 * R, d = lattice->nx * lattice->nt;
-    const int64_t chunk_samples = bfi::plan_chunk_samples(total);
+    const bfi::ChunkLayout layout = bfi::plan_chunk_layout(samples, nsub);
     int64_t nchunks = 0;
-    for (int64_t s = 0; s < nsub; ++s)
-        nchunks += static_cast<int64_t>((samples[s] + chunk_samples - 1) / chunk_samples);
+    for (int64_t s = 0; s < nsub; ++s) nchunks += layout.chunks_of(s, samples[s]);
     const size_t off_bytes = round_up(sizeof(int64_t) * (nsub + 1));
     const size_t smp_bytes = round_up(sizeof(uint64_t) * nsub);
     const size_t hint_bytes = round_up(sizeof(float) * nsub);
@@ -163,14 +166,14 @@ extern "C" bfi_status bfi_integrate_static_scratch(const bfi_lattice *lattice, i
         return cuda_fail("copy of the budgets", e);
     if ((e = cudaMemsetAsync(d_stats, 0, 2 * sizeof(unsigned long long), cs)) != cudaSuccess)
         return cuda_fail("clearing the counters", e);
-    chunk_table<<<1, kScanThreads, 0, cs>>>(d_samples, nsub, chunk_samples, d_off);
+    chunk_table<<<1, kScanThreads, 0, cs>>>(d_samples, nsub, layout, d_off);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("chunk table launch", e);
     const bfi::LatticeParams lp{lattice->nx, lattice->nt, lattice->nu, lattice->D,
                                 lattice->a,  lattice->tau, lattice->nonlinear, lattice->mass2};
     if (nchunks > 0) {
         bfi::IntegrandArgs a{lo,         hi,     sub_id, d_samples, d_off,         d_partials,
-                             d_hint,     d_stats, nsub,  nchunks,   chunk_samples, bfi::plan_negligible_window(precision, n_max),
-                             nullptr,    nullptr, d_stats + 1};
+                             d_hint,     d_stats, nsub,  nchunks,   layout.chunk_samples, bfi::plan_negligible_window(precision, n_max),
+                             nullptr,    nullptr, d_stats + 1, layout.tail_sub, layout.tail_chunk_samples};
         if ((e = shape->integrand[precision](a, lp, seed, job_id, static_cast<int>(grid), cs)) != cudaSuccess)
             return cuda_fail("integrand launch", e);
     }

@@ -306,32 +306,45 @@ def test_chunk_size_follows_the_job_alone(bfi, dev, total, rows):
             info = plan.info()
             plan.close()
             assert info.chunk_samples == rows * 256 and info.total_samples == total
+            # the plan cuts the job as the host rule says, tail included
+            ch = bfi.chunking(smp)
+            assert (info.chunk_samples, info.tail_subvolume, info.tail_chunk_samples, info.chunks) == \
+                (ch.chunk_samples, ch.tail_subvolume, ch.tail_chunk_samples, ch.chunks)
 
 
-@pytest.mark.parametrize("nx,nt,precision,sampler", [(10, 2, 0, 0), (10, 2, 1, 0), (6, 4, 0, 0), (32, 4, 1, 0),
-                                                      (64, 8, 0, 0), (4, 2, 0, 1), (4, 2, 0, 2), (5, 3, 0, 2)])
-def test_results_do_not_depend_on_which_cta_takes_a_chunk(bfi, dev, nx, nt, precision, sampler):
+@pytest.mark.parametrize("nx,nt,precision,sampler,log2n", [(10, 2, 0, 0, 21), (10, 2, 1, 0, 21), (6, 4, 0, 0, 21),
+                                                             (32, 4, 1, 0, 21), (64, 8, 0, 0, 21), (4, 2, 0, 1, 21),
+                                                             (4, 2, 0, 2, 21), (5, 3, 0, 2, 21), (10, 2, 0, 0, 28),
+                                                             (10, 2, 1, 0, 28)])
+def test_results_do_not_depend_on_which_cta_takes_a_chunk(bfi, dev, nx, nt, precision, sampler, log2n):
     """After its first chunk a CTA takes the next chunk not yet taken, so the
     chunk-to-CTA map changes from run to run and with the grid.  A chunk's
     record depends on the chunk alone: every grid (1 CTA per SM up to the
     occupancy limit) and a repeat give bitwise the same slots, totals and work
-    counts.  The job has 2^21 samples, 2048 chunks, so each CTA takes several
-    (thread-per-sample, warp-per-sample, range-map and Gaussian kernels)."""
+    counts.  Jobs of 2^21 samples have 2048 chunks, so each CTA takes several
+    (thread-per-sample, warp-per-sample, range-map and Gaussian kernels); the
+    2^28-sample jobs have chunks of 512 rows and, in their last two
+    subvolumes, tail chunks of 256 rows."""
     d = nx * nt
     nsub = 16
     lo = np.full((nsub, d), -3.0 if sampler != 1 else -0.9)
     hi = np.full((nsub, d), 3.0 if sampler != 1 else 0.9)
     lo[:, 0] = np.linspace(lo[0, 0], hi[0, 0], nsub + 1)[:-1]
     hi[:, 0] = np.linspace(lo[0, 0], hi[0, 0], nsub + 1)[1:]
-    samples = np.full(nsub, (1 << 21) // nsub, dtype=np.uint64)
+    samples = np.full(nsub, (1 << log2n) // nsub, dtype=np.uint64)
     samples[3] += 777
-    samples[5] -= 1000
+    if log2n == 28:
+        samples[5] += 1000   # 2^28 + 1777 in all: chunks of 512 rows
+    else:
+        samples[5] -= 1000
     lat = bfi.lattice(nx, nt)
     plan = bfi.Plan(lat, samples, precision)
     if sampler:
         plan.set_sampler(sampler, mean=np.zeros(d) if sampler == 2 else None,
                          factor=np.eye(d) * 0.8 if sampler == 2 else None)
     assert plan.info().chunks >= 2048
+    if log2n == 28:
+        assert plan.info().tail_subvolume == 14 and plan.info().tail_chunk_samples == 256 * 256
     lo_t, hi_t = torch.tensor(lo, device=dev), torch.tensor(hi, device=dev)
 
     def run():
@@ -355,9 +368,12 @@ def test_results_do_not_depend_on_which_cta_takes_a_chunk(bfi, dev, nx, nt, prec
 def test_paper_10x2_full_size_sampled(bfi, dev, precision):
     job = workloads.paper_10x2()
     g_s, g_t, plan = run_gpu(bfi, dev, job, precision)
-    assert plan.info().chunk_samples == 1024 * 256   # 4096 chunks of 1024 rows per thread
+    # 1024 rows per thread; the last 128 subvolumes in chunks of 256 rows, handed out last
+    info = plan.info()
+    assert info.chunk_samples == 1024 * 256 and info.tail_subvolume == 896 and info.tail_chunk_samples == 256 * 256
     # a fixed random subset of 64 of the 1024 subvolumes (subvolumes are independent, so subset parity is exact)
     pick = np.sort(np.random.default_rng(64).choice(1024, 64, replace=False))
+    assert (pick >= 896).sum() >= 4 and (pick < 896).sum() >= 4
     o_s, _ = run_oracle(job.subset(pick), fp32_points=bool(precision))
     tol = FP64_RTOL if precision == 0 else FP32_RTOL
     assert_slots_close(g_s[pick], o_s, 6, tol)

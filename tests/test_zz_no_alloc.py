@@ -61,21 +61,27 @@ def test_static_scratch_matches_plan_twice(bfi, dev, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_static_scratch_two_stage_screen(bfi, dev, precision):
+@pytest.mark.parametrize("log2n", [23, 24])
+def test_static_scratch_two_stage_screen(bfi, dev, precision, log2n):
     """10x2 with 16 subvolumes of 2^23 samples (2^27 in all, 2048 chunk
     records, well inside the array): chunks of 256 rows per thread, so the
     two-stage screen and its survivor queue run on the static scratch's hint
-    and counter layout.  Two calls in a row, each against the plan path."""
+    and counter layout.  With 2^24 per subvolume the chunks hold 512 rows and
+    the last two subvolumes are cut into tail chunks of 256 rows, the table
+    the static scratch builds on the device.  Two calls in a row, each against
+    the plan path."""
     rtol = FP64_RTOL if precision == 0 else FP32_RTOL
     lo_np, hi_np = workloads.bisected_boxes(20, 4)
-    samples = np.full(16, 1 << 23, dtype=np.uint64)
+    samples = np.full(16, 1 << log2n, dtype=np.uint64)
     lat = bfi.lattice(10, 2)
     lo = torch.tensor(lo_np, device=dev)
     hi = torch.tensor(hi_np, device=dev)
     plan = bfi.Plan(lat, samples, precision)
     p_slots, p_tot = plan.execute(lo, hi, 6)
     torch.cuda.synchronize()
-    assert plan.screen_stats()[1] and plan.info().chunk_samples == 256 * 256
+    info = plan.info()
+    assert plan.screen_stats()[1] and info.chunk_samples == (256 << (log2n - 23)) * 256
+    assert info.tail_subvolume == (16 if log2n == 23 else 14)
     p_slots, p_tot = p_slots.cpu().numpy(), p_tot.cpu().numpy()
     for _ in range(2):
         s_slots, s_tot = bfi.integrate_static_scratch(lat, samples, lo, hi, 6, precision=precision)
