@@ -509,7 +509,7 @@ def run_batch(bfi, dev, stream, njobs=256):
     tuned = {f"{nx}x{nt}": bfi.autotune_grid(bfi.lattice(nx, nt), bfi.FP32) for nx, nt in shapes}
     # the same jobs one after another, each alone on the device with its own plan and the same grid: the
     # sum of their CUDA-event times, against which the graph's replay shows what overlapping them gains
-    alone_ms = 0.0
+    alone_ms, alone_by_job = 0.0, []
     for j, dsc in zip(jobs, descs):
         plan = bfi.Plan(dsc["lattice"], j.samples, bfi.FP32)
         plan.set_grid(tuned[f"{j.nx}x{j.nt}"])
@@ -518,7 +518,8 @@ def run_batch(bfi, dev, stream, njobs=256):
         plan.execute(dsc["lo"], dsc["hi"], j.seed, j.job_id, stream=stream)
         ev1.record(stream)
         ev1.synchronize()
-        alone_ms += ev0.elapsed_time(ev1)
+        alone_by_job.append(ev0.elapsed_time(ev1))
+        alone_ms += alone_by_job[-1]
         plan.close()
     ok = all(bool(torch.isfinite(t[0]).item()) for t in b.totals)
     # the ops-weighted roofline of one replay: every job's counted work (its own screen, stage-1 and evaluation
@@ -529,11 +530,15 @@ def run_batch(bfi, dev, stream, njobs=256):
         ops = screen_work(w, j.nx, j.nt) + w["evaluated"] * eval_ops_fp32(j.nx, j.nt)
         issue += ops
         key = f"{j.nx}x{j.nt}"
-        acc = by_shape.setdefault(key, {"jobs": 0, "samples": 0, "Gops": 0.0, "stage1": 0})
+        acc = by_shape.setdefault(key, {"jobs": 0, "samples": 0, "Gops": 0.0, "stage1": 0, "alone_ms": 0.0})
         acc["jobs"] += 1
         acc["samples"] += w["samples"]
         acc["Gops"] += ops / 1e9
         acc["stage1"] += w["stage1"]
+        acc["alone_ms"] += alone_by_job[k]
+    for acc in by_shape.values():
+        # the shape's jobs run alone: their counted work over their own time, against the issue peak
+        acc["alone_frac"] = acc["Gops"] * 1e9 / (acc["alone_ms"] * 1e-3) / ISSUE_PEAK_OPS
     b.close()
     achieved = issue / (ms * 1e-3)
     roof = {"bound": "alu", "resource": "FP32/INT issue", "achieved": achieved / 1e9, "peak": ISSUE_PEAK_OPS / 1e9,

@@ -228,25 +228,38 @@ struct GenArgs {
 };
 
 // ---------------------------------------------------------------------------
-// Register-resident FP32 screen for Nx = 32 SPL.  Lane t owns the spatial
-// sites [SPL t, SPL t + SPL) with all NT time slices: the coordinates
-// [C t, C t + C), C = SPL NT, which are whole Philox blocks (C is a multiple
-// of 4).  It draws its own blocks, keeps the field and the chunk's box in
-// registers, and takes the one site of each spatial neighbour from lanes
-// t - 1 and t + 1 (2 NT shuffles), so the screen touches no shared memory.
-// For even NT the residuals of slices l and l + NT/2 run as one f32x2 pair.
-// The per-lane residual sums meet in an XOR butterfly (bit-identical on all
-// lanes).  Points and residuals round as the shared-memory screen's do; only
-// the order of the sum differs.
+// Register-resident FP32 screen for Nx = G SPL.  A group of G lanes (the whole
+// warp, or each half of it: two samples per warp) screens one sample, and its
+// lane t owns the spatial sites [SPL t, SPL t + SPL) with all NT time slices:
+// the coordinates [C t, C t + C), C = SPL NT, which are whole Philox blocks
+// (C is a multiple of 4).  It draws its own blocks, keeps the field and the
+// chunk's box in registers, and takes the one site of each spatial neighbour
+// from lanes t - 1 and t + 1 of its group (2 NT shuffles), so the screen
+// touches no shared memory.  For even NT the residuals of slices l and
+// l + NT/2 run as one f32x2 pair.  The per-lane residual sums meet in an XOR
+// butterfly within the group (bit-identical on its lanes).  Points and
+// residuals round as the shared-memory screen's do; only the order of the sum
+// differs.  Half-warp groups serve the shapes whose lanes would otherwise own
+// a single Philox block (C = 4 at G = 32): the fixed costs of a sample (the
+// neighbour shuffles, the butterfly, the screen's decision) then spread over
+// twice the sites, and each lane runs two independent Philox chains.
 // ---------------------------------------------------------------------------
-template <int SPL, int NT>
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <int SPL, int NT, int G = 32>
 struct LaneScreen {
     static constexpr int C = SPL * NT;
     static_assert(C % 4 == 0, "a lane's coordinates must be whole Philox blocks");
+    static_assert(G == 32 || G == 16, "a sample's group is a warp or half of one");
     float lo[C], w[C];
 
     __device__ __forceinline__ void load(const float2 *bf) {
-        const int j0 = (threadIdx.x & 31) * C;
+        const int j0 = (threadIdx.x & (G - 1)) * C;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             lo[c] = bf[j0 + c].x;
@@ -254,18 +267,20 @@ struct LaneScreen {
         }
     }
 
-    // Where block q = lane (C/4) + b of the chunk keeps its Philox prefix: at
-    // b 32 + lane, so that the lanes of a warp read consecutive words.
-    __host__ __device__ static int prefix_slot(int q) { return (q % (C / 4)) * 32 + q / (C / 4); }
+    // Where block q = t (C/4) + b of the chunk keeps its Philox prefix: at
+    // b G + t, so that the lanes of a group read consecutive words (and the
+    // two groups of a warp the same ones).
+    __host__ __device__ static int prefix_slot(int q) { return (q % (C / 4)) * G + q / (C / 4); }
 
+    // S of sample i (the group's own sample), on every lane of the group.
     __device__ __forceinline__ float action(uint64_t i, const uint4 *pre4, const uint32_t *pre1, const RoundKeys &rk,
                                             const LatticeConst<float> &cf) const {
-        const int lane = threadIdx.x & 31;
+        const int lane = threadIdx.x & 31, t = lane & (G - 1), base = lane - t;
         float X[C];  // X[s NT + l]
 #pragma unroll
         for (int b = 0; b < C / 4; ++b) {
-            const uint4 a = pre4[b * 32 + lane];
-            const PhiloxPrefix p{a.x, a.y, a.z, a.w, pre1[b * 32 + lane], {0u, 0u, 0u}};
+            const uint4 a = pre4[b * G + t];
+            const PhiloxPrefix p{a.x, a.y, a.z, a.w, pre1[b * G + t], {0u, 0u, 0u}};
             const uint4 r = philox_from_prefix(static_cast<uint32_t>(i), p, rk);
             X[4 * b + 0] = Coord<float>::map(r.x, lo[4 * b + 0], w[4 * b + 0]);
             X[4 * b + 1] = Coord<float>::map(r.y, lo[4 * b + 1], w[4 * b + 1]);
@@ -275,8 +290,8 @@ struct LaneScreen {
         float left[NT], right[NT];
 #pragma unroll
         for (int l = 0; l < NT; ++l) {
-            left[l] = __shfl_sync(0xffffffffu, X[(SPL - 1) * NT + l], (lane + 31) & 31);
-            right[l] = __shfl_sync(0xffffffffu, X[l], (lane + 1) & 31);
+            left[l] = __shfl_sync(0xffffffffu, X[(SPL - 1) * NT + l], base + ((t + G - 1) & (G - 1)));
+            right[l] = __shfl_sync(0xffffffffu, X[l], base + ((t + 1) & (G - 1)));
         }
         float acc;
         if constexpr (NT % 2 == 0) {
@@ -321,12 +336,12 @@ struct LaneScreen {
                 }
             }
         }
-        float S = warp_sum(acc) * cf.inv_2Dtau;
+        float S = group_sum<G>(acc) * cf.inv_2Dtau;
         if (cf.half_mass2 != 0.f) {
             float s2 = 0.f;
 #pragma unroll
             for (int c = 0; c < C; ++c) s2 = fmaf(X[c], X[c], s2);
-            S = fmaf(cf.half_mass2, warp_sum(s2), S);
+            S = fmaf(cf.half_mass2, group_sum<G>(s2), S);
         }
         return S;
     }
@@ -337,23 +352,25 @@ struct NoLaneScreen {
     __device__ __forceinline__ void load(const float2 *) {}
     __host__ __device__ static int prefix_slot(int q) { return q; }
 };
-template <int SPL, int NT>
+template <int SPL, int NT, int G>
 struct ScreenOf {
-    using type = LaneScreen<SPL, NT>;
+    using type = LaneScreen<SPL, NT, G>;
 };
-template <int NT>
-struct ScreenOf<0, NT> {
+template <int NT, int G>
+struct ScreenOf<0, NT, G> {
     using type = NoLaneScreen;
 };
 
 // ---------------------------------------------------------------------------
 // The integrand.  FP64 = true: FP32 screen, FP64 evaluation; false: FP32
 // screen and evaluation with the compensated action near the minimum.  SPL > 0
-// takes the register-resident screen (Nx = 32 SPL, NT time slices); SPL = 0
-// the shared-memory one, for any shape.
+// takes the register-resident screen (Nx = G SPL, NT time slices; with G = 16
+// a warp screens two consecutive samples at once and evaluates the candidates
+// among them in sample order); SPL = 0 the shared-memory one, for any shape.
 // ---------------------------------------------------------------------------
-template <bool FP64, int SPL, int NT>
+template <bool FP64, int SPL, int NT, int G = 32>
 __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
+    constexpr int P = SPL > 0 ? 32 / G : 1;  // samples a warp screens at once
     extern __shared__ __align__(16) unsigned char sm[];
     const IntegrandArgs &args = ga.a;
     const GenShape &g = ga.g;
@@ -383,7 +400,7 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
         }
         if (tid == 0) *cnt_all = 0u;
         __syncthreads();
-        typename ScreenOf<SPL, NT>::type scr;
+        typename ScreenOf<SPL, NT, G>::type scr;
         scr.load(bf);
         // the chunk's Philox prefixes: the sample index's high word and the sub_id are fixed within a chunk
         uint4 *pre4 = reinterpret_cast<uint4 *>(sm + L.pre4);
@@ -402,74 +419,81 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
         float m_ref = hint;
         double m_acc = static_cast<double>(hint);
         unsigned n_eval = 0;
-        for (uint64_t k = warp; k < v.cnt; k += kGWarps) {
-            const uint64_t i = v.first + k;
-            float S_f;
+        for (uint64_t k0 = static_cast<uint64_t>(warp) * P; k0 < v.cnt; k0 += kGWarps * P) {
+            // the screen of samples k0 .. k0 + P - 1 (group p of the warp screens k0 + p)
+            float S_group;
             if constexpr (SPL > 0) {
-                S_f = scr.action(i, pre4, pre1, ga.rk, ga.cf);
+                S_group = scr.action(v.first + k0 + (P > 1 ? lane / G : 0), pre4, pre1, ga.rk, ga.cf);
             } else {
-                warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
-                S_f = warp_action<float>(uf, next, g, ga.cf);
+                warp_point<float>(v.first + k0, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
+                S_group = warp_action<float>(uf, next, g, ga.cf);
             }
-            if (FP64) {
-                if (!(S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f)) continue;
-                warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<double>::map(w, ld[j], wd[j]); }, ud);
-                const double S = warp_action<double>(ud, next, g, ga.cd);
-                m_ref = fminf(m_ref, __double2float_rn(S));
-                if (S < m_acc - kRescaleMargin) {
-                    const double f = exp(S - m_acc), f2 = f * f;
-                    for (int kk = lane; kk < g.K; kk += 32) sd[kk] *= second_order(kk, g.R) ? f2 : f;
-                    m_acc = S;
-                    __syncwarp();  // another lane owns some of the sums it rescaled
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const uint64_t k = k0 + p;
+                if (P > 1 && k >= v.cnt) break;  // the chunk's ragged end (warp-uniform)
+                const uint64_t i = v.first + k;
+                const float S_f = P > 1 ? __shfl_sync(0xffffffffu, S_group, p * G) : S_group;
+                if (FP64) {
+                    if (!(S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f)) continue;
+                    warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<double>::map(w, ld[j], wd[j]); }, ud);
+                    const double S = warp_action<double>(ud, next, g, ga.cd);
+                    m_ref = fminf(m_ref, __double2float_rn(S));
+                    if (S < m_acc - kRescaleMargin) {
+                        const double f = exp(S - m_acc), f2 = f * f;
+                        for (int kk = lane; kk < g.K; kk += 32) sd[kk] *= second_order(kk, g.R) ? f2 : f;
+                        m_acc = S;
+                        __syncwarp();  // another lane owns some of the sums it rescaled
+                    }
+                    const double w = exp(m_acc - S);
+                    if (lane == 0) {
+                        sd[0] += w;
+                        sd[1] += w * w;
+                    }
+                    lane_products(ud, g, [&](int r, double q) {
+                        const double wq = w * q;
+                        sd[2 + r] += wq;
+                        sd[2 + g.R + r] += w * wq;
+                        sd[2 + 2 * g.R + r] += wq * wq;
+                    });
+                } else {
+                    // the screen's margin, as in FP64 mode: no sample within the window is dropped
+                    if (!(S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f)) continue;
+                    if constexpr (SPL > 0)  // the evaluation reads the point from shared memory
+                        warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
+                    // every candidate: compensated action, exact power-of-two shift moves, split-argument weight
+                    const DF S = warp_action_df(uf, next, g, ga.cdf);
+                    m_ref = fminf(m_ref, S.h);
+                    const double S_d = static_cast<double>(S.h) + static_cast<double>(S.l);
+                    if (S_d < m_acc - kRescaleMargin) {
+                        const int steps = shift_steps(m_acc, S_d);
+                        const float f = pow2_neg(steps), f2 = f * f;
+                        for (int kk = lane; kk < g.K; kk += 32) sf[kk] *= second_order(kk, g.R) ? f2 : f;
+                        for (int kk = lane; kk < 1 + g.R; kk += 32) cf[kk] *= f;
+                        m_acc -= steps * kLn2;
+                        __syncwarp();  // another lane owns some of the sums it rescaled
+                    }
+                    const float w = weight_f32(m_acc, S);
+                    auto kahan = [&](int k, int ci, float x) {
+                        const float y = x - cf[ci];
+                        const float t = sf[k] + y;
+                        cf[ci] = (t - sf[k]) - y;
+                        sf[k] = t;
+                    };
+                    if (lane == 0) {
+                        kahan(0, 0, w);
+                        sf[1] += w * w;
+                    }
+                    lane_products(uf, g, [&](int r, DF q) {
+                        const float wq = __fmaf_rn(w, q.h, w * q.l);  // w Q_r rounded once
+                        kahan(2 + r, 1 + r, wq);
+                        sf[2 + g.R + r] += w * wq;
+                        sf[2 + 2 * g.R + r] += wq * wq;
+                    });
                 }
-                const double w = exp(m_acc - S);
-                if (lane == 0) {
-                    sd[0] += w;
-                    sd[1] += w * w;
-                }
-                lane_products(ud, g, [&](int r, double q) {
-                    const double wq = w * q;
-                    sd[2 + r] += wq;
-                    sd[2 + g.R + r] += w * wq;
-                    sd[2 + 2 * g.R + r] += wq * wq;
-                });
-            } else {
-                // the screen's margin, as in FP64 mode: no sample within the window is dropped
-                if (!(S_f <= m_ref + args.skip_window + 1.0f + 1e-3f * S_f)) continue;
-                if constexpr (SPL > 0)  // the evaluation reads the point from shared memory
-                    warp_point<float>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
-                // every candidate: compensated action, exact power-of-two shift moves, split-argument weight
-                const DF S = warp_action_df(uf, next, g, ga.cdf);
-                m_ref = fminf(m_ref, S.h);
-                const double S_d = static_cast<double>(S.h) + static_cast<double>(S.l);
-                if (S_d < m_acc - kRescaleMargin) {
-                    const int steps = shift_steps(m_acc, S_d);
-                    const float f = pow2_neg(steps), f2 = f * f;
-                    for (int kk = lane; kk < g.K; kk += 32) sf[kk] *= second_order(kk, g.R) ? f2 : f;
-                    for (int kk = lane; kk < 1 + g.R; kk += 32) cf[kk] *= f;
-                    m_acc -= steps * kLn2;
-                    __syncwarp();  // another lane owns some of the sums it rescaled
-                }
-                const float w = weight_f32(m_acc, S);
-                auto kahan = [&](int k, int ci, float x) {
-                    const float y = x - cf[ci];
-                    const float t = sf[k] + y;
-                    cf[ci] = (t - sf[k]) - y;
-                    sf[k] = t;
-                };
-                if (lane == 0) {
-                    kahan(0, 0, w);
-                    sf[1] += w * w;
-                }
-                lane_products(uf, g, [&](int r, DF q) {
-                    const float wq = __fmaf_rn(w, q.h, w * q.l);  // w Q_r rounded once
-                    kahan(2 + r, 1 + r, wq);
-                    sf[2 + g.R + r] += w * wq;
-                    sf[2 + 2 * g.R + r] += wq * wq;
-                });
+                ++n_eval;
+                __syncwarp();
             }
-            ++n_eval;
-            __syncwarp();
         }
         if (lane == 0) {
             mw[warp] = m_acc;
@@ -717,28 +741,28 @@ GenArgs make_gen_args(const IntegrandArgs &a, const LatticeParams &p, uint32_t s
     return ga;
 }
 
-template <bool FP64, int SPL = 0, int NT = 0>
+template <bool FP64, int SPL = 0, int NT = 0, int G = 32>
 cudaError_t gen_integrand_launcher(const IntegrandArgs &args, const LatticeParams &p, uint32_t seed, uint32_t job,
                                    int grid, cudaStream_t st) {
     const GenArgs ga = make_gen_args(args, p, seed, job);
     cudaError_t e = cudaFuncSetAttribute(generic_hint, cudaFuncAttributeMaxDynamicSharedMemorySize, ga.L.total);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(generic_integrand<FP64, SPL, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(generic_integrand<FP64, SPL, NT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  ga.L.total);
     if (e != cudaSuccess) return e;
     generic_hint<<<static_cast<unsigned>(args.nsub), kGBlock, ga.L.total, st>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    generic_integrand<FP64, SPL, NT><<<grid, kGBlock, ga.L.total, st>>>(ga);
+    generic_integrand<FP64, SPL, NT, G><<<grid, kGBlock, ga.L.total, st>>>(ga);
     return cudaGetLastError();
 }
 
-template <bool FP64, int SPL = 0, int NT = 0>
+template <bool FP64, int SPL = 0, int NT = 0, int G = 32>
 cudaError_t gen_occupancy(int nx, int nt, int *blocks_per_sm) {
     const GenLayout L = gen_layout(gen_shape(nx, nt));
-    cudaError_t e = cudaFuncSetAttribute(generic_integrand<FP64, SPL, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         L.total);
+    cudaError_t e = cudaFuncSetAttribute(generic_integrand<FP64, SPL, NT, G>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, generic_integrand<FP64, SPL, NT>, kGBlock,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, generic_integrand<FP64, SPL, NT, G>, kGBlock,
                                                          L.total);
 }
 
@@ -775,13 +799,17 @@ cudaError_t mapped_occupancy(int nx, int nt, int *blocks_per_sm) {
 const ShapeKernels kGeneric = {0, 0, 1, {gen_integrand_launcher<true>, gen_integrand_launcher<false>},
                                {gen_occupancy<true>, gen_occupancy<false>}, gen_eval, nullptr, nullptr, nullptr, nullptr, 0};
 
-// Shapes with Nx = 32 SPL and SPL NT in {4, 8, 16}: the register-resident screen.
-#define BFI_LANES(SPL, NT)                                                                                   \
-    {32 * SPL, NT, 1, {gen_integrand_launcher<true, SPL, NT>, gen_integrand_launcher<false, SPL, NT>},      \
-     {gen_occupancy<true, SPL, NT>, gen_occupancy<false, SPL, NT>}, gen_eval, nullptr, nullptr, nullptr, nullptr, 0}
-const ShapeKernels kLanes[] = {BFI_LANES(1, 4),  BFI_LANES(1, 8), BFI_LANES(1, 16), BFI_LANES(2, 2),
-                               BFI_LANES(2, 4),  BFI_LANES(2, 8), BFI_LANES(4, 1),  BFI_LANES(4, 2),
-                               BFI_LANES(4, 4),  BFI_LANES(8, 1), BFI_LANES(8, 2),  BFI_LANES(16, 1)};
+// Shapes with Nx = G SPL and SPL NT in {4, 8, 16}: the register-resident
+// screen.  The shapes whose lanes would own one Philox block each (32x4, 64x2,
+// 128x1) screen two samples per warp in half-warp groups, eight coordinates a
+// lane.
+#define BFI_LANES(SPL, NT, G)                                                                                     \
+    {G * SPL, NT, 1, {gen_integrand_launcher<true, SPL, NT, G>, gen_integrand_launcher<false, SPL, NT, G>},      \
+     {gen_occupancy<true, SPL, NT, G>, gen_occupancy<false, SPL, NT, G>}, gen_eval, nullptr, nullptr, nullptr, \
+     nullptr, 0}
+const ShapeKernels kLanes[] = {BFI_LANES(2, 4, 16), BFI_LANES(1, 8, 32), BFI_LANES(1, 16, 32), BFI_LANES(4, 2, 16),
+                               BFI_LANES(2, 4, 32), BFI_LANES(2, 8, 32), BFI_LANES(8, 1, 16), BFI_LANES(4, 2, 32),
+                               BFI_LANES(4, 4, 32), BFI_LANES(8, 1, 32), BFI_LANES(8, 2, 32), BFI_LANES(16, 1, 32)};
 #undef BFI_LANES
 
 }  // namespace

@@ -1,8 +1,9 @@
-"""The register-resident screen of the generic kernel (Nx = 32 SPL, each lane
-owning whole sites and Philox blocks) on every shape it is compiled for,
-against the oracle: FP64 records at the FP64 parity bound, FP32 records against
-the oracle on the same float points, and general parameters with the mass term
-(the screen's second warp sum)."""
+"""The register-resident screen of the generic kernel (Nx = G SPL, each lane
+of a G-lane group owning whole sites and Philox blocks; half-warp groups, two
+samples per warp, for 32x4, 64x2 and 128x1) on every shape it is compiled
+for, against the oracle: FP64 records at the FP64 parity bound, FP32 records
+against the oracle on the same float points, and general parameters with the
+mass term (the screen's second group sum) on the half-warp shapes."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,7 @@ import workloads
 from test_parity_gpu import (FP32_ERR_ATOL, FP32_RTOL, FP64_RTOL, assert_slots_close, assert_totals_close, budget,
                              dev, run_gpu, run_oracle)  # noqa: F401 (dev is a fixture)
 
-# Nx = 32 SPL with SPL Nt in {4, 8, 16}: odd Nt (scalar residuals), Nt = 2 (the
+# Nx = G SPL with SPL Nt in {4, 8, 16}: odd Nt (scalar residuals), Nt = 2 (the
 # packed pair's seam on every slice), and up to 16 coordinates per lane
 LANES = [(32, 4), (32, 8), (32, 16), (64, 2), (64, 4), (64, 8), (128, 1), (128, 2), (128, 4), (256, 1),
          (256, 2), (512, 1)]
