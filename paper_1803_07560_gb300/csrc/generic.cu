@@ -272,8 +272,9 @@ struct LaneScreen {
     // two groups of a warp the same ones).
     __host__ __device__ static int prefix_slot(int q) { return (q % (C / 4)) * G + q / (C / 4); }
 
-    // S of sample i (the group's own sample), on every lane of the group.
-    __device__ __forceinline__ float action(uint64_t i, const uint4 *pre4, const uint32_t *pre1, const RoundKeys &rk,
+    // S of the group's own sample, whose index has low word i (the chunk's
+    // prefixes hold the rest), on every lane of the group.
+    __device__ __forceinline__ float action(uint32_t i, const uint4 *pre4, const uint32_t *pre1, const RoundKeys &rk,
                                             const LatticeConst<float> &cf) const {
         const int lane = threadIdx.x & 31, t = lane & (G - 1), base = lane - t;
         float X[C];  // X[s NT + l]
@@ -281,7 +282,7 @@ struct LaneScreen {
         for (int b = 0; b < C / 4; ++b) {
             const uint4 a = pre4[b * G + t];
             const PhiloxPrefix p{a.x, a.y, a.z, a.w, pre1[b * G + t], {0u, 0u, 0u}};
-            const uint4 r = philox_from_prefix(static_cast<uint32_t>(i), p, rk);
+            const uint4 r = philox_from_prefix(i, p, rk);
             X[4 * b + 0] = Coord<float>::map(r.x, lo[4 * b + 0], w[4 * b + 0]);
             X[4 * b + 1] = Coord<float>::map(r.y, lo[4 * b + 1], w[4 * b + 1]);
             X[4 * b + 2] = Coord<float>::map(r.z, lo[4 * b + 2], w[4 * b + 2]);
@@ -368,8 +369,15 @@ struct ScreenOf<0, NT, G> {
 // a warp screens two consecutive samples at once and evaluates the candidates
 // among them in sample order); SPL = 0 the shared-memory one, for any shape.
 // ---------------------------------------------------------------------------
+// 16 coordinates a lane at SPL >= 2 (64x8, 128x4, 256x2, 512x1) compile to 96
+// registers without spilling when asked for 5 CTAs per SM (4 otherwise); 32x16
+// would spill.  0 asks for no minimum and leaves every other shape to the
+// compiler's own allocation (an explicit 1 would let it take up to 255).
+template <int SPL, int NT>
+constexpr int lane_min_blocks() { return SPL * NT == 16 && SPL >= 2 ? 5 : 0; }
+
 template <bool FP64, int SPL, int NT, int G = 32>
-__global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
+__global__ void __launch_bounds__(kGBlock, lane_min_blocks<SPL, NT>()) generic_integrand(const GenArgs ga) {
     constexpr int P = SPL > 0 ? 32 / G : 1;  // samples a warp screens at once
     extern __shared__ __align__(16) unsigned char sm[];
     const IntegrandArgs &args = ga.a;
@@ -419,19 +427,21 @@ __global__ void __launch_bounds__(kGBlock) generic_integrand(const GenArgs ga) {
         float m_ref = hint;
         double m_acc = static_cast<double>(hint);
         unsigned n_eval = 0;
-        for (uint64_t k0 = static_cast<uint64_t>(warp) * P; k0 < v.cnt; k0 += kGWarps * P) {
+        // sample offsets in the chunk are 32-bit (a chunk never crosses a multiple of 2^32)
+        const uint32_t cnt = static_cast<uint32_t>(v.cnt), xb = static_cast<uint32_t>(v.first);
+        for (uint32_t k0 = static_cast<uint32_t>(warp) * P; k0 < cnt; k0 += kGWarps * P) {
             // the screen of samples k0 .. k0 + P - 1 (group p of the warp screens k0 + p)
             float S_group;
             if constexpr (SPL > 0) {
-                S_group = scr.action(v.first + k0 + (P > 1 ? lane / G : 0), pre4, pre1, ga.rk, ga.cf);
+                S_group = scr.action(xb + k0 + (P > 1 ? lane / G : 0), pre4, pre1, ga.rk, ga.cf);
             } else {
                 warp_point<float>(v.first + k0, v.sid, ga.rk, g, [&](int j, uint32_t w) { return Coord<float>::map(w, bf[j].x, bf[j].y); }, uf);
                 S_group = warp_action<float>(uf, next, g, ga.cf);
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const uint64_t k = k0 + p;
-                if (P > 1 && k >= v.cnt) break;  // the chunk's ragged end (warp-uniform)
+                const uint32_t k = k0 + p;
+                if (P > 1 && k >= cnt) break;  // the chunk's ragged end (warp-uniform)
                 const uint64_t i = v.first + k;
                 const float S_f = P > 1 ? __shfl_sync(0xffffffffu, S_group, p * G) : S_group;
                 if (FP64) {
