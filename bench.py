@@ -297,7 +297,8 @@ def workload_config(world, per_sub=SAMPLES_PER_SUB):
 def make_job(rank, world, samples_per_sub):
     import workloads
     k = 10 + int(round(math.log2(world)))
-    lo, hi = workloads.bisected_boxes(D, min(k, D))
+    lo, hi = workloads.bisected_boxes(D, k)   # 2^k boxes for any d (the bisection cycles when d < k)
+    assert lo.shape[0] == NSUB_PER_RANK * world
     sl = slice(rank * NSUB_PER_RANK, (rank + 1) * NSUB_PER_RANK)
     return workloads.Job(NX, NT, lo[sl], hi[sl], np.full(NSUB_PER_RANK, samples_per_sub, dtype=np.uint64),
                          seed=2, sub_id=np.arange(sl.start, sl.stop, dtype=np.uint32))

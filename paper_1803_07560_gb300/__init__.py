@@ -247,7 +247,10 @@ def totals_len(nx: int) -> int:
     return _lib.bfi_totals_len(nx)
 
 
-def _dev_ptr(t, dtype=None):
+def _dev_ptr(t, dtype=None, numel=None, what="tensor"):
+    """Device address of a contiguous CUDA tensor.  With numel, the tensor must
+    hold exactly that many elements: the library reads and writes device
+    arrays by the sizes the plan or call fixes, and cannot check them there."""
     import torch
     if t is None:
         return None
@@ -255,6 +258,8 @@ def _dev_ptr(t, dtype=None):
         raise TypeError("expected a contiguous CUDA tensor")
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} has {t.numel()} elements, the call needs {numel}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -299,10 +304,13 @@ class Plan:
             slots = torch.empty((self.nsub, slot_len(nx)), dtype=torch.float64, device=lo.device)
         if totals is None:
             totals = torch.empty(totals_len(nx), dtype=torch.float64, device=lo.device)
-        _check(_lib.bfi_plan_execute(self._h, _dev_ptr(lo, torch.float64), _dev_ptr(hi, torch.float64),
-                                     _dev_ptr(sub_id, torch.int32) if sub_id is not None else None,
+        n, d = self.nsub, self.d
+        _check(_lib.bfi_plan_execute(self._h, _dev_ptr(lo, torch.float64, n * d, "lo"),
+                                     _dev_ptr(hi, torch.float64, n * d, "hi"),
+                                     _dev_ptr(sub_id, torch.int32, n, "sub_id") if sub_id is not None else None,
                                      seed & 0xFFFFFFFF, job_id & 0xFFFFFFFF,
-                                     _dev_ptr(slots, torch.float64), _dev_ptr(totals, torch.float64),
+                                     _dev_ptr(slots, torch.float64, n * slot_len(nx), "slots"),
+                                     _dev_ptr(totals, torch.float64, totals_len(nx), "totals"),
                                      _stream_ptr(stream)))
         return slots, totals
 
@@ -374,9 +382,14 @@ class Context:
         nsub = lo_a.shape[0]
         smp_a, smp_p = _host(np.broadcast_to(np.asarray(samples, dtype=np.uint64), (nsub,)), np.uint64)
         sid_a, sid_p = (None, None) if sub_id is None else _host(sub_id, np.uint32)
+        if hi_a.shape != lo_a.shape or (sid_a is not None and sid_a.size != nsub):
+            raise ValueError("lo, hi and sub_id must describe the same subvolumes")
         slots = out_slots if out_slots is not None else (
             np.empty((nsub, slot_len(lat.nx))) if want_slots else None)
         totals = out_totals if out_totals is not None else np.empty(totals_len(lat.nx))
+        for a, n in ((slots, nsub * slot_len(lat.nx)), (totals, totals_len(lat.nx))):
+            if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n):
+                raise ValueError(f"an output array needs {n} contiguous float64 elements")
         _check(_lib.bfi_integrate(self._h, ctypes.byref(lat), nsub, lo_p, hi_p, smp_p, sid_p,
                                   seed & 0xFFFFFFFF, job_id & 0xFFFFFFFF, precision,
                                   None if slots is None else ctypes.c_void_p(slots.ctypes.data),
@@ -440,11 +453,14 @@ def integrate_static_scratch(lat: Lattice, samples, lo, hi, seed: int, job_id: i
         slots = torch.empty((nsub, slot_len(lat.nx)), dtype=torch.float64, device=lo.device)
     if totals is None:
         totals = torch.empty(totals_len(lat.nx), dtype=torch.float64, device=lo.device)
+    d = lat.nx * lat.nt
     _check(_lib.bfi_integrate_static_scratch(
-        ctypes.byref(lat), nsub, smp.ctypes.data_as(_P(ctypes.c_uint64)), _dev_ptr(lo, torch.float64),
-        _dev_ptr(hi, torch.float64), _dev_ptr(sub_id, torch.int32) if sub_id is not None else None,
-        seed & 0xFFFFFFFF, job_id & 0xFFFFFFFF, precision, _dev_ptr(slots, torch.float64),
-        _dev_ptr(totals, torch.float64), _stream_ptr(stream)))
+        ctypes.byref(lat), nsub, smp.ctypes.data_as(_P(ctypes.c_uint64)), _dev_ptr(lo, torch.float64, nsub * d, "lo"),
+        _dev_ptr(hi, torch.float64, nsub * d, "hi"),
+        _dev_ptr(sub_id, torch.int32, nsub, "sub_id") if sub_id is not None else None,
+        seed & 0xFFFFFFFF, job_id & 0xFFFFFFFF, precision,
+        _dev_ptr(slots, torch.float64, nsub * slot_len(lat.nx), "slots"),
+        _dev_ptr(totals, torch.float64, totals_len(lat.nx), "totals"), _stream_ptr(stream)))
     return slots, totals
 
 
@@ -482,13 +498,14 @@ class Batch:
             arr[i].lattice = lat
             arr[i].nsub = smp.size
             arr[i].samples = smp.ctypes.data_as(_P(ctypes.c_uint64))
-            arr[i].lo = _dev_ptr(lo, torch.float64)
-            arr[i].hi = _dev_ptr(hi, torch.float64)
-            arr[i].sub_id = None if sid is None else _dev_ptr(sid, torch.int32)
+            n, d = int(smp.size), lat.nx * lat.nt
+            arr[i].lo = _dev_ptr(lo, torch.float64, n * d, f"job {i} lo")
+            arr[i].hi = _dev_ptr(hi, torch.float64, n * d, f"job {i} hi")
+            arr[i].sub_id = None if sid is None else _dev_ptr(sid, torch.int32, n, f"job {i} sub_id")
             arr[i].seed = j.get("seed", 0) & 0xFFFFFFFF
             arr[i].job_id = j.get("job_id", i) & 0xFFFFFFFF
-            arr[i].slots = _dev_ptr(slots, torch.float64)
-            arr[i].totals = _dev_ptr(totals, torch.float64)
+            arr[i].slots = _dev_ptr(slots, torch.float64, n * slot_len(lat.nx), f"job {i} slots")
+            arr[i].totals = _dev_ptr(totals, torch.float64, totals_len(lat.nx), f"job {i} totals")
             self._keep += [smp, lo, hi, sid]
             self.slots.append(slots)
             self.totals.append(totals)
@@ -597,6 +614,8 @@ class Server:
         hi_a, hi_p = _host(np.reshape(hi, (-1, d)), np.float64)
         nsub = lo_a.shape[0]
         smp_a, smp_p = _host(np.broadcast_to(np.asarray(samples, dtype=np.uint64), (nsub,)), np.uint64)
+        if hi_a.shape != lo_a.shape:
+            raise ValueError("lo and hi must describe the same subvolumes")
         h = ctypes.c_void_p()
         _check(_lib.bfi_submit(self._h, ctypes.byref(lat), nsub, lo_p, hi_p, smp_p, seed & 0xFFFFFFFF,
                                job_id & 0xFFFFFFFF, ctypes.byref(h)))
@@ -688,7 +707,7 @@ def points(d, lo, hi, sub_id, seed, job_id, first, count, precision=FP64, stream
     """Coordinates of samples [first, first+count) of one subvolume (CUDA tensors)."""
     import torch
     y = torch.empty((count, d), dtype=torch.float64, device=lo.device)
-    _check(_lib.bfi_points(d, _dev_ptr(lo, torch.float64), _dev_ptr(hi, torch.float64), sub_id,
+    _check(_lib.bfi_points(d, _dev_ptr(lo, torch.float64, d, "lo"), _dev_ptr(hi, torch.float64, d, "hi"), sub_id,
                            seed, job_id, first, count, precision, _dev_ptr(y), _stream_ptr(stream)))
     return y
 
@@ -699,6 +718,6 @@ def evaluate(lat: Lattice, y, precision=FP64, stream=None):
     n = y.shape[0]
     S = torch.empty(n, dtype=torch.float64, device=y.device)
     P = torch.empty((n, num_r(lat.nx)), dtype=torch.float64, device=y.device)
-    _check(_lib.bfi_eval(ctypes.byref(lat), n, _dev_ptr(y, torch.float64), precision, _dev_ptr(S),
+    _check(_lib.bfi_eval(ctypes.byref(lat), n, _dev_ptr(y, torch.float64, n * lat.nx * lat.nt, "y"), precision, _dev_ptr(S),
                          _dev_ptr(P), _stream_ptr(stream)))
     return S, P

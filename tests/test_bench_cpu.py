@@ -95,3 +95,25 @@ def test_kernel_hash_follows_code_not_comments():
     changed = dict(src)
     changed[bench.KERNEL_SOURCES[0]] = src[bench.KERNEL_SOURCES[0]].replace("x + 1", "x + 2")
     assert bench.kernel_sources_sha256(lambda n: changed[n]) != base
+
+
+def test_bench_jobs_have_one_box_per_budget_for_every_lattice(monkeypatch):
+    """The bench's job for --lattice NXxNT: 1024 subvolumes whatever d is (the
+    bisection cycles over the coordinates when d < 10), which partition
+    [-5, 5]^d; the plan reads one box per budget."""
+    import numpy as np
+    for nx, nt in [(4, 2), (3, 1), (10, 2), (32, 4)]:
+        monkeypatch.setattr(bench, "NX", nx)
+        monkeypatch.setattr(bench, "NT", nt)
+        monkeypatch.setattr(bench, "D", nx * nt)
+        job = bench.make_job(0, 1, 1 << 10)
+        d = nx * nt
+        assert job.lo.shape == job.hi.shape == (1024, d) and job.samples.shape == (1024,)
+        assert np.all(job.hi > job.lo) and np.all(job.lo >= -5.0) and np.all(job.hi <= 5.0)
+        vol = np.prod(job.hi - job.lo, axis=1)
+        assert abs(vol.sum() / 10.0 ** d - 1.0) < 1e-12 and len({tuple(r) for r in job.lo}) == 1024
+        # disjoint: in every pair of boxes some coordinate's intervals do not overlap
+        rng = np.random.default_rng(d)
+        for a, b in rng.integers(0, 1024, (200, 2)):
+            if a != b:
+                assert np.any((job.hi[a] <= job.lo[b]) | (job.hi[b] <= job.lo[a]))

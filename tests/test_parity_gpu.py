@@ -245,6 +245,28 @@ def test_edge_cases_empty_single_and_tiny(bfi, dev):
     assert_totals_close(g_t2, o_t2, 3, FP64_RTOL, 1e-9)
 
 
+def test_binding_checks_array_sizes_before_any_launch(bfi, dev):
+    """The library reads and writes device arrays by the sizes the plan fixes;
+    the binding refuses tensors of another size before calling it."""
+    lat = bfi.lattice(4, 2)
+    plan = bfi.Plan(lat, [1000, 1000])
+    lo, hi = torch.zeros((2, 8), dtype=torch.float64, device=dev), torch.ones((2, 8), dtype=torch.float64, device=dev)
+    with pytest.raises(ValueError):
+        plan.execute(lo[:1], hi[:1], 1)
+    with pytest.raises(ValueError):
+        plan.execute(lo, hi, 1, sub_id=torch.zeros(3, dtype=torch.int32, device=dev))
+    with pytest.raises(ValueError):
+        plan.execute(lo, hi, 1, slots=torch.empty((1, bfi.slot_len(4)), dtype=torch.float64, device=dev))
+    with pytest.raises(ValueError):
+        bfi.integrate_static_scratch(lat, [1000, 1000, 1000], lo, hi, 1)
+    with pytest.raises(ValueError):
+        bfi.Batch([dict(lattice=lat, samples=[10, 10, 10], lo=lo, hi=hi)], autotune=False)
+    s, t = plan.execute(lo, hi, 1)   # the right sizes still run
+    torch.cuda.synchronize()
+    assert np.isfinite(t.cpu().numpy()[0])
+    plan.close()
+
+
 def test_device_merge_equals_host_merge_and_is_deterministic(bfi, dev):
     job = workloads.small_ragged(10, 2, seed=2, nsub=5, base=20_000)
     g_s, g_t, _ = run_gpu(bfi, dev, job, 0)

@@ -53,17 +53,25 @@ class Job:
 
 
 def bisected_boxes(d: int, k: int, half: float = 5.0):
-    """2^k subvolumes of [-half, half]^d: coordinate j < k is bisected once;
-    subvolume s takes the upper half [0, half] of coordinate j iff bit j of s
-    is set, and the full range in coordinates j >= k."""
+    """2^k subvolumes of [-half, half]^d.  With k <= d, coordinate j < k is
+    bisected once: subvolume s takes the upper half [0, half] of coordinate j
+    iff bit j of s is set, and the full range in coordinates j >= k.  With
+    k > d the bisection cycles over the coordinates: bit b of s splits
+    coordinate b mod d once more, the bits of a coordinate read from its first
+    split (most significant) on, so every subvolume is one of 2^(levels)
+    equal intervals in each coordinate."""
     nsub = 1 << k
     lo = np.full((nsub, d), -half)
     hi = np.full((nsub, d), half)
     s = np.arange(nsub)
-    for j in range(k):
-        upper = ((s >> j) & 1).astype(bool)
-        lo[upper, j] = 0.0
-        hi[~upper, j] = 0.0
+    for j in range(min(d, k)):
+        bits = list(range(j, k, d))   # the bits of s that split coordinate j, first split first
+        idx = np.zeros(nsub, dtype=np.int64)
+        for b in bits:
+            idx = 2 * idx + ((s >> b) & 1)
+        width = 2.0 * half / (1 << len(bits))
+        lo[:, j] = -half + idx * width
+        hi[:, j] = -half + (idx + 1) * width
     return lo, hi
 
 
