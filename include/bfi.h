@@ -400,9 +400,11 @@ bfi_status bfi_batch_get_work(bfi_batch *batch, int32_t job, bfi_work *work);
 bfi_status bfi_batch_destroy(bfi_batch *batch);
 
 /* Autotuner of the persistent grid: times the integrand of a synthetic job of
- * this lattice shape ([-5,5]^d, 64 subvolumes) at every CTAs-per-SM value up
- * to the occupancy limit and returns the fastest; the choice is cached per
- * (shape, precision, device) for the process.  Errors: as bfi_plan_create. */
+ * this lattice shape ([-5,5]^d, 64 subvolumes) at every CTAs-per-SM value
+ * from the occupancy limit down and returns the occupancy limit unless a
+ * smaller grid is at least 2% faster (median of 5 runs); the choice is cached
+ * per (shape, precision, device) for the process.  Errors: as
+ * bfi_plan_create. */
 bfi_status bfi_autotune_grid(const bfi_lattice *lattice, bfi_precision precision, int device,
                              int32_t *ctas_per_sm);
 

@@ -97,13 +97,17 @@ bfi_status bfi_autotune_grid(const bfi_lattice *lattice, bfi_precision precision
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
+    // From the occupancy limit down: a smaller grid is chosen only when it wins
+    // by 2%.  Measured on GB300, the batching workload ran 0.8% faster with
+    // every job at its occupancy limit than with grids an earlier tuner picked
+    // from the smallest grid up (ties and timing noise favoured small grids).
     int best = max_per_sm;
     float best_ms = INFINITY;
-    for (int c = 1; c <= max_per_sm && st == BFI_OK; ++c) {
+    for (int c = max_per_sm; c >= 1 && st == BFI_OK; --c) {
         if ((st = bfi_plan_set_grid(plan, c)) != BFI_OK) break;
         st = bfi_plan_execute(plan, d_lo, d_hi, nullptr, 1u, 0u, d_slots, d_tot, nullptr);  // warm-up
         std::vector<float> t;
-        for (int rep = 0; rep < 3 && st == BFI_OK; ++rep) {
+        for (int rep = 0; rep < 5 && st == BFI_OK; ++rep) {
             cudaEventRecord(a, nullptr);
             st = bfi_plan_execute(plan, d_lo, d_hi, nullptr, 1u, 0u, d_slots, d_tot, nullptr);
             cudaEventRecord(b, nullptr);
@@ -114,8 +118,8 @@ bfi_status bfi_autotune_grid(const bfi_lattice *lattice, bfi_precision precision
         }
         if (st != BFI_OK) break;
         std::sort(t.begin(), t.end());
-        if (t[1] < best_ms * 0.99f) {  // a smaller grid must win by 1% to be chosen
-            best_ms = t[1];
+        if (best_ms == INFINITY || t[2] < best_ms * 0.98f) {
+            best_ms = t[2];
             best = c;
         }
     }
