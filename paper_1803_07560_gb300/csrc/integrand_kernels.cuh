@@ -635,6 +635,7 @@ struct ChunkShared {
     double f[BLOCK];  // per-thread shift factors of the chunk record
     double mb;
     long long next;   // the chunk this CTA takes next
+    int left[BLOCK / 32];  // each warp's candidates left at the end of the chunk
     int min_bits;
     unsigned evaluated;
     unsigned screened;
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
     __shared__ uint32_t s_queue[WARPS][kQueueCap];
     __shared__ uint32_t s_squeue[PartialScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];
     __shared__ float s_pqueue[RestScreen<NX, NT>::enabled ? WARPS : 1][kQueueCap];  // survivors' partial actions
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;  // the lanes below this one
     uint32_t *queue = s_queue[tid >> 5];
     uint32_t *squeue = s_squeue[PartialScreen<NX, NT>::enabled ? tid >> 5 : 0];
@@ -880,7 +881,28 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<NX, NT>()) integrand_f64(con
         if (scount > 0)  // survivors still queued
             screen(lane < scount ? squeue[lane] : 0u, lane < scount, rest_ok,
                    RestScreen<NX, NT>::enabled && lane < scount ? pqueue[lane] : 0.f);
-        if (lane < count) evaluate(queue[lane]);
+        // The warps' leftover candidates (fewer than 32 each) are gathered into
+        // one list in warp order and evaluated in as few warps as possible:
+        // an FP64 evaluation costs its warp the full width of every FP64
+        // instruction however few lanes are busy, and at the end of a short
+        // chunk every warp would otherwise pay that for one or two candidates
+        // at the same time as the others.
+        {
+            uint32_t *flat = &s_queue[0][0];
+            const uint32_t mine = lane < count ? queue[lane] : 0u;
+            if (lane == 0) sh.left[warp] = count;
+            __syncthreads();
+            int off = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) {
+                const int c_w = sh.left[w];
+                off += w < warp ? c_w : 0;
+                total += c_w;
+            }
+            if (lane < count) flat[off + lane] = mine;
+            __syncthreads();
+            if (tid < total) evaluate(flat[tid]);
+        }
         add_evaluated(args.stats, n_eval, &sh.evaluated);
         if (PartialScreen<NX, NT>::enabled) add_screened(args.screened, n_full, &sh.screened);
         if (two_stage) add_stage1(args.stage1, v.cnt);
