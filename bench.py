@@ -779,7 +779,7 @@ def _next_gaussian(bfi, dev, stream, lat, d, nr):
         ms, t, n_eval = _time_plan(plan, box_lo, box_hi, 2, stream)
         plan.close()
         # FP64 add, multiply and FMA: per sample drawn |z|^2, the triangular F z and the box test; per sample
-        # inside the box S_eff, the products and the sums (Phi^-1, log and exp not counted)
+        # inside the box S_eff, the products and the sums (the Box-Muller log, sqrt and sincospi, and exp, not counted)
         ops = (1 << k) * (d + d * (d + 1) // 2 + 2 * d) + n_eval * ((6 * d + 3) + (5 * d + d // 2 + 1) + 39)
         gauss.append({"samples": 1 << k, "ms": ms, "samples_per_s": (1 << k) / (ms * 1e-3),
                       "inside_box": n_eval / (1 << k),

@@ -243,7 +243,10 @@ bfi_status bfi_plan_set_grid(bfi_plan *plan, int32_t ctas_per_sm);
  *       out-of-range access); the Jacobian prod (1 + y^2)/(1 - y^2)^2 is in
  *       the weight, so a box of [-1, 1]^d integrates over all of R^d.
  *   BFI_SAMPLE_GAUSSIAN   importance sampling (the better-concentrated
- *       integrand Sec. 5 calls for): z_j = Phi^-1(u_j), v = mean + F z, so
+ *       integrand Sec. 5 calls for): z standard normal from the unit point u
+ *       in Box-Muller pairs, z_{2p} = r cos(2 pi u_{2p+1}), z_{2p+1} =
+ *       r sin(2 pi u_{2p+1}), r = sqrt(-2 ln u_{2p}) (for odd d, u_d is the
+ *       next Philox word), v = mean + F z, so
  *       v ~ N(mean, F F^T) with density q; the weight is exp(-S(v)) / q(v)
  *       for v in the box [lo, hi) and 0 outside, so each box's Z_s is still
  *       the integral over that box.  d <= 64.  The record's log V_s holds

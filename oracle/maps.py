@@ -13,8 +13,13 @@ so the estimator is the box estimator of exp(-S_eff) with
 S_eff = S(T(y)) - sum_j ln T'(y_j).
 
 GAUSSIAN (Sec. 5 names a better-concentrated integrand as the way to large
-gains; this is importance sampling): v = mean + F z with z_j = Phi^-1(u_j),
-u the unit point, so v ~ N(mean, F F^T) with density q.  For a box B,
+gains; this is importance sampling): v = mean + F z with z standard normal,
+drawn from the unit point u in Box-Muller pairs (Box & Muller 1958; the paper
+fixes no generator):
+    z_{2p} = r cos(2 pi u_{2p+1}),  z_{2p+1} = r sin(2 pi u_{2p+1}),
+    r = sqrt(-2 ln u_{2p}),
+with u_d the next Philox word when d is odd.  So v ~ N(mean, F F^T) with
+density q.  For a box B,
     int_B exp(-S(v)) dv = E_q[ 1_B(v) exp(-S(v)) / q(v) ],
     1 / q(v) = (2 pi)^(d/2) |det F| exp(|z|^2 / 2),
 so the weight is exp(-S_eff) with S_eff = S(v) - |z|^2 / 2 (0 outside B) and
@@ -36,11 +41,34 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.special import ndtri
 
 from . import eval_points, merge, num_r, points, slot_len
 
 BOX, TRANSFORM, GAUSSIAN = 0, 1, 2
+
+
+def sincospi(x):
+    """(sin(pi x), cos(pi x)) for x in [0, 2].  x - k/2 (k = the nearest
+    integer to 2x) is exact for the unit coordinates, so only pi * y with
+    |y| <= 1/4 rounds; the quarter turns k are applied exactly."""
+    x = np.asarray(x, dtype=float)
+    k = np.rint(2.0 * x)
+    y = x - 0.5 * k
+    s0, c0 = np.sin(math.pi * y), np.cos(math.pi * y)
+    k = k.astype(np.int64) % 4
+    s = np.choose(k, [s0, c0, -s0, -c0])
+    c = np.choose(k, [c0, -s0, -c0, s0])
+    return s, c
+
+
+def standard_normals(u, d):
+    """z [n, d] from unit points u [n, d + (d odd)], pair by pair: Box-Muller."""
+    r = np.sqrt(-2.0 * np.log(u[:, 0::2]))
+    s, c = sincospi(2.0 * u[:, 1::2])
+    z = np.empty((u.shape[0], 2 * r.shape[1]))
+    z[:, 0::2] = r * c
+    z[:, 1::2] = r * s
+    return z[:, :d]
 
 
 def transform(y):
@@ -143,8 +171,9 @@ def integrate_mapped(lat, lo, hi, samples, seed, job_id=0, sub_id=None, kind=TRA
             inside = np.ones(n, dtype=bool)
             log_v = float(np.sum(np.log(hi[s] - lo[s])))
         elif kind == GAUSSIAN:
-            u = points(d, np.zeros(d), np.ones(d), int(sid[s]), seed, job_id, 0, n)
-            z = ndtri(u)
+            dp = d + d % 2
+            u = points(dp, np.zeros(dp), np.ones(dp), int(sid[s]), seed, job_id, 0, n)
+            z = standard_normals(u, d)
             v = mean + z @ factor.T
             lj = 0.5 * np.sum(z * z, axis=1)
             inside = np.all((v >= lo[s]) & (v < hi[s]), axis=1)
@@ -157,4 +186,4 @@ def integrate_mapped(lat, lo, hi, samples, seed, job_id=0, sub_id=None, kind=TRA
 
 
 __all__ = ["BOX", "TRANSFORM", "GAUSSIAN", "transform", "log_jacobian", "linear_limit_eigen",
-           "proposal_covariance", "integrate_mapped", "num_r"]
+           "proposal_covariance", "integrate_mapped", "num_r", "sincospi", "standard_normals"]

@@ -123,6 +123,19 @@ __device__ __forceinline__ double unit_f64(uint32_t w) {
            0.99999999988358467817306518554688;  // 1 - 2^-33
 }
 
+// Standard normal pair from two unit coordinates (Box & Muller, 1958):
+// z0 = r cos(2 pi u2), z1 = r sin(2 pi u2) with r = sqrt(-2 ln u1); u1 > 0
+// always (a unit coordinate lies in (0, 1)).  One logarithm, one square root
+// and one sincospi give two normals, where Phi^-1 costs about as much as all
+// three for each one.
+__device__ __forceinline__ void box_muller(double u1, double u2, double &z0, double &z1) {
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
 template <typename Real>
 struct Coord;
 

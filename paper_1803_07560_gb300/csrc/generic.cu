@@ -181,16 +181,18 @@ __device__ __forceinline__ void lane_products(const float *u, const GenShape &g,
 // word by word.
 template <typename Real, typename Box>
 __device__ __forceinline__ void warp_point(uint64_t i, uint32_t sid, const RoundKeys &rk, const GenShape &g, Box box,
-                                           Real *u) {
+                                           Real *u, int n = -1) {
+    // coordinates 0 .. n - 1 (n <= 4 nq; default d)
+    const int nd = n < 0 ? g.d : n;
     for (int q = threadIdx.x & 31; q < g.nq; q += 32) {
         const uint4 b = philox4x32_10(
             make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), sid), rk);
         const int j = 4 * q;
-        if (j + 4 <= g.d) {
+        if (j + 4 <= nd) {
             store4(u + j, box(j, b.x), box(j + 1, b.y), box(j + 2, b.z), box(j + 3, b.w));
         } else {
             const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
-            for (int t = 0; t < 4 && j + t < g.d; ++t) u[j + t] = box(j + t, w4[t]);
+            for (int t = 0; t < 4 && j + t < nd; ++t) u[j + t] = box(j + t, w4[t]);
         }
     }
     __syncwarp();
@@ -546,7 +548,8 @@ __global__ void __launch_bounds__(kGBlock, lane_min_blocks<SPL, NT>()) generic_i
 //   KIND 1 (the range map of Sec. 4): y uniform in the box (inside
 //          [-1,1]^d), v_j = y_j / (1 - y_j^2), ln J = sum_j ln(1 + y_j^2)
 //          - 2 ln(1 - y_j^2);
-//   KIND 2 (Gaussian importance sampling): z_j = Phi^-1(u_j), v = mean + F z,
+//   KIND 2 (Gaussian importance sampling): z standard normal from the unit
+//          point in Box-Muller pairs (box_muller), v = mean + F z,
 //          ln J = |z|^2 / 2 (the rest of 1/q goes into the record's
 //          log-volume on the host); samples outside the box [lo, hi) have
 //          weight 0.
@@ -609,11 +612,19 @@ __global__ void __launch_bounds__(kGBlock) generic_mapped(const GenArgs ga, cons
                     ud[j] = y / one_m;
                 }
             } else {
-                warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return unit_f64(w); }, zb);
-                for (int j = lane; j < g.d; j += 32) {
-                    const double z = normcdfinv(zb[j]);
-                    part += z * z;
-                    zb[j] = z;
+                // the unit point with one more coordinate for odd d (word d of
+                // the last block), then z in Box-Muller pairs, one pair a lane
+                warp_point<double>(i, v.sid, ga.rk, g, [&](int j, uint32_t w) { return unit_f64(w); }, zb,
+                                   g.d + (g.d & 1));
+                for (int j = 2 * lane; j < g.d; j += 64) {
+                    double z0, z1;
+                    box_muller(zb[j], zb[j + 1], z0, z1);
+                    part += z0 * z0;
+                    zb[j] = z0;
+                    if (j + 1 < g.d) {
+                        part += z1 * z1;
+                        zb[j + 1] = z1;
+                    }
                 }
                 part *= 0.5;
                 __syncwarp();

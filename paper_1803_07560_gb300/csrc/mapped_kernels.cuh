@@ -8,7 +8,8 @@
 //                  v_j = y_j / (1 - y_j^2), S_eff = S(v) - ln J with
 //                  ln J = sum_j ln[(1 + y_j^2) / (1 - y_j^2)^2], weight,
 //                  products and per-thread sums -> one FP64 record per chunk
-//   gaussian_f64   the same with v = mean + F Phi^-1(u), S_eff = S(v) -
+//   gaussian_f64   the same with v = mean + F z, z standard normal from the
+//                  unit point by the Box-Muller transform, S_eff = S(v) -
 //                  |z|^2 / 2 and weight 0 outside the box (d <= 40)
 //
 // There is no FP32 screen: the map stretches the coordinates without bound
@@ -141,8 +142,10 @@ __global__ void __launch_bounds__(BLOCK, 1) transform_f64(const IntegrandArgs ar
 
 // ---------------------------------------------------------------------------
 // Gaussian importance sampling, thread per sample (d <= kGaussThreadMaxD):
-// z_j = Phi^-1(u_j) for the unit point u (the box plays no part in drawing),
-// v = mean + F z, S_eff = S(v) - |z|^2 / 2, and weight 0 outside the box
+// z_{2p}, z_{2p+1} = box_muller(u_{2p}, u_{2p+1}) for the unit point u (the
+// box plays no part in drawing; for odd d the pair of z_{d-1} takes word d of
+// the last Philox block), v = mean + F z, S_eff = S(v) - |z|^2 / 2, and
+// weight 0 outside the box
 // [lo, hi).  The rest of 1/q (the record's log-volume (d/2) ln 2 pi +
 // ln |det F|) is set by the merge.  F, held transposed in shared memory
 // (column j of F contiguous, every thread reading the same word), is applied
@@ -196,13 +199,21 @@ __global__ void __launch_bounds__(BLOCK, 1) gaussian_f64(const IntegrandArgs arg
                 const uint4 b = philox_from_prefix(x, s_pre[q], rk);
                 const uint32_t w4[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
+                for (int t = 0; t < 4; t += 2) {
                     const int j = 4 * q + t;
                     if (j < D) {
-                        const double z = normcdfinv(unit_f64(w4[t]));
-                        zz = fma(z, z, zz);
+                        double zp[2];
+                        box_muller(unit_f64(w4[t]), unit_f64(w4[t + 1]), zp[0], zp[1]);
 #pragma unroll
-                        for (int r = 0; r < (TRI ? j + 1 : D); ++r) u[r] = fma(s_ft[j * D + r], z, u[r]);
+                        for (int e = 0; e < 2; ++e) {
+                            if (j + e < D) {
+                                const double z = zp[e];
+                                zz = fma(z, z, zz);
+#pragma unroll
+                                for (int r = 0; r < (TRI ? j + e + 1 : D); ++r)
+                                    u[r] = fma(s_ft[(j + e) * D + r], z, u[r]);
+                            }
+                        }
                     }
                 }
             }

@@ -10,7 +10,7 @@ from scipy import integrate as sint
 
 import oracle
 from oracle.maps import (BOX, GAUSSIAN, TRANSFORM, integrate_mapped, linear_limit_eigen, log_jacobian,
-                         proposal_covariance, transform)
+                         proposal_covariance, sincospi, standard_normals, transform)
 from gl_reference import action_np, gl_box, linear_limit
 
 
@@ -121,3 +121,31 @@ def test_gaussian_with_no_sample_in_the_box():
     slots, tot = integrate_mapped(lat, 4 * np.ones(3), 5 * np.ones(3), 100, seed=1, kind=GAUSSIAN, factor=F)
     assert slots[0, 0] == 100 and slots[0, 1] == math.inf and slots[0, 3] == 0.0
     assert tot[0] == -math.inf
+
+
+def test_normal_pairs_at_closed_form_points():
+    """Box-Muller at points where it has exact values: u_{2p} = e^-2 gives
+    r = 2; angles of 2 pi u in eighths and quarters of a turn, with cos on the
+    even coordinate and sin on the odd one."""
+    u = np.array([[math.exp(-2.0), 0.125, math.exp(-0.5), 0.25, math.exp(-2.0), 0.75]])
+    z = standard_normals(u, 5)    # d = 5: the sixth word completes the last pair and is dropped
+    assert z.shape == (1, 5)
+    np.testing.assert_allclose(z[0], [math.sqrt(2.0), math.sqrt(2.0), 0.0, 1.0, 0.0], atol=1e-15)
+    s, c = sincospi(np.array([0.0, 0.5, 1.0, 1.5, 1.0 / 6.0, 1.75]))
+    np.testing.assert_allclose(s, [0.0, 1.0, 0.0, -1.0, 0.5, -math.sqrt(0.5)], atol=1e-16)
+    np.testing.assert_allclose(c, [1.0, 0.0, -1.0, 0.0, math.sqrt(0.75), math.sqrt(0.5)], atol=1e-16)
+
+
+def test_normals_from_philox_points_are_standard_and_independent():
+    """z from 2^16 oracle unit points (d = 5, six words): each coordinate passes
+    a Kolmogorov-Smirnov test against N(0, 1), its variance is 1 within four
+    standard errors, and the two members of a pair are uncorrelated."""
+    from scipy import stats
+    n, d = 1 << 16, 5
+    u = oracle.points(d + 1, np.zeros(d + 1), np.ones(d + 1), 4, 11, 2, 0, n)
+    z = standard_normals(u, d)
+    for j in range(d):
+        assert stats.kstest(z[:, j], "norm").pvalue > 1e-3, j
+        assert abs(np.mean(z[:, j] ** 2) - 1.0) < 4.0 * math.sqrt(2.0 / n)
+    for j in (0, 2):
+        assert abs(np.corrcoef(z[:, j], z[:, j + 1])[0, 1]) < 4.0 / math.sqrt(n)
