@@ -824,7 +824,9 @@ bfi_status bfi_merge_host(int32_t nx, int64_t nsub, const double *slots, double 
 //            (|Q_r| <= Q_0 by Cauchy-Schwarz), then w Q_r, one rounding
 //   sums     per thread (at most N_t terms per chunk): FP32 Kahan 2u + N_t u^2,
 //            FP64 plain (N_t - 1) u; then the FP64 merges of threads, chunks
-//            and subvolumes, 2^-53 (64 + 4 chunks + 4 nsub)
+//            and subvolumes, 2^-53 (64 + 4 chunks + 4 nsub); in FP32 the
+//            chunk record first adds each lane's 8 threads in double-float
+//            (16 exactly scaled terms), 2^-42 more
 //   dropped  e^-c of Z (c = 20 in FP32, 34 in FP64); of N(r), e^-c vmax^2 Z,
 //            since |P_r| <= vmax^2
 // Z: b_Z = weight + sums + merges + e^-c.  N(r) relative to N(0): b_N =
@@ -870,7 +872,8 @@ bfi_status bfi_error_bound(const bfi_lattice *lattice, bfi_precision precision, 
     // chunk: at most 2048 rows per thread
     const double n_t = shape && shape->kernel == 0 ? 2048.0 : 2048.0 * bfi::kBlock / 4.0;
     const double e_sum = f32 ? 2.0 * u + n_t * u * u : (n_t - 1.0) * u;
-    const double e_merge = 0x1p-53 * (64.0 + 4.0 * std::ceil(n_max / 1024.0) + 4.0 * static_cast<double>(nsub));
+    const double e_merge = 0x1p-53 * (64.0 + 4.0 * std::ceil(n_max / 1024.0) + 4.0 * static_cast<double>(nsub)) +
+                           (f32 ? 0x1p-42 : 0.0);
     const double drop = std::exp(-c);
     const double bz = e_w + e_sum + e_merge + drop;
     const double bn = e_w + e_q + e_sum + e_merge + drop * vmax * vmax / C0;

@@ -17,6 +17,7 @@
 #include "bfi_kernels.h"
 
 #include <cmath>
+#include <type_traits>
 
 // Resident CTAs per SM the integrand kernels are compiled for; 0 (default)
 // picks it from the lattice size (registers grow with d, shared memory with R).
@@ -552,6 +553,14 @@ struct SmemSums<double, K, BLOCK> {
 // s_f; then warp w sums elements k = w, w + WARPS, ... over all threads, lane
 // l taking threads l, l + 32, ... in order and the lanes combining in a fixed
 // butterfly.  Every order is fixed, so the record is reproducible.
+// FP32 sums: every thread's shift is the hint moved down by whole steps of
+// ln 2 (shift_steps), so m_t - m_b is n ln 2 up to the double roundings of
+// those moves, far below half a step, and the factor is exactly 2^-n.  A lane
+// then scales its threads' float sums exactly and adds them (and their Kahan
+// compensations) in double-float on the FP32 pipe, 16 terms with a relative
+// error below 2^-42 of their magnitudes; only its partial and the butterfly
+// are double.  (In double the same took a multiply, an add and, per thread,
+// an exp on the FP64 pipe, 2 lanes per SM and clock, for every short chunk.)
 template <typename Real, int K, int R, int BLOCK>
 __device__ __forceinline__ void chunk_record(const SmemSums<Real, K, BLOCK> &acc, double m_t, double *s_f,
                                              double *s_mb, double *out, uint64_t cnt) {
@@ -568,16 +577,33 @@ __device__ __forceinline__ void chunk_record(const SmemSums<Real, K, BLOCK> &acc
     }
     __syncthreads();
     const double mb = *s_mb;
-    s_f[tid] = (m_t == INFINITY) ? 0.0 : (m_t == mb ? 1.0 : exp(mb - m_t));
+    if constexpr (std::is_same<Real, float>::value) {
+        const double n = (m_t - mb) * (1.0 / kLn2);  // >= 0; NaN or huge: no weight
+        s_f[tid] = n < 1000.0 ? ldexp(1.0, -static_cast<int>(rint(n))) : 0.0;
+    } else {
+        s_f[tid] = (m_t == INFINITY) ? 0.0 : (m_t == mb ? 1.0 : exp(mb - m_t));
+    }
     __syncthreads();
     const Real *base = acc.b - tid;  // element k of thread t: sums of thread t
     for (int k = warp; k < K; k += WARPS) {
         const bool sq = second_order(k, R);
         double part = 0.0;
-        for (int t = lane; t < BLOCK; t += 32) {
-            SmemSums<Real, K, BLOCK> other{const_cast<Real *>(base) + t};
-            const double f = s_f[t];
-            part = __dadd_rn(part, __dmul_rn(other.value(k), sq ? f * f : f));
+        if constexpr (std::is_same<Real, float>::value) {
+            using F32Sums = SmemSums<float, K, BLOCK>;
+            DF p{0.f, 0.f};
+            for (int t = lane; t < BLOCK; t += 32) {
+                const double f = s_f[t];
+                const float ff = static_cast<float>(sq ? f * f : f);
+                p = df_add_f(p, __fmul_rn(base[k * BLOCK + t], ff));
+                if (F32Sums::compensated(k)) p = df_add_f(p, -__fmul_rn(base[F32Sums::cidx(k) * BLOCK + t], ff));
+            }
+            part = static_cast<double>(p.h) + static_cast<double>(p.l);
+        } else {
+            for (int t = lane; t < BLOCK; t += 32) {
+                SmemSums<Real, K, BLOCK> other{const_cast<Real *>(base) + t};
+                const double f = s_f[t];
+                part = __dadd_rn(part, __dmul_rn(other.value(k), sq ? f * f : f));
+            }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) part = __dadd_rn(part, __shfl_xor_sync(0xffffffffu, part, off));
