@@ -218,7 +218,10 @@ bfi_status bfi_chunking_of(int64_t nsub, const uint64_t *samples, bfi_chunking *
  *   slots   device [nsub * bfi_slot_len(nx)]   out
  *   totals  device [bfi_totals_len(nx)]        out
  * Bounds are not validated on the device; lo >= hi gives undefined numbers
- * (never an out-of-range access).  Errors: BFI_E_INVALID (NULL pointers),
+ * (never an out-of-range access).  One plan holds one execution's scratch
+ * (chunk records, counters, the chunk hand-out counter): executions of the
+ * same plan must not overlap on the GPU (order them on one stream); use one
+ * plan per concurrent job.  Errors: BFI_E_INVALID (NULL pointers),
  * BFI_E_CUDA (launch failure). */
 bfi_status bfi_plan_execute(bfi_plan *plan, const double *lo, const double *hi,
                             const uint32_t *sub_id, uint32_t seed, uint32_t job_id,
