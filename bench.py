@@ -188,9 +188,10 @@ def rank_info():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs; the
-    raw samples go to $BFI_CLOCKS_DIR (default: the system temporary
-    directory) as clocks_<pid>.csv."""
+    """nvidia-smi clock / throttle sampling while the timed region runs, every
+    100 ms with a timestamp; stop(region) keeps the samples inside the timed
+    region's host wall-clock interval.  The raw samples go to $BFI_CLOCKS_DIR
+    (default: the system temporary directory) as clocks_<pid>.csv."""
 
     def __init__(self, gpu_index: int):
         import tempfile
@@ -198,18 +199,34 @@ class ClockSampler:
         self.path = os.path.join(os.environ.get("BFI_CLOCKS_DIR") or tempfile.gettempdir(),
                                  f"clocks_{os.getpid()}.csv")
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
+    def wait_first(self, timeout_s: float = 5.0):
+        """Returns once the sampler has written its first sample (or after
+        timeout_s), so that sampling is running when the timed region starts."""
+        t_end = time.time() + timeout_s
+        while self.proc is not None and time.time() < t_end:
+            self.fh.flush()
+            try:
+                if any(len(line.split(",")) >= 10 for line in open(self.path)):
+                    return
+            except OSError:
+                return
+            time.sleep(0.02)
+
+    def stop(self, region=None):
+        """Median SM clock, the maximum, and the throttle reasons seen, over the
+        samples inside region = (t0, t1) host wall-clock seconds (all samples
+        when none falls inside, with in_region false)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -218,23 +235,31 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        mhz, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                mhz.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(mhz) if mhz else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(mhz)}
+        return parse_clock_samples(open(self.path).read().splitlines(), region)
+
+
+def parse_clock_samples(lines, region=None):
+    """The clocks record from nvidia-smi CSV lines (timestamp, index, SM clock,
+    max SM clock, power, reasons active, hw_slowdown, hw_thermal_slowdown,
+    sw_thermal_slowdown, sw_power_cap)."""
+    import datetime
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            rows.append((ts, float(f[2]), float(f[3]), [n for n, v in zip(names, f[6:10]) if v.lower() == "active"]))
+        except ValueError:
+            continue
+    inside = [r for r in rows if region is not None and region[0] <= r[0] <= region[1]]
+    use = inside if inside else rows
+    return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+            "sm_max_mhz": max(r[2] for r in use) if use else None,
+            "reasons": sorted({n for r in use for n in r[3]}),
+            "samples": len(inside), "samples_total": len(rows), "in_region": bool(inside)}
 
 
 def cpu_sample_job():
@@ -304,8 +329,10 @@ def make_job(rank, world, samples_per_sub):
                          seed=2, sub_id=np.arange(sl.start, sl.stop, dtype=np.uint32))
 
 
-def timed_steps(plan, lo, hi, sid, job, steps, warmup, flush_buf, dist, stream):
-    """Per-step CUDA events on the launch stream; the L2 flush sits between steps."""
+def timed_steps(plan, lo, hi, sid, job, steps, warmup, flush_buf, dist, stream, region=None):
+    """Per-step CUDA events on the launch stream; the L2 flush sits between
+    steps.  region (a list) receives the timed region's host wall-clock
+    interval."""
     import torch
     for _ in range(warmup):
         plan.execute(lo, hi, job.seed, job.job_id, sub_id=sid, stream=stream)
@@ -316,6 +343,7 @@ def timed_steps(plan, lo, hi, sid, job, steps, warmup, flush_buf, dist, stream):
     plan.set_timing(True)
     total_ms, kern_ms = 0.0, 0.0
     slots = totals = None
+    t0 = time.time()
     for _ in range(steps):
         with torch.cuda.stream(stream):
             flush_buf.zero_()
@@ -329,6 +357,8 @@ def timed_steps(plan, lo, hi, sid, job, steps, warmup, flush_buf, dist, stream):
         kern_ms += plan.timing()[0]
     plan.set_timing(False)
     torch.cuda.synchronize()
+    if region is not None:
+        region.extend([t0, time.time()])
     if dist is not None:
         dist.barrier()
     return total_ms / steps, kern_ms / steps, slots, totals, plan.work().as_dict()
@@ -360,9 +390,12 @@ def run_bfi(args):
     plan = bfi.Plan(lat, job.samples, bfi.FP64, device=local_rank)
     info = plan.info()
     sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.wait_first()
+    region = []
     ms, kern_ms, slots, totals, work = timed_steps(plan, lo, hi, sid, job, args.steps, args.warmup, flush_buf, dist,
-                                                   stream)
-    clocks = sampler.stop() if sampler else None
+                                                   stream, region)
+    clocks = sampler.stop(region) if sampler else None
 
     # the exchange: gather every rank's subvolume records, merge in FP64
     from paper_1803_07560_gb300 import shard
@@ -918,7 +951,7 @@ def main():
     ap.add_argument("--lattice", default="10x2",
                     help="NXxNT of the timed job (the workload is 10x2; others for profiling other kernels)")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="bfi", choices=["bfi", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")

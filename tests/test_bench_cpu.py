@@ -117,3 +117,26 @@ def test_bench_jobs_have_one_box_per_budget_for_every_lattice(monkeypatch):
         for a, b in rng.integers(0, 1024, (200, 2)):
             if a != b:
                 assert np.any((job.hi[a] <= job.lo[b]) | (job.hi[b] <= job.lo[a]))
+
+
+def test_clock_record_keeps_the_samples_inside_the_timed_region():
+    """nvidia-smi lines (timestamp first): the record's median clock and
+    throttle reasons come from the samples inside the timed region only, and
+    fall back to all samples, flagged, when none falls inside."""
+    import datetime
+    t0 = datetime.datetime(2026, 1, 2, 3, 4, 5, 0)
+
+    def line(ds, mhz, thermal="Not Active"):
+        ts = (t0 + datetime.timedelta(seconds=ds)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 900.5, 0x0000000000000000, Not Active, {thermal}, Not Active, Active"
+
+    lines = [line(0.0, 1500, "Active"), line(0.1, 2070), line(0.2, 2070), line(0.3, 2055), line(0.9, 1400)]
+    base = t0.timestamp()
+    rec = bench.parse_clock_samples(lines, (base + 0.05, base + 0.35))
+    assert rec["samples"] == 3 and rec["samples_total"] == 5 and rec["in_region"]
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"]          # the thermal flag at t = 0 lies outside
+    rec = bench.parse_clock_samples(lines, (base + 5.0, base + 6.0))
+    assert rec["samples"] == 0 and not rec["in_region"] and rec["samples_total"] == 5
+    assert "hw_thermal_slowdown" in rec["reasons"]     # all samples, so the rejection rule still sees it
+    assert bench.parse_clock_samples(["garbage", ""], None)["sm_mhz"] is None
